@@ -1,0 +1,200 @@
+/*
+ * acm.h -- C ABI of the GB300 (sm_103a) implementation of accelerated
+ * computational micromechanics (ACM) for periodic porous unit cells
+ * (Karimi & Bhattacharya, arXiv 2312.15554).
+ *
+ * Problem (Section 2, Eq. 1): in the periodic unit cube Y = Y_p (pore) + Y_s (solid),
+ *   Stokes flow   -grad p + nu Lap u + g = 0, div u = 0 in Y_p, u = 0 in Y_s;
+ *   solute        Pe u.(grad chi) - Lap chi = Pe (ubar - u).g_chi in Y_p,
+ *                 zero-flux condition on the pore boundary;
+ * with effective permeability K (Eq. 2) and diffusivity D (Eq. 3).
+ *
+ * Method (Section 3): Stokes by ADMM on an augmented Lagrangian (Eq. 6-13) with
+ * adaptive penalties (Eq. 22); solute by a Lippmann-Schwinger fixed point with a
+ * fictitious solid diffusivity (Eq. 14-21). Every iteration is a voxelwise local
+ * step plus a constant-coefficient solve in Fourier space.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid      (n0, n1, n2), each a power of two in [8, 512]; axis 2 is contiguous.
+ *           The cell is the unit cube; h_c = 1/n_c; V = n0*n1*n2 voxels.
+ * H         uint8_t[n0][n1][n2], 1 = solid, 0 = pore (Eq. 4).
+ * Vectors   component-planar [3][n0][n1][n2]; component c is along array axis c.
+ *           Load direction e_j therefore means array axis j.
+ * Reals     float when the precision is ACM_FP32, double otherwise (the
+ *           "real type" below).
+ * Pointers  every array argument may be a device pointer or a host pointer.
+ *           Device pointers are used in place; host buffers (pageable or
+ *           pinned) are staged through the context's device workspace with
+ *           copies on the context's stream, so a host call includes the
+ *           host<->device transfers. Scalars and reports are host memory.
+ * Ownership the library never frees or retains caller memory. A context owns
+ *           its workspace (allocated on first use of a precision, freed by
+ *           acm_destroy). Calls on one context are not thread safe; distinct
+ *           contexts are independent.
+ * Streams   all device work of a context is ordered on the stream given at
+ *           acm_create (NULL = legacy default stream). Every solver entry point
+ *           returns after its results are complete on the host side (K, D,
+ *           reports) and enqueued on the stream (fields).
+ * Errors    every entry point returns an acm_status and never aborts. On any
+ *           status other than ACM_OK and ACM_ERR_MAXITER the output fields are
+ *           unspecified; ACM_ERR_MAXITER still writes every output.
+ */
+#ifndef ACM_H
+#define ACM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct acm_ctx acm_ctx;
+
+typedef enum acm_status {
+  ACM_OK = 0,
+  ACM_ERR_ARG = -1,              /* invalid argument (null pointer, bad size or parameter) */
+  ACM_ERR_NOMEM = -2,            /* device allocation failed */
+  ACM_ERR_CUDA = -3,             /* a CUDA runtime call failed */
+  ACM_ERR_MAXITER = -4,          /* max_iter reached before the tolerance; outputs written */
+  ACM_ERR_DIVERGED = -5,         /* residual grew 1e3x above its running minimum */
+  ACM_ERR_NONFINITE = -6,        /* a residual became NaN or infinite */
+  ACM_ERR_NO_SOLID = -7,         /* Stokes: H has no solid voxel (mean flow unbounded) */
+  ACM_ERR_NO_FLUID = -8,         /* H has no pore voxel */
+  ACM_ERR_TIMEOUT = -9,          /* a bounded device wait gave up */
+  ACM_ERR_UNSUPPORTED_SIZE = -10 /* grid size outside the supported set */
+} acm_status;
+
+typedef enum acm_deriv {
+  ACM_DERIV_EXACT = 0,   /* d_c = k_c (0 on the Nyquist plane), L = |k|^2 (Eq. 13) */
+  ACM_DERIV_CENTRAL = 1  /* d_c = sin(h k_c)/h, L = sum 4 sin^2(h k_c/2)/h^2 (Eq. 21) */
+} acm_deriv;
+
+typedef enum acm_precision {
+  ACM_FP32 = 0,           /* FP32 fields and FFTs, FP64 reductions */
+  ACM_FP64 = 1,           /* FP64 throughout */
+  ACM_FP32_THEN_FP64 = 2  /* FP32 iterations to eps32, then FP64 iterations to eps */
+} acm_precision;
+
+/* Stokes (ADMM) parameters, Section 3.1 and Eq. 22. */
+typedef struct acm_stokes_params {
+  double nu;           /* viscosity (default 1) */
+  double eps;          /* eps_abs = eps_rel of Eq. 11-12 (default 1e-5) */
+  double alpha0;       /* initial penalty alpha (solid constraint); <= 0 selects the default */
+  double beta0;        /* initial penalty beta (incompressibility); <= 0 selects the default */
+  double b0;           /* initial penalty b (u = u~); <= 0 selects the default */
+  double phi[3];       /* Eq. 22 growth factors for (alpha, beta, b) (default 1.1) */
+  double tau[3];       /* Eq. 22 residual-balance ratios (default {5, 10, 5}) */
+  double psi_min_frac; /* psi_min = psi_min_frac * psi0 (default 1e-3) */
+  double eps32;        /* FP32 phase tolerance of ACM_FP32_THEN_FP64 (default 1e-5) */
+  int max_iter;        /* iteration cap (default 20000) */
+  int adaptive;        /* 1: Eq. 22 penalty updates; 0: fixed penalties (default 1) */
+  int deriv;           /* acm_deriv (default ACM_DERIV_EXACT) */
+  int precision;       /* acm_precision (default ACM_FP32) */
+  int check_every;     /* iterations between host checks of the stop flag (default 16) */
+} acm_stokes_params;
+
+/* Solute (Lippmann-Schwinger) parameters, Section 3.2. */
+typedef struct acm_advdiff_params {
+  double eta;          /* fictitious solid diffusivity (default 0.01) */
+  double A0;           /* comparison medium A0 > 0 (default 0.55) */
+  double B0[3];        /* comparison medium B0, used when B0_explicit = 1 */
+  int B0_explicit;     /* 0: B0 = mean over Y of B = Pe (1-H) u (default); 1: B0 as given */
+  double eps;          /* tolerance of Eq. 19 (default 1e-5) */
+  int max_iter;        /* iteration cap (default 20000) */
+  int deriv;           /* acm_deriv (default ACM_DERIV_CENTRAL) */
+  int precision;       /* acm_precision (default ACM_FP32) */
+  int check_every;     /* iterations between host checks of the stop flag (default 16) */
+} acm_advdiff_params;
+
+/* Per-solve report. For Stokes res/tol hold r_p1, r_d1, r_p2, r_d2, r_p3, r_d3
+ * (Eq. 10) and their tolerances (Eq. 11-12) of the last iteration; psi the
+ * penalties alpha, beta, b of that iteration. For the solute res[0..1] hold
+ * r1, r2 (Eq. 19) and tol[0..1] their tolerances. */
+typedef struct acm_report {
+  int iters;           /* total iterations */
+  int iters_fp64;      /* iterations of those run in FP64 */
+  int converged;       /* 1 when every residual passed its tolerance */
+  int status;          /* acm_status of this solve */
+  double res[6];
+  double tol[6];
+  double psi[3];
+  double time_ms;      /* wall time of the solve (host clock, stream synchronised) */
+} acm_report;
+
+/* Fill defaults (documented in the structs above). Returns ACM_ERR_ARG on NULL. */
+acm_status acm_stokes_default_params(acm_stokes_params* p);
+acm_status acm_advdiff_default_params(acm_advdiff_params* p);
+
+/* Create a context for grids of shape (n0, n1, n2) whose device work runs on
+ * `cuda_stream` (a cudaStream_t, NULL for the default stream) of the current
+ * device. Returns ACM_ERR_UNSUPPORTED_SIZE unless every n_c is a power of two
+ * in [8, 512]. */
+acm_status acm_create(acm_ctx** ctx, int n0, int n1, int n2, void* cuda_stream);
+acm_status acm_destroy(acm_ctx* ctx);
+
+/* Problem 1 of Algorithm 1 (Section 3.1): Stokes flow for the body force g
+ * (g = -g_p, the negative average pressure gradient of Eq. 1).
+ *   init_u, init_lambda  optional warm start (NULL = zero): X^0 = {u, u~ = u,
+ *                        q = 0, a = H lambda, lambda = H lambda}; real type.
+ *   u       out [3][V] velocity u^{n} of the last iteration (real type).
+ *   p       out [V] pressure q - mean(q) (nullable; real type).
+ *   lambda  out [3][V] solid multiplier H lambda (nullable; real type).
+ *   K_col   out (host, 3 doubles, nullable) volume average of u, i.e. K g for
+ *           nu = 1 (the average-velocity form of Eq. 2).
+ *   rep     out (host, nullable).
+ * Returns ACM_ERR_NO_SOLID when H has no solid voxel (the mean flow is then
+ * unbounded) and ACM_ERR_NO_FLUID when H is all solid. */
+acm_status acm_stokes(acm_ctx* ctx, const uint8_t* H, const double g[3],
+                      const acm_stokes_params* prm,
+                      const void* init_u, const void* init_lambda,
+                      void* u, void* p, void* lambda,
+                      double K_col[3], acm_report* rep);
+
+/* The three unit loads e_j solved together (superposition, Section 2).
+ *   u3      out [3 loads][3][V] (real type; nullable).
+ *   K       out (host, 9 doubles, row-major K[i][j] = mean of u^j_i).
+ *   K_grad  out (host, 9 doubles, nullable): Eq. 2 literally, the integral over
+ *           Y_p of grad u^i : grad u^j with the spectral gradient of prm->deriv.
+ *   rep     out (host, 3 reports, nullable). */
+acm_status acm_stokes_tensor(acm_ctx* ctx, const uint8_t* H, const acm_stokes_params* prm,
+                             void* u3, double K[9], double K_grad[9], acm_report rep[3]);
+
+/* Problem 2 of Algorithm 1 (Section 3.2): the concentration corrector chi for
+ * the composition gradient g_chi, advected by the velocity u (real type
+ * [3][V], e.g. the output of acm_stokes) at Peclet number Pe.
+ *   chi       out [V] (real type, nullable), mean zero.
+ *   grad_chi  out [3][V] (real type, nullable), spectral gradient.
+ *   Dg        out (host, 3 doubles): Eq. 3 contracted with g_chi,
+ *             (D g)_i = (1/V) sum_pore [g_i + Pe (ubar - u)_i chi + d_i chi].
+ *   Dg_ext    out (host, 3 doubles, nullable): extended-domain average
+ *             (1/V) sum_Y A (g + grad chi)_i + the same Pe term.
+ * The real type of u, chi and grad_chi follows prm->precision. */
+acm_status acm_advdiff(acm_ctx* ctx, const uint8_t* H, const void* u, double Pe,
+                       const double g_chi[3], const acm_advdiff_params* prm,
+                       void* chi, void* grad_chi, double Dg[3], double Dg_ext[3],
+                       acm_report* rep);
+
+/* The three composition loads e_j: D (host, 9 doubles, row-major D[i][j] =
+ * (D e_j)_i), D_ext (nullable), chi3 out [3 loads][V] (nullable). */
+acm_status acm_advdiff_tensor(acm_ctx* ctx, const uint8_t* H, const void* u, double Pe,
+                              const acm_advdiff_params* prm, void* chi3,
+                              double D[9], double D_ext[9], acm_report rep[3]);
+
+/* The 3D real-to-complex transform used by both solvers, exposed for testing:
+ * f^(m) = sum_x f(x) exp(-2 pi i m.x), unnormalised.
+ *   in   real [nbatch][V] (float when fp64 = 0, double otherwise).
+ *   out  complex interleaved (re, im) [nbatch][n0][n1][n2/2 + 1].
+ * acm_fft_c2r is the exact inverse: it divides by V. */
+acm_status acm_fft_r2c(acm_ctx* ctx, int fp64, int nbatch, const void* in, void* out);
+acm_status acm_fft_c2r(acm_ctx* ctx, int fp64, int nbatch, const void* in, void* out);
+
+/* Human-readable name of a status code (static string). */
+const char* acm_status_str(acm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACM_H */

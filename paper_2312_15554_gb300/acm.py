@@ -1,0 +1,228 @@
+"""Thin Python binding of the ACM C ABI (include/acm.h).
+
+Argument marshalling only: every step of the method runs inside libacm.so. The
+names mirror the C entry points. Array arguments may be torch tensors (CUDA or
+CPU, contiguous) or numpy arrays (host memory); scalars and reports are Python
+values. The library is loaded lazily and a missing or unloadable build raises
+immediately: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB = None
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libacm.so")
+
+ACM_OK = 0
+ACM_ERR_MAXITER = -4
+DERIV_EXACT, DERIV_CENTRAL = 0, 1
+FP32, FP64, FP32_THEN_FP64 = 0, 1, 2
+
+EXPORTED = (
+    "acm_stokes_default_params", "acm_advdiff_default_params", "acm_create", "acm_destroy",
+    "acm_stokes", "acm_stokes_tensor", "acm_advdiff", "acm_advdiff_tensor",
+    "acm_fft_r2c", "acm_fft_c2r", "acm_status_str",
+)
+
+
+class acm_stokes_params(C.Structure):
+    _fields_ = [("nu", C.c_double), ("eps", C.c_double), ("alpha0", C.c_double), ("beta0", C.c_double),
+                ("b0", C.c_double), ("phi", C.c_double * 3), ("tau", C.c_double * 3),
+                ("psi_min_frac", C.c_double), ("eps32", C.c_double), ("max_iter", C.c_int),
+                ("adaptive", C.c_int), ("deriv", C.c_int), ("precision", C.c_int), ("check_every", C.c_int)]
+
+
+class acm_advdiff_params(C.Structure):
+    _fields_ = [("eta", C.c_double), ("A0", C.c_double), ("B0", C.c_double * 3), ("B0_explicit", C.c_int),
+                ("eps", C.c_double), ("max_iter", C.c_int), ("deriv", C.c_int), ("precision", C.c_int),
+                ("check_every", C.c_int)]
+
+
+class acm_report(C.Structure):
+    _fields_ = [("iters", C.c_int), ("iters_fp64", C.c_int), ("converged", C.c_int), ("status", C.c_int),
+                ("res", C.c_double * 6), ("tol", C.c_double * 6), ("psi", C.c_double * 3),
+                ("time_ms", C.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "iters_fp64": self.iters_fp64, "converged": bool(self.converged),
+                "status": self.status, "res": list(self.res), "tol": list(self.tol), "psi": list(self.psi),
+                "time_ms": self.time_ms}
+
+
+class AcmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+        self.status = status
+
+
+def load(path: str = None):
+    """Load libacm.so; raises if it has not been built or cannot be loaded."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libacm.so not built at {path}: run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, cp, dp, ip = C.c_void_p, C.c_char_p, C.POINTER(C.c_double), C.c_int
+    lib.acm_stokes_default_params.argtypes = [C.POINTER(acm_stokes_params)]
+    lib.acm_advdiff_default_params.argtypes = [C.POINTER(acm_advdiff_params)]
+    lib.acm_create.argtypes = [C.POINTER(vp), ip, ip, ip, vp]
+    lib.acm_destroy.argtypes = [vp]
+    lib.acm_stokes.argtypes = [vp, vp, dp, C.POINTER(acm_stokes_params), vp, vp, vp, vp, vp, dp,
+                               C.POINTER(acm_report)]
+    lib.acm_stokes_tensor.argtypes = [vp, vp, C.POINTER(acm_stokes_params), vp, dp, dp, C.POINTER(acm_report)]
+    lib.acm_advdiff.argtypes = [vp, vp, vp, C.c_double, dp, C.POINTER(acm_advdiff_params), vp, vp, dp, dp,
+                                C.POINTER(acm_report)]
+    lib.acm_advdiff_tensor.argtypes = [vp, vp, vp, C.c_double, C.POINTER(acm_advdiff_params), vp, dp, dp,
+                                       C.POINTER(acm_report)]
+    lib.acm_fft_r2c.argtypes = [vp, ip, ip, vp, vp]
+    lib.acm_fft_c2r.argtypes = [vp, ip, ip, vp, vp]
+    lib.acm_status_str.argtypes = [ip]
+    lib.acm_status_str.restype = cp
+    for name in EXPORTED:
+        if name not in ("acm_status_str",):
+            getattr(lib, name).restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+def status_str(s: int) -> str:
+    return load().acm_status_str(int(s)).decode()
+
+
+def _check(s: int, where: str, allow_maxiter: bool = False):
+    if s == ACM_OK or (allow_maxiter and s == ACM_ERR_MAXITER):
+        return s
+    raise AcmError(s, where)
+
+
+def _ptr(x):
+    """Raw address of a contiguous torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _dvec(v, n=3):
+    return (C.c_double * n)(*[float(a) for a in v])
+
+
+def stokes_params(**kw) -> acm_stokes_params:
+    p = acm_stokes_params()
+    load().acm_stokes_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k in ("phi", "tau"):
+            setattr(p, k, (C.c_double * 3)(*v))
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def advdiff_params(**kw) -> acm_advdiff_params:
+    p = acm_advdiff_params()
+    load().acm_advdiff_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "B0":
+            p.B0 = (C.c_double * 3)(*v)
+            p.B0_explicit = 1
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class acm_ctx:
+    """Owns an acm_ctx* for grids of shape (n0, n1, n2) on a CUDA stream (handle or 0)."""
+
+    def __init__(self, shape, stream: int = 0):
+        lib = load()
+        self.shape = tuple(int(s) for s in shape)
+        h = C.c_void_p()
+        _check(lib.acm_create(C.byref(h), *self.shape, C.c_void_p(stream)), "acm_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().acm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def acm_create(shape, stream: int = 0) -> acm_ctx:
+    return acm_ctx(shape, stream)
+
+
+def acm_destroy(ctx: acm_ctx):
+    ctx.close()
+
+
+def acm_stokes(ctx, H, g, params=None, init_u=None, init_lambda=None, u=None, p=None, lam=None):
+    """acm_stokes: returns (status, K_col, report); fields are written into u, p, lam."""
+    K = (C.c_double * 3)()
+    rep = acm_report()
+    s = load().acm_stokes(ctx.h, _ptr(H), _dvec(g), C.byref(params or stokes_params()), _ptr(init_u),
+                          _ptr(init_lambda), _ptr(u), _ptr(p), _ptr(lam), K, C.byref(rep))
+    _check(s, "acm_stokes", allow_maxiter=True)
+    return s, np.array(K[:]), rep
+
+
+def acm_stokes_tensor(ctx, H, params=None, u3=None, grad_form=False):
+    K = (C.c_double * 9)()
+    Kg = (C.c_double * 9)() if grad_form else None
+    reps = (acm_report * 3)()
+    s = load().acm_stokes_tensor(ctx.h, _ptr(H), C.byref(params or stokes_params()), _ptr(u3), K,
+                                 Kg, reps)
+    _check(s, "acm_stokes_tensor", allow_maxiter=True)
+    return s, np.array(K[:]).reshape(3, 3), (np.array(Kg[:]).reshape(3, 3) if grad_form else None), list(reps)
+
+
+def acm_advdiff(ctx, H, u, Pe, g_chi, params=None, chi=None, grad_chi=None):
+    Dg = (C.c_double * 3)()
+    Dx = (C.c_double * 3)()
+    rep = acm_report()
+    s = load().acm_advdiff(ctx.h, _ptr(H), _ptr(u), float(Pe), _dvec(g_chi), C.byref(params or advdiff_params()),
+                           _ptr(chi), _ptr(grad_chi), Dg, Dx, C.byref(rep))
+    _check(s, "acm_advdiff", allow_maxiter=True)
+    return s, np.array(Dg[:]), np.array(Dx[:]), rep
+
+
+def acm_advdiff_tensor(ctx, H, u, Pe, params=None, chi3=None):
+    D = (C.c_double * 9)()
+    Dx = (C.c_double * 9)()
+    reps = (acm_report * 3)()
+    s = load().acm_advdiff_tensor(ctx.h, _ptr(H), _ptr(u), float(Pe), C.byref(params or advdiff_params()),
+                                  _ptr(chi3), D, Dx, reps)
+    _check(s, "acm_advdiff_tensor", allow_maxiter=True)
+    return s, np.array(D[:]).reshape(3, 3), np.array(Dx[:]).reshape(3, 3), list(reps)
+
+
+def acm_fft_r2c(ctx, x, out, fp64: bool, nbatch: int = 1):
+    _check(load().acm_fft_r2c(ctx.h, int(fp64), nbatch, _ptr(x), _ptr(out)), "acm_fft_r2c")
+
+
+def acm_fft_c2r(ctx, x, out, fp64: bool, nbatch: int = 1):
+    _check(load().acm_fft_c2r(ctx.h, int(fp64), nbatch, _ptr(x), _ptr(out)), "acm_fft_c2r")

@@ -1,0 +1,1009 @@
+// acm_api.cu -- the C ABI (include/acm.h): contexts, workspace, and the
+// device-resident iteration drivers of Algorithm 1 (Problems 1 and 2).
+//
+// Each solve runs entirely on the context's stream. The host only launches
+// kernels and, every `check_every` iterations, reads the per-problem stop flags
+// that the FP64 finalize kernel writes (no per-iteration synchronisation).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "acm.h"
+#include "acm_ops.h"
+
+using namespace acm;
+
+namespace {
+
+constexpr int BMAX = 3;          // problems solved together by one context
+constexpr int HIST_CAP = 20000;  // per-problem history records
+constexpr int NRED = 304;        // blocks of the FP64 field reductions
+
+struct Prec {
+  bool ready = false;
+  void* spec = nullptr;  // [BMAX][4][S] complex
+  void* st0 = nullptr;   // [BMAX][S] complex: q^ (Stokes) or chi^ (solute)
+  void* st1 = nullptr;   // [BMAX][S] complex: div^ of the previous iteration
+  void* u = nullptr;     // [BMAX][3][V] real
+  void* lam = nullptr;   // [BMAX][3][V] real: H lambda
+  void* aux = nullptr;   // [BMAX][4][V] real: grad chi [B][3][V], then chi [B][V]
+  void* tw = nullptr;    // [TW_MAX] complex twiddles W_1024^k
+  void* sym = nullptr;   // two symbol sets (EXACT, CENTRAL)
+};
+
+template <typename T>
+struct CxT {
+  T x, y;
+};
+
+}  // namespace
+
+struct acm_ctx {
+  int n0, n1, n2;
+  Geo g;
+  cudaStream_t st;
+  Prec pf, pd;
+  StokesDev* sprm = nullptr;
+  SoluteDev* cprm = nullptr;
+  double* part_x = nullptr;
+  double* part_z = nullptr;
+  double* part_r = nullptr;
+  int nbx = 0, nbz = 0;
+  uint8_t* Hd = nullptr;
+  unsigned long long* cnt = nullptr;
+  double* hist = nullptr;
+  int hist_kind = 0;  // 1: Stokes (16 doubles / record), 2: solute (4 doubles / record)
+  int hist_n[BMAX] = {0, 0, 0};
+  void* pin = nullptr;  // pinned host scratch
+  size_t pin_bytes = 0;
+};
+
+namespace {
+
+#define CK(x)                               \
+  do {                                      \
+    cudaError_t e_ = (x);                   \
+    if (e_ != cudaSuccess) {                \
+      cudaGetLastError();                   \
+      return ACM_ERR_CUDA;                  \
+    }                                       \
+  } while (0)
+
+#define CKS(x)                              \
+  do {                                      \
+    acm_status s_ = (x);                    \
+    if (s_ != ACM_OK) return s_;            \
+  } while (0)
+
+bool pow2_in_range(int n) { return n >= 8 && n <= 512 && (n & (n - 1)) == 0; }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+Prec& prec(acm_ctx* c);
+template <>
+Prec& prec<float>(acm_ctx* c) { return c->pf; }
+template <>
+Prec& prec<double>(acm_ctx* c) { return c->pd; }
+
+// per-axis symbols (Eq. 13 exact, Eq. 21 central); index m in FFT order
+void axis_symbols(int n, int len, int deriv, std::vector<double>& d, std::vector<double>& l) {
+  d.resize(len);
+  l.resize(len);
+  const double PI = 3.14159265358979323846;
+  for (int m = 0; m < len; ++m) {
+    const int ms = (m <= n / 2) ? m : m - n;
+    const double k = 2.0 * PI * ms;
+    if (deriv == ACM_DERIV_EXACT) {
+      d[m] = (2 * m == n) ? 0.0 : k;
+      l[m] = k * k;
+    } else {
+      d[m] = (2 * m == n || m == 0) ? 0.0 : std::sin(2.0 * PI * ms / n) * n;
+      const double s = std::sin(PI * ms / n);
+      l[m] = 4.0 * s * s * (double)n * n;
+    }
+  }
+}
+
+template <typename T>
+size_t sym_count(const Geo& g) {
+  return (size_t)2 * (g.n0 + g.n1 + g.Pu);
+}
+
+template <typename T>
+Sym<T> sym_of(acm_ctx* c, int deriv) {
+  const Geo& g = c->g;
+  const T* base = (const T*)prec<T>(c).sym + (size_t)deriv * sym_count<T>(g);
+  Sym<T> s;
+  s.d0 = base;
+  s.l0 = base + g.n0;
+  s.d1 = base + 2 * g.n0;
+  s.l1 = base + 2 * g.n0 + g.n1;
+  s.d2 = base + 2 * (g.n0 + g.n1);
+  s.l2 = base + 2 * (g.n0 + g.n1) + g.Pu;
+  return s;
+}
+
+template <typename T>
+acm_status ensure_prec(acm_ctx* c) {
+  Prec& w = prec<T>(c);
+  if (w.ready) return ACM_OK;
+  const Geo& g = c->g;
+  const size_t cs = 2 * sizeof(T);
+  auto alloc = [&](void** p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
+  if (!alloc(&w.spec, (size_t)BMAX * 4 * g.S * cs) || !alloc(&w.st0, (size_t)BMAX * g.S * cs) ||
+      !alloc(&w.st1, (size_t)BMAX * g.S * cs) || !alloc(&w.u, (size_t)BMAX * 3 * g.V * sizeof(T)) ||
+      !alloc(&w.lam, (size_t)BMAX * 3 * g.V * sizeof(T)) || !alloc(&w.aux, (size_t)BMAX * 4 * g.V * sizeof(T)) ||
+      !alloc(&w.tw, (size_t)TW_MAX * cs) || !alloc(&w.sym, 2 * sym_count<T>(g) * sizeof(T))) {
+    cudaGetLastError();
+    return ACM_ERR_NOMEM;
+  }
+  // zero the spectral padding columns once (they are never written by the passes)
+  CK(cudaMemset(w.spec, 0, (size_t)BMAX * 4 * g.S * cs));
+  CK(cudaMemset(w.st0, 0, (size_t)BMAX * g.S * cs));
+  CK(cudaMemset(w.st1, 0, (size_t)BMAX * g.S * cs));
+  std::vector<T> tw(2 * TW_MAX);
+  const double PI = 3.14159265358979323846;
+  for (int k = 0; k < TW_MAX; ++k) {
+    tw[2 * k] = (T)std::cos(2.0 * PI * k / TW_MAX);
+    tw[2 * k + 1] = (T)(-std::sin(2.0 * PI * k / TW_MAX));
+  }
+  CK(cudaMemcpy(w.tw, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice));
+  std::vector<T> sym;
+  for (int deriv = 0; deriv < 2; ++deriv) {
+    std::vector<double> d, l;
+    axis_symbols(g.n0, g.n0, deriv, d, l);
+    for (double x : d) sym.push_back((T)x);
+    for (double x : l) sym.push_back((T)x);
+    axis_symbols(g.n1, g.n1, deriv, d, l);
+    for (double x : d) sym.push_back((T)x);
+    for (double x : l) sym.push_back((T)x);
+    axis_symbols(g.n2, g.Pu, deriv, d, l);
+    for (double x : d) sym.push_back((T)x);
+    for (double x : l) sym.push_back((T)x);
+  }
+  CK(cudaMemcpy(w.sym, sym.data(), sym.size() * sizeof(T), cudaMemcpyHostToDevice));
+  w.ready = true;
+  return ACM_OK;
+}
+
+void free_prec(Prec& w) {
+  void* ps[] = {w.spec, w.st0, w.st1, w.u, w.lam, w.aux, w.tw, w.sym};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  w = Prec();
+}
+
+acm_status pin_scratch(acm_ctx* c, size_t bytes) {
+  if (c->pin_bytes >= bytes) return ACM_OK;
+  if (c->pin) cudaFreeHost(c->pin);
+  c->pin = nullptr;
+  c->pin_bytes = 0;
+  if (cudaMallocHost(&c->pin, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return ACM_ERR_NOMEM;
+  }
+  c->pin_bytes = bytes;
+  return ACM_OK;
+}
+
+// H to device memory (staged when it is a host buffer); counts solid voxels
+acm_status stage_H(acm_ctx* c, const uint8_t* H, const uint8_t** Hdev, long long* nsolid) {
+  const Geo& g = c->g;
+  if (is_device_ptr(H)) {
+    *Hdev = H;
+  } else {
+    CK(cudaMemcpyAsync(c->Hd, H, (size_t)g.V, cudaMemcpyHostToDevice, c->st));
+    *Hdev = c->Hd;
+  }
+  CK(count_solid(*Hdev, g.V, c->cnt, c->st));
+  CKS(pin_scratch(c, 1 << 20));
+  CK(cudaMemcpyAsync(c->pin, c->cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *nsolid = (long long)*(unsigned long long*)c->pin;
+  return ACM_OK;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// sum of NRED FP64 partial records (stride 8) per problem, in a fixed order
+acm_status read_partials(acm_ctx* c, int nprob, int nval, std::vector<double>& out) {
+  CKS(pin_scratch(c, (size_t)nprob * NRED * 8 * sizeof(double)));
+  CK(cudaMemcpyAsync(c->pin, c->part_r, (size_t)nprob * NRED * 8 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  const double* h = (const double*)c->pin;
+  out.assign((size_t)nprob * nval, 0.0);
+  for (int p = 0; p < nprob; ++p)
+    for (int i = 0; i < NRED; ++i)
+      for (int k = 0; k < nval; ++k) out[(size_t)p * nval + k] += h[((size_t)p * NRED + i) * 8 + k];
+  return ACM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stokes (Section 3.1, Algorithm 1 Problem 1)
+// ---------------------------------------------------------------------------
+struct StokesCfg {
+  acm_stokes_params prm;
+  double psi0[3];
+};
+
+void fill_stokes_params(const acm_stokes_params* in, acm_stokes_params* out) {
+  acm_stokes_default_params(out);
+  if (in) *out = *in;
+}
+
+double default_penalty(const Geo& g, double nu) {
+  // nu times the squared wavenumber of the geometric-mean grid spacing / 8
+  const double n = std::cbrt((double)g.n0 * g.n1 * g.n2);
+  const double PI = 3.14159265358979323846;
+  return nu * (PI * n) * (PI * n) / 8.0;
+}
+
+template <typename T>
+acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, const double (*gs)[3],
+                        const acm_stokes_params& P, double eps, const void* init_u, const void* init_lam) {
+  CKS(ensure_prec<T>(c));
+  Prec& w = prec<T>(c);
+  Geo g = c->g;
+  g.hs = hs;
+  const size_t cs = 2 * sizeof(T);
+  CK(cudaMemsetAsync(w.u, 0, (size_t)nprob * 3 * g.V * sizeof(T), c->st));
+  CK(cudaMemsetAsync(w.lam, 0, (size_t)nprob * 3 * g.V * sizeof(T), c->st));
+  CK(cudaMemsetAsync(w.st0, 0, (size_t)nprob * g.S * cs, c->st));
+  CK(cudaMemsetAsync(w.st1, 0, (size_t)nprob * g.S * cs, c->st));
+  const Sym<T> sym = sym_of<T>(c, P.deriv);
+  for (int p = 0; p < nprob; ++p) {
+    T* up = (T*)w.u + (size_t)p * 3 * g.V;
+    T* lp = (T*)w.lam + (size_t)p * 3 * g.V;
+    if (init_u) {
+      CK(cudaMemcpyAsync(up, init_u, 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
+      // div u^0 in Fourier space for the first dual residual of pair 2
+      void* sp = (char*)w.spec;
+      CK(Ops<T>::x_r2c(g, 1, 3, sp, 3 * g.S, up, 3 * g.V, w.tw, c->st));
+      CK(Ops<T>::pass(g, 1, P_FWD, 3, 1, sp, 3 * g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+      CK(Ops<T>::pass(g, 0, P_FWD, 3, 1, sp, 3 * g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+      CK(Ops<T>::div_spec(g, sp, (char*)w.st1 + (size_t)p * g.S * cs, sym, c->st));
+    }
+    if (init_lam) {
+      CK(cudaMemcpyAsync(w.aux, init_lam, 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
+      CK(Ops<T>::mask_solid(g, w.aux, lp, Hdev + (size_t)p * hs, c->st));
+    }
+  }
+  std::vector<StokesDev> hp(nprob);
+  const double p0 = default_penalty(g, P.nu);
+  for (int p = 0; p < nprob; ++p) {
+    StokesDev& d = hp[p];
+    std::memset(&d, 0, sizeof(d));
+    d.nu = P.nu;
+    d.eps = eps;
+    for (int k = 0; k < 3; ++k) {
+      d.g[k] = gs[p][k];
+      d.phi[k] = P.phi[k];
+      d.tau[k] = P.tau[k];
+    }
+    d.psi[0] = P.alpha0 > 0 ? P.alpha0 : p0;
+    d.psi[1] = P.beta0 > 0 ? P.beta0 : p0;
+    d.psi[2] = P.b0 > 0 ? P.b0 : p0;
+    for (int k = 0; k < 3; ++k) d.psi_min[k] = P.psi_min_frac * d.psi[k];
+    // u~^0 = u^0 on the solid: s_prev = b_prev / (b_prev + alpha_prev) = 1
+    d.psi_prev[0] = 0.0;
+    d.psi_prev[1] = d.psi[1];
+    d.psi_prev[2] = 1.0;
+    for (int k = 0; k < 3; ++k) d.psi_last[k] = d.psi[k];
+    d.adaptive = P.adaptive;
+    d.max_iter = P.max_iter;
+  }
+  CK(cudaMemcpyAsync(c->sprm, hp.data(), nprob * sizeof(StokesDev), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return ACM_OK;
+}
+
+// step 1 of the coming iteration (Eq. 7 / Eq. 13): w -> u^ -> u (up to the x-pass)
+template <typename T>
+acm_status stokes_step1(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, const Sym<T>& sym) {
+  Prec& w = prec<T>(c);
+  Geo g = c->g;
+  g.hs = hs;
+  const long long ps = 3 * g.S;
+  CK(Ops<T>::x_stokes_rhs(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, w.tw, c->st));
+  CK(Ops<T>::pass(g, 1, P_FWD, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, c->sprm, nullptr, nullptr, c->st));
+  CK(Ops<T>::pass(g, 0, P_STOKES, 3, nprob, w.spec, ps, sym, w.tw, w.st0, w.st1, c->sprm, nullptr, c->part_z, c->st));
+  CK(Ops<T>::pass(g, 1, P_INV, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, c->sprm, nullptr, nullptr, c->st));
+  return ACM_OK;
+}
+
+template <typename T>
+acm_status stokes_iterate(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int deriv, int check_every) {
+  Prec& w = prec<T>(c);
+  Geo g = c->g;
+  g.hs = hs;
+  const Sym<T> sym = sym_of<T>(c, deriv);
+  const int nbx = Ops<T>::x_blocks(g), nbz = Ops<T>::z_blocks(g, P_STOKES);
+  CKS(stokes_step1<T>(c, nprob, Hdev, hs, sym));
+  CKS(pin_scratch(c, BMAX * sizeof(StokesDev)));
+  if (check_every < 1) check_every = 1;
+  for (;;) {
+    for (int k = 0; k < check_every; ++k) {
+      CK(Ops<T>::x_stokes_local(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, c->part_x, w.tw, c->st));
+      CK(stokes_finalize(nprob, c->sprm, c->part_x, nbx, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
+      CKS(stokes_step1<T>(c, nprob, Hdev, hs, sym));
+    }
+    CK(cudaMemcpyAsync(c->pin, c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    const StokesDev* hp = (const StokesDev*)c->pin;
+    bool all = true;
+    for (int p = 0; p < nprob; ++p) all = all && hp[p].done;
+    if (all) break;
+  }
+  return ACM_OK;
+}
+
+// continue an FP32 solve in FP64: convert the state, re-arm the stop flags
+acm_status stokes_promote(acm_ctx* c, int nprob, double eps) {
+  CKS(ensure_prec<double>(c));
+  Prec& f = c->pf;
+  Prec& d = c->pd;
+  const Geo& g = c->g;
+  CK(convert_f2d((const float*)f.u, (double*)d.u, (long long)nprob * 3 * g.V, c->st));
+  CK(convert_f2d((const float*)f.lam, (double*)d.lam, (long long)nprob * 3 * g.V, c->st));
+  CK(convert_f2d((const float*)f.st0, (double*)d.st0, (long long)nprob * 2 * g.S, c->st));
+  CK(convert_f2d((const float*)f.st1, (double*)d.st1, (long long)nprob * 2 * g.S, c->st));
+  std::vector<StokesDev> hp(nprob);
+  CK(cudaMemcpyAsync(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (auto& x : hp) {
+    x.done = 0;
+    x.converged = 0;
+    x.status = 0;
+    x.eps = eps;
+  }
+  CK(cudaMemcpyAsync(c->sprm, hp.data(), nprob * sizeof(StokesDev), cudaMemcpyHostToDevice, c->st));
+  return ACM_OK;
+}
+
+template <typename T>
+acm_status stokes_outputs(acm_ctx* c, int nprob, void* u_out, long long u_stride, void* p_out, void* lam_out,
+                          double (*Kcol)[3]) {
+  Prec& w = prec<T>(c);
+  Geo g = c->g;
+  g.us = 3 * g.V;
+  g.hs = 0;
+  for (int p = 0; p < nprob; ++p) {
+    if (u_out)
+      CK(cudaMemcpyAsync((char*)u_out + (size_t)p * u_stride * sizeof(T), (T*)w.u + (size_t)p * 3 * g.V,
+                         3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
+    if (lam_out)
+      CK(cudaMemcpyAsync((char*)lam_out + (size_t)p * 3 * g.V * sizeof(T), (T*)w.lam + (size_t)p * 3 * g.V,
+                         3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
+  }
+  if (p_out) {
+    // p = q - mean(q): inverse transform of q^ (its k = 0 coefficient is 0)
+    const Sym<T> sym = sym_of<T>(c, 0);
+    CK(Ops<T>::pass(g, 0, P_INV_SCALE, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr,
+                    c->st));
+    CK(Ops<T>::pass(g, 1, P_INV, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+    CK(Ops<T>::x_c2r(g, nprob, 1, w.st0, g.S, w.aux, g.V, w.tw, c->st));
+    CK(cudaMemcpyAsync(p_out, w.aux, (size_t)nprob * g.V * sizeof(T), cudaMemcpyDefault, c->st));
+  }
+  if (Kcol) {
+    g.hs = 0;
+    CK(Ops<T>::field_sums(g, nprob, w.u, c->Hd, c->part_r, NRED, c->st));
+    std::vector<double> s;
+    CKS(read_partials(c, nprob, 3, s));
+    for (int p = 0; p < nprob; ++p)
+      for (int k = 0; k < 3; ++k) Kcol[p][k] = s[(size_t)p * 3 + k] / (double)g.V;
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return ACM_OK;
+}
+
+acm_status stokes_reports(acm_ctx* c, int nprob, acm_report* rep, int fp64_from, double t0) {
+  std::vector<StokesDev> hp(nprob);
+  CK(cudaMemcpyAsync(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  const double t1 = now_ms();
+  acm_status worst = ACM_OK;
+  for (int p = 0; p < nprob; ++p) {
+    const StokesDev& d = hp[p];
+    if (rep) {
+      acm_report& r = rep[p];
+      std::memset(&r, 0, sizeof(r));
+      r.iters = d.iter;
+      r.iters_fp64 = fp64_from >= 0 ? d.iter - fp64_from : (fp64_from == -2 ? d.iter : 0);
+      r.converged = d.converged;
+      r.status = d.status;
+      for (int k = 0; k < 6; ++k) {
+        r.res[k] = d.res[k];
+        r.tol[k] = d.tol[k];
+      }
+      for (int k = 0; k < 3; ++k) r.psi[k] = d.psi_last[k];
+      r.time_ms = t1 - t0;
+    }
+    if (d.status != ACM_OK && worst == ACM_OK) worst = (acm_status)d.status;
+  }
+  c->hist_kind = 1;
+  for (int p = 0; p < nprob && p < BMAX; ++p) c->hist_n[p] = hp[p].iter < HIST_CAP ? hp[p].iter : HIST_CAP;
+  return worst;
+}
+
+acm_status check_stokes_args(const acm_stokes_params& P) {
+  if (!(P.nu > 0) || !(P.eps >= 0) || P.max_iter < 1 || (P.deriv != 0 && P.deriv != 1) || P.precision < 0 ||
+      P.precision > 2 || !(P.psi_min_frac > 0) || !(P.eps32 > 0))
+    return ACM_ERR_ARG;
+  for (int k = 0; k < 3; ++k)
+    if (!(P.phi[k] >= 1.0) || !(P.tau[k] >= 1.0)) return ACM_ERR_ARG;
+  return ACM_OK;
+}
+
+// solve nprob loads on one H; u_out stride in elements between loads
+acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*gs)[3], const acm_stokes_params* prm,
+                        const void* init_u, const void* init_lam, void* u_out, long long u_stride, void* p_out,
+                        void* lam_out, double (*Kcol)[3], acm_report* rep) {
+  acm_stokes_params P;
+  fill_stokes_params(prm, &P);
+  CKS(check_stokes_args(P));
+  const double t0 = now_ms();
+  const uint8_t* Hdev = nullptr;
+  long long nsolid = 0;
+  CKS(stage_H(c, H, &Hdev, &nsolid));
+  if (nsolid == 0) return ACM_ERR_NO_SOLID;
+  if (nsolid == c->g.V) return ACM_ERR_NO_FLUID;
+  if (Hdev != c->Hd) CK(cudaMemcpyAsync(c->Hd, Hdev, (size_t)c->g.V, cudaMemcpyDeviceToDevice, c->st));
+  acm_status st = ACM_OK;
+  if (P.precision == ACM_FP32) {
+    CKS(stokes_setup<float>(c, nprob, Hdev, 0, gs, P, P.eps, init_u, init_lam));
+    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, P.deriv, P.check_every));
+    CKS(stokes_outputs<float>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
+    st = stokes_reports(c, nprob, rep, -1, t0);
+  } else if (P.precision == ACM_FP64) {
+    CKS(stokes_setup<double>(c, nprob, Hdev, 0, gs, P, P.eps, init_u, init_lam));
+    CKS(stokes_iterate<double>(c, nprob, Hdev, 0, P.deriv, P.check_every));
+    CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
+    st = stokes_reports(c, nprob, rep, -2, t0);
+  } else {
+    // FP32 iterations to eps32 (warm start given in double is cast on the host side by the caller)
+    const double e32 = P.eps < P.eps32 ? P.eps32 : P.eps;
+    if (init_u || init_lam) return ACM_ERR_ARG;  // warm starts are taken in the FP32 or FP64 modes
+    CKS(stokes_setup<float>(c, nprob, Hdev, 0, gs, P, e32, nullptr, nullptr));
+    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, P.deriv, P.check_every));
+    std::vector<StokesDev> hp(nprob);
+    CK(cudaMemcpy(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost));
+    int it32 = hp[0].iter;
+    bool ok = true;
+    for (auto& x : hp) ok = ok && x.status == ACM_OK;
+    if (ok && P.eps < e32) {
+      CKS(stokes_promote(c, nprob, P.eps));
+      CKS(stokes_iterate<double>(c, nprob, Hdev, 0, P.deriv, P.check_every));
+      CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
+      st = stokes_reports(c, nprob, rep, it32, t0);
+    } else {
+      // nothing left for FP64: report the FP32 result converted to the caller's double buffers
+      CKS(stokes_promote(c, nprob, P.eps));
+      CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
+      std::vector<StokesDev> h2 = hp;
+      CK(cudaMemcpy(c->sprm, h2.data(), nprob * sizeof(StokesDev), cudaMemcpyHostToDevice));
+      st = stokes_reports(c, nprob, rep, -1, t0);
+    }
+  }
+  return st;
+}
+
+// Eq. 2 literally: K_ij = h^3 sum over pore voxels of grad u^i : grad u^j, with the
+// spectral gradient of the solve's derivative symbol; u^i in the Stokes state.
+template <typename T>
+acm_status perm_grad(acm_ctx* c, const uint8_t* Hdev, int deriv, double Kg[9]) {
+  Prec& w = prec<T>(c);
+  const Geo& g = c->g;
+  const Sym<T> sym = sym_of<T>(c, deriv);
+  const size_t cs = 2 * sizeof(T);
+  T* f = (T*)w.aux;
+  double K[6] = {0, 0, 0, 0, 0, 0};
+  for (int l = 0; l < 3; ++l) {
+    CK(Ops<T>::x_r2c(g, 3, 1, w.st0, g.S, (T*)w.u + (size_t)l * g.V, 3 * g.V, w.tw, c->st));
+    CK(Ops<T>::pass(g, 1, P_FWD, 1, 3, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+    for (int m = 0; m < 3; ++m) {
+      CK(cudaMemcpyAsync(w.spec, w.st0, 3 * g.S * cs, cudaMemcpyDeviceToDevice, c->st));
+      CK(Ops<T>::pass(g, 0, P_DERIV, 1, 3, w.spec, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st, m));
+      CK(Ops<T>::pass(g, 1, P_INV, 1, 3, w.spec, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+      CK(Ops<T>::x_c2r(g, 3, 1, w.spec, g.S, f, g.V, w.tw, c->st));
+      CK(Ops<T>::pore_products(g, f, Hdev, c->part_r, NRED, c->st));
+      std::vector<double> s;
+      CKS(read_partials(c, 1, 6, s));
+      for (int k = 0; k < 6; ++k) K[k] += s[k];
+    }
+  }
+  const int map[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Kg[i * 3 + j] = K[map[i][j]] / (double)g.V;
+  return ACM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solute (Section 3.2, Algorithm 1 Problem 2)
+// ---------------------------------------------------------------------------
+template <typename T>
+acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us,
+                      const double (*gchi)[3], double Pe, const acm_advdiff_params& P, double eps, bool setup,
+                      const double* B0, const double* ubar) {
+  CKS(ensure_prec<T>(c));
+  Prec& w = prec<T>(c);
+  Geo g = c->g;
+  g.hs = 0;
+  g.us = us;
+  const size_t cs = 2 * sizeof(T);
+  const Sym<T> sym = sym_of<T>(c, P.deriv);
+  if (setup) {
+    CK(cudaMemsetAsync(w.st0, 0, (size_t)nprob * g.S * cs, c->st));
+    CK(cudaMemsetAsync(w.spec, 0, (size_t)nprob * 4 * g.S * cs, c->st));
+    std::vector<SoluteDev> hp(nprob);
+    for (int p = 0; p < nprob; ++p) {
+      SoluteDev& d = hp[p];
+      std::memset(&d, 0, sizeof(d));
+      d.eps = eps;
+      d.A0 = P.A0;
+      d.eta = P.eta;
+      d.Pe = Pe;
+      double ug = 0;
+      for (int k = 0; k < 3; ++k) {
+        d.B0[k] = B0[k];
+        d.g[k] = gchi[p][k];
+        d.ubar[k] = ubar[k];
+        ug += ubar[k] * gchi[p][k];
+      }
+      d.Fc = Pe * ug;
+      d.max_iter = P.max_iter;
+      d.rmin = 1e300;
+    }
+    CK(cudaMemcpyAsync(c->cprm, hp.data(), nprob * sizeof(SoluteDev), cudaMemcpyHostToDevice, c->st));
+  }
+  const int nbz = Ops<T>::z_blocks(g, P_SOLUTE);
+  const long long ps = 4 * g.S;
+  CKS(pin_scratch(c, BMAX * sizeof(SoluteDev)));
+  const int ce = P.check_every < 1 ? 1 : P.check_every;
+  for (;;) {
+    for (int k = 0; k < ce; ++k) {
+      CK(Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->cprm, w.tw, c->st));
+      CK(Ops<T>::pass(g, 1, P_FWD, 4, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm, nullptr,
+                      c->st));
+      CK(Ops<T>::pass(g, 0, P_SOLUTE, 4, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm, c->part_z,
+                      c->st));
+      CK(Ops<T>::pass(g, 1, P_INV, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm, nullptr,
+                      c->st));
+      CK(solute_finalize(nprob, c->cprm, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
+    }
+    CK(cudaMemcpyAsync(c->pin, c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    const SoluteDev* hp = (const SoluteDev*)c->pin;
+    bool all = true;
+    for (int p = 0; p < nprob; ++p) all = all && hp[p].done;
+    if (all) break;
+  }
+  return ACM_OK;
+}
+
+template <typename T>
+acm_status solute_outputs(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us, void* chi_out,
+                          void* grad_out, double (*Dg)[3], double (*Dx)[3]) {
+  Prec& w = prec<T>(c);
+  Geo g = c->g;
+  g.hs = 0;
+  g.us = us;
+  const Sym<T> sym = sym_of<T>(c, 0);
+  T* grad = (T*)w.aux;
+  T* chi = (T*)w.aux + (size_t)BMAX * 3 * g.V;
+  // grad chi^{n+1}: the last pass left i d chi^ (inverse along z and y) in components 0..2
+  CK(Ops<T>::x_c2r(g, nprob, 3, w.spec, 4 * g.S, grad, 3 * g.V, w.tw, c->st));
+  // chi^{n+1}
+  CK(Ops<T>::pass(g, 0, P_INV_SCALE, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  c->st));
+  CK(Ops<T>::pass(g, 1, P_INV, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+  CK(Ops<T>::x_c2r(g, nprob, 1, w.st0, g.S, chi, g.V, w.tw, c->st));
+  CK(Ops<T>::diffusivity(g, nprob, chi, grad, udev, Hdev, c->cprm, c->part_r, NRED, c->st));
+  std::vector<double> s;
+  CKS(read_partials(c, nprob, 6, s));
+  for (int p = 0; p < nprob; ++p)
+    for (int k = 0; k < 3; ++k) {
+      Dg[p][k] = s[(size_t)p * 6 + k] / (double)g.V;
+      if (Dx) Dx[p][k] = s[(size_t)p * 6 + 3 + k] / (double)g.V;
+    }
+  for (int p = 0; p < nprob; ++p) {
+    if (chi_out)
+      CK(cudaMemcpyAsync((T*)chi_out + (size_t)p * g.V, chi + (size_t)p * g.V, g.V * sizeof(T), cudaMemcpyDefault,
+                         c->st));
+    if (grad_out)
+      CK(cudaMemcpyAsync((T*)grad_out + (size_t)p * 3 * g.V, grad + (size_t)p * 3 * g.V, 3 * g.V * sizeof(T),
+                         cudaMemcpyDefault, c->st));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return ACM_OK;
+}
+
+acm_status solute_promote(acm_ctx* c, int nprob, double eps) {
+  CKS(ensure_prec<double>(c));
+  const Geo& g = c->g;
+  CK(convert_f2d((const float*)c->pf.st0, (double*)c->pd.st0, (long long)nprob * 2 * g.S, c->st));
+  CK(convert_f2d((const float*)c->pf.spec, (double*)c->pd.spec, (long long)nprob * 4 * 2 * g.S, c->st));
+  std::vector<SoluteDev> hp(nprob);
+  CK(cudaMemcpyAsync(hp.data(), c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (auto& x : hp) {
+    x.done = 0;
+    x.converged = 0;
+    x.status = 0;
+    x.eps = eps;
+  }
+  CK(cudaMemcpyAsync(c->cprm, hp.data(), nprob * sizeof(SoluteDev), cudaMemcpyHostToDevice, c->st));
+  return ACM_OK;
+}
+
+acm_status solute_reports(acm_ctx* c, int nprob, acm_report* rep, int it32, bool fp64_all, double t0) {
+  std::vector<SoluteDev> hp(nprob);
+  CK(cudaMemcpyAsync(hp.data(), c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  const double t1 = now_ms();
+  acm_status worst = ACM_OK;
+  for (int p = 0; p < nprob; ++p) {
+    const SoluteDev& d = hp[p];
+    if (rep) {
+      acm_report& r = rep[p];
+      std::memset(&r, 0, sizeof(r));
+      r.iters = d.iter;
+      r.iters_fp64 = fp64_all ? d.iter : (it32 >= 0 ? d.iter - it32 : 0);
+      r.converged = d.converged;
+      r.status = d.status;
+      r.res[0] = d.res[0];
+      r.res[1] = d.res[1];
+      r.tol[0] = d.tol[0];
+      r.tol[1] = d.tol[1];
+      r.time_ms = t1 - t0;
+    }
+    if (d.status != ACM_OK && worst == ACM_OK) worst = (acm_status)d.status;
+  }
+  c->hist_kind = 2;
+  for (int p = 0; p < nprob && p < BMAX; ++p) c->hist_n[p] = hp[p].iter < HIST_CAP ? hp[p].iter : HIST_CAP;
+  return worst;
+}
+
+acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u, double Pe, const double (*gchi)[3],
+                         const acm_advdiff_params* prm, void* chi_out, void* grad_out, double (*Dg)[3],
+                         double (*Dx)[3], acm_report* rep) {
+  acm_advdiff_params P;
+  acm_advdiff_default_params(&P);
+  if (prm) P = *prm;
+  if (!u || !(P.A0 > 0) || !(P.eta >= 0) || !(P.eps >= 0) || P.max_iter < 1 || (P.deriv != 0 && P.deriv != 1) ||
+      P.precision < 0 || P.precision > 2 || !std::isfinite(Pe))
+    return ACM_ERR_ARG;
+  const double t0 = now_ms();
+  const uint8_t* Hdev = nullptr;
+  long long nsolid = 0;
+  CKS(stage_H(c, H, &Hdev, &nsolid));
+  if (nsolid == c->g.V) return ACM_ERR_NO_FLUID;
+  const bool fp32 = P.precision == ACM_FP32;
+  const size_t rs = fp32 ? sizeof(float) : sizeof(double);
+  const Geo& g0 = c->g;
+  // the advecting velocity in device memory of the working precision
+  const void* ud = u;
+  if (fp32) {
+    CKS(ensure_prec<float>(c));
+    if (!is_device_ptr(u)) {
+      CK(cudaMemcpyAsync(c->pf.u, u, 3 * g0.V * rs, cudaMemcpyHostToDevice, c->st));
+      ud = c->pf.u;
+    }
+  } else {
+    CKS(ensure_prec<double>(c));
+    if (!is_device_ptr(u)) {
+      CK(cudaMemcpyAsync(c->pd.u, u, 3 * g0.V * rs, cudaMemcpyHostToDevice, c->st));
+      ud = c->pd.u;
+    }
+  }
+  // pore average of u (definition below Eq. 1) and the default comparison medium B0
+  Geo g = g0;
+  g.us = 0;
+  g.hs = 0;
+  std::vector<double> s;
+  if (fp32) CK(Ops<float>::field_sums(g, 1, ud, Hdev, c->part_r, NRED, c->st));
+  else CK(Ops<double>::field_sums(g, 1, ud, Hdev, c->part_r, NRED, c->st));
+  {
+    CKS(pin_scratch(c, (size_t)NRED * 8 * sizeof(double)));
+    CK(cudaMemcpyAsync(c->pin, c->part_r, (size_t)NRED * 8 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    const double* h = (const double*)c->pin;
+    s.assign(7, 0.0);
+    for (int i = 0; i < NRED; ++i)
+      for (int k = 0; k < 7; ++k) s[k] += h[(size_t)i * 8 + k];
+  }
+  const double npore = s[6];
+  double ubar[3], B0[3];
+  for (int k = 0; k < 3; ++k) {
+    ubar[k] = s[3 + k] / npore;
+    B0[k] = P.B0_explicit ? P.B0[k] : Pe * s[3 + k] / (double)g.V;
+  }
+  acm_status st = ACM_OK;
+  if (P.precision == ACM_FP32) {
+    CKS(solute_run<float>(c, nprob, Hdev, ud, 0, gchi, Pe, P, P.eps, true, B0, ubar));
+    CKS(solute_outputs<float>(c, nprob, Hdev, ud, 0, chi_out, grad_out, Dg, Dx));
+    st = solute_reports(c, nprob, rep, -1, false, t0);
+  } else if (P.precision == ACM_FP64) {
+    CKS(solute_run<double>(c, nprob, Hdev, ud, 0, gchi, Pe, P, P.eps, true, B0, ubar));
+    CKS(solute_outputs<double>(c, nprob, Hdev, ud, 0, chi_out, grad_out, Dg, Dx));
+    st = solute_reports(c, nprob, rep, -1, true, t0);
+  } else {
+    // FP32 phase needs the velocity in FP32
+    CKS(ensure_prec<float>(c));
+    CK(convert_d2f((const double*)ud, (float*)c->pf.u, 3 * g.V, c->st));
+    const double e32 = P.eps < 1e-5 ? 1e-5 : P.eps;
+    CKS(solute_run<float>(c, nprob, Hdev, c->pf.u, 0, gchi, Pe, P, e32, true, B0, ubar));
+    std::vector<SoluteDev> hp(nprob);
+    CK(cudaMemcpy(hp.data(), c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost));
+    const int it32 = hp[0].iter;
+    bool ok = true;
+    for (auto& x : hp) ok = ok && x.status == ACM_OK;
+    CKS(solute_promote(c, nprob, P.eps));
+    if (ok && P.eps < e32) CKS(solute_run<double>(c, nprob, Hdev, ud, 0, gchi, Pe, P, P.eps, false, B0, ubar));
+    else CK(cudaMemcpy(c->cprm, hp.data(), nprob * sizeof(SoluteDev), cudaMemcpyHostToDevice));
+    CKS(solute_outputs<double>(c, nprob, Hdev, ud, 0, chi_out, grad_out, Dg, Dx));
+    st = solute_reports(c, nprob, rep, it32, false, t0);
+  }
+  return st;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+acm_status acm_stokes_default_params(acm_stokes_params* p) {
+  if (!p) return ACM_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->nu = 1.0;
+  p->eps = 1e-5;
+  p->alpha0 = p->beta0 = p->b0 = 0.0;
+  for (int k = 0; k < 3; ++k) p->phi[k] = 1.1;
+  p->tau[0] = 5.0;
+  p->tau[1] = 10.0;
+  p->tau[2] = 5.0;
+  p->psi_min_frac = 1e-3;
+  p->eps32 = 1e-5;
+  p->max_iter = 20000;
+  p->adaptive = 1;
+  p->deriv = ACM_DERIV_EXACT;
+  p->precision = ACM_FP32;
+  p->check_every = 16;
+  return ACM_OK;
+}
+
+acm_status acm_advdiff_default_params(acm_advdiff_params* p) {
+  if (!p) return ACM_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->eta = 0.01;
+  p->A0 = 0.55;
+  p->B0_explicit = 0;
+  p->eps = 1e-5;
+  p->max_iter = 20000;
+  p->deriv = ACM_DERIV_CENTRAL;
+  p->precision = ACM_FP32;
+  p->check_every = 16;
+  return ACM_OK;
+}
+
+acm_status acm_create(acm_ctx** out, int n0, int n1, int n2, void* stream) {
+  if (!out) return ACM_ERR_ARG;
+  *out = nullptr;
+  if (!pow2_in_range(n0) || !pow2_in_range(n1) || !pow2_in_range(n2)) return ACM_ERR_UNSUPPORTED_SIZE;
+  acm_ctx* c = new (std::nothrow) acm_ctx();
+  if (!c) return ACM_ERR_NOMEM;
+  c->n0 = n0;
+  c->n1 = n1;
+  c->n2 = n2;
+  Geo& g = c->g;
+  g.n0 = n0;
+  g.n1 = n1;
+  g.n2 = n2;
+  g.Pu = n2 / 2 + 1;
+  g.P = n2 / 2 + 4;  // rows start on 32-byte sectors for both precisions
+  g.V = (long long)n0 * n1 * n2;
+  g.S = (long long)n0 * n1 * g.P;
+  g.hs = 0;
+  g.us = 3 * g.V;
+  c->st = (cudaStream_t)stream;
+  const int nbx = Ops<float>::x_blocks(g);
+  const int nbz = std::max(std::max(Ops<float>::z_blocks(g, P_STOKES), Ops<float>::z_blocks(g, P_SOLUTE)),
+                           std::max(Ops<double>::z_blocks(g, P_STOKES), Ops<double>::z_blocks(g, P_SOLUTE)));
+  c->nbx = nbx;
+  c->nbz = nbz;
+  bool ok = cudaMalloc(&c->sprm, BMAX * sizeof(StokesDev)) == cudaSuccess &&
+            cudaMalloc(&c->cprm, BMAX * sizeof(SoluteDev)) == cudaSuccess &&
+            cudaMalloc(&c->part_x, (size_t)BMAX * nbx * 8 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->part_z, (size_t)BMAX * nbz * 4 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->part_r, (size_t)BMAX * NRED * 8 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->Hd, (size_t)g.V) == cudaSuccess &&
+            cudaMalloc(&c->cnt, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&c->hist, (size_t)BMAX * HIST_CAP * 16 * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    acm_destroy(c);
+    return ACM_ERR_NOMEM;
+  }
+  if (cudaMemset(c->sprm, 0, BMAX * sizeof(StokesDev)) != cudaSuccess ||
+      cudaMemset(c->cprm, 0, BMAX * sizeof(SoluteDev)) != cudaSuccess) {
+    cudaGetLastError();
+    acm_destroy(c);
+    return ACM_ERR_CUDA;
+  }
+  *out = c;
+  return ACM_OK;
+}
+
+acm_status acm_destroy(acm_ctx* c) {
+  if (!c) return ACM_ERR_ARG;
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  free_prec(c->pf);
+  free_prec(c->pd);
+  void* ps[] = {c->sprm, c->cprm, c->part_x, c->part_z, c->part_r, c->Hd, c->cnt, c->hist};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  if (c->pin) cudaFreeHost(c->pin);
+  cudaGetLastError();
+  delete c;
+  return ACM_OK;
+}
+
+acm_status acm_stokes(acm_ctx* c, const uint8_t* H, const double g[3], const acm_stokes_params* prm,
+                      const void* init_u, const void* init_lambda, void* u, void* p, void* lambda, double K_col[3],
+                      acm_report* rep) {
+  if (!c || !H || !g || !u) return ACM_ERR_ARG;
+  double gs[1][3] = {{g[0], g[1], g[2]}};
+  double K[1][3];
+  acm_status s = stokes_solve(c, 1, H, gs, prm, init_u, init_lambda, u, 3 * c->g.V, p, lambda, K_col ? K : nullptr,
+                              rep);
+  if ((s == ACM_OK || s == ACM_ERR_MAXITER) && K_col)
+    for (int k = 0; k < 3; ++k) K_col[k] = K[0][k];
+  return s;
+}
+
+acm_status acm_stokes_tensor(acm_ctx* c, const uint8_t* H, const acm_stokes_params* prm, void* u3, double K[9],
+                             double K_grad[9], acm_report rep[3]) {
+  if (!c || !H || !K) return ACM_ERR_ARG;
+  double gs[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  double Kc[3][3];
+  acm_status s = stokes_solve(c, 3, H, gs, prm, nullptr, nullptr, u3, 3 * c->g.V, nullptr, nullptr, Kc, rep);
+  if (s == ACM_OK || s == ACM_ERR_MAXITER) {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) K[i * 3 + j] = Kc[j][i];
+    if (K_grad) {
+      acm_stokes_params P;
+      fill_stokes_params(prm, &P);
+      acm_status s2 = P.precision == ACM_FP32 ? perm_grad<float>(c, c->Hd, P.deriv, K_grad)
+                                              : perm_grad<double>(c, c->Hd, P.deriv, K_grad);
+      if (s2 != ACM_OK) return s2;
+    }
+  }
+  return s;
+}
+
+acm_status acm_advdiff(acm_ctx* c, const uint8_t* H, const void* u, double Pe, const double g_chi[3],
+                       const acm_advdiff_params* prm, void* chi, void* grad_chi, double Dg[3], double Dg_ext[3],
+                       acm_report* rep) {
+  if (!c || !H || !u || !g_chi || !Dg) return ACM_ERR_ARG;
+  double gs[1][3] = {{g_chi[0], g_chi[1], g_chi[2]}};
+  double D[1][3], Dx[1][3];
+  acm_status s = advdiff_solve(c, 1, H, u, Pe, gs, prm, chi, grad_chi, D, Dx, rep);
+  if (s == ACM_OK || s == ACM_ERR_MAXITER)
+    for (int k = 0; k < 3; ++k) {
+      Dg[k] = D[0][k];
+      if (Dg_ext) Dg_ext[k] = Dx[0][k];
+    }
+  return s;
+}
+
+acm_status acm_advdiff_tensor(acm_ctx* c, const uint8_t* H, const void* u, double Pe, const acm_advdiff_params* prm,
+                              void* chi3, double D[9], double D_ext[9], acm_report rep[3]) {
+  if (!c || !H || !u || !D) return ACM_ERR_ARG;
+  double gs[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  double Dc[3][3], Dx[3][3];
+  acm_status s = advdiff_solve(c, 3, H, u, Pe, gs, prm, chi3, nullptr, Dc, Dx, rep);
+  if (s == ACM_OK || s == ACM_ERR_MAXITER)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        D[i * 3 + j] = Dc[j][i];
+        if (D_ext) D_ext[i * 3 + j] = Dx[j][i];
+      }
+  return s;
+}
+
+static acm_status fft_impl(acm_ctx* c, int fp64, int nbatch, const void* in, void* out, bool forward) {
+  if (!c || !in || !out || nbatch < 1 || (fp64 != 0 && fp64 != 1)) return ACM_ERR_ARG;
+  const Geo& g = c->g;
+  const size_t rs = fp64 ? sizeof(double) : sizeof(float);
+  const size_t cs = 2 * rs;
+  if (fp64) CKS(ensure_prec<double>(c));
+  else CKS(ensure_prec<float>(c));
+  Prec& w = fp64 ? c->pd : c->pf;
+  for (int b = 0; b < nbatch; ++b) {
+    if (forward) {
+      const void* src = (const char*)in + (size_t)b * g.V * rs;
+      if (!is_device_ptr(in)) {
+        CK(cudaMemcpyAsync(w.aux, src, g.V * rs, cudaMemcpyHostToDevice, c->st));
+        src = w.aux;
+      }
+      if (fp64) {
+        const Sym<double> sym = sym_of<double>(c, 0);
+        CK(Ops<double>::x_r2c(g, 1, 1, w.st0, g.S, src, g.V, w.tw, c->st));
+        CK(Ops<double>::pass(g, 1, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        CK(Ops<double>::pass(g, 0, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+      } else {
+        const Sym<float> sym = sym_of<float>(c, 0);
+        CK(Ops<float>::x_r2c(g, 1, 1, w.st0, g.S, src, g.V, w.tw, c->st));
+        CK(Ops<float>::pass(g, 1, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        CK(Ops<float>::pass(g, 0, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+      }
+      CK(cudaMemcpy2DAsync((char*)out + (size_t)b * g.n0 * g.n1 * g.Pu * cs, g.Pu * cs, w.st0, g.P * cs, g.Pu * cs,
+                           (size_t)g.n0 * g.n1, cudaMemcpyDefault, c->st));
+    } else {
+      CK(cudaMemcpy2DAsync(w.st0, g.P * cs, (const char*)in + (size_t)b * g.n0 * g.n1 * g.Pu * cs, g.Pu * cs,
+                           g.Pu * cs, (size_t)g.n0 * g.n1, cudaMemcpyDefault, c->st));
+      void* dst = (char*)out + (size_t)b * g.V * rs;
+      const bool dev = is_device_ptr(out);
+      void* tgt = dev ? dst : w.aux;
+      if (fp64) {
+        const Sym<double> sym = sym_of<double>(c, 0);
+        CK(Ops<double>::pass(g, 0, P_INV_SCALE, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        CK(Ops<double>::pass(g, 1, P_INV, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        CK(Ops<double>::x_c2r(g, 1, 1, w.st0, g.S, tgt, g.V, w.tw, c->st));
+      } else {
+        const Sym<float> sym = sym_of<float>(c, 0);
+        CK(Ops<float>::pass(g, 0, P_INV_SCALE, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        CK(Ops<float>::pass(g, 1, P_INV, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        CK(Ops<float>::x_c2r(g, 1, 1, w.st0, g.S, tgt, g.V, w.tw, c->st));
+      }
+      if (!dev) CK(cudaMemcpyAsync(dst, w.aux, g.V * rs, cudaMemcpyDeviceToHost, c->st));
+    }
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return ACM_OK;
+}
+
+acm_status acm_fft_r2c(acm_ctx* c, int fp64, int nbatch, const void* in, void* out) {
+  return fft_impl(c, fp64, nbatch, in, out, true);
+}
+
+acm_status acm_fft_c2r(acm_ctx* c, int fp64, int nbatch, const void* in, void* out) {
+  return fft_impl(c, fp64, nbatch, in, out, false);
+}
+
+const char* acm_status_str(acm_status s) {
+  switch (s) {
+    case ACM_OK: return "ok";
+    case ACM_ERR_ARG: return "invalid argument";
+    case ACM_ERR_NOMEM: return "device allocation failed";
+    case ACM_ERR_CUDA: return "CUDA runtime error";
+    case ACM_ERR_MAXITER: return "iteration cap reached before the tolerance";
+    case ACM_ERR_DIVERGED: return "iteration diverged";
+    case ACM_ERR_NONFINITE: return "non-finite residual";
+    case ACM_ERR_NO_SOLID: return "indicator has no solid voxel";
+    case ACM_ERR_NO_FLUID: return "indicator has no pore voxel";
+    case ACM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case ACM_ERR_UNSUPPORTED_SIZE: return "unsupported grid size";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,3 @@
+// FP32 instantiation of the ACM launch wrappers.
+#include "acm_ops_impl.cuh"
+template struct acm::Ops<float>;

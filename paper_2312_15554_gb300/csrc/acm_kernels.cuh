@@ -1,0 +1,657 @@
+// acm_kernels.cuh -- the ACM hot path as fused FFT-pass kernels (sm_103a).
+//
+// One Stokes ADMM iteration (Section 3.1) is five pass kernels plus a tiny
+// FP64 finalize kernel:
+//   x_stokes_local   C2R along x of u^{n+1}, steps 2-3 (Eq. 8-9) pointwise,
+//                    partial sums of the Eq. 10 residuals
+//   stokes_finalize  residuals, tolerances (Eq. 11-12), stop test, Eq. 22
+//   x_stokes_rhs     w = b u~ - a (the known part of Eq. 7), R2C along x
+//   strided<FWD>     forward FFT along y
+//   strided<STOKES>  forward FFT along z, Eq. 13 solve per wavevector, q update
+//                    of Eq. 9 in Fourier space, divergence residuals by
+//                    Parseval, inverse FFT along z
+//   strided<INV>     inverse FFT along y
+// One solute iteration (Section 3.2) is x_solute (C2R of grad chi, local
+// residual terms of Eq. 18, R2C), strided<FWD>, strided<SOLUTE> (Eq. 20 with
+// the Eq. 21 symbols, Eq. 19 residuals by Parseval), strided<INV> and
+// solute_finalize.
+//
+// The ADMM state is reduced by an identity of steps 2-3: with a^0 = H lambda^0,
+// step 3 gives a^{n+1} = H lambda^{n+1} after every iteration, so a is never
+// stored, u~ = u on pore voxels and u~ = b u / (b + alpha) on solid voxels.
+// The multiplier q only enters through its gradient and is kept in Fourier space.
+#pragma once
+#include "acm_fft.cuh"
+#include "acm_types.h"
+
+namespace acm {
+
+// dynamic shared memory of an x-pass kernel with NC component lines per line
+template <typename T, int N2, int NC>
+constexpr int x_smem_bytes() {
+  return (NC * (64 / ((N2 / 2) / ept(N2 / 2))) * line_stride(N2 / 2) + N2) * (int)sizeof(cx<T>);
+}
+
+// ---------------------------------------------------------------------------
+// x-pass configuration (real lines of length N2, complex FFT of length M = N2/2)
+// ---------------------------------------------------------------------------
+template <int N2>
+struct XCfg {
+  static constexpr int M = N2 / 2;
+  static constexpr int E = ept(M);
+  static constexpr int TL = M / E;          // threads per line transform
+  static constexpr int LPB = 64 / TL;       // lines per block
+  static constexpr int LS = line_stride(M); // complex slots per component line
+};
+
+template <typename T>
+__device__ __forceinline__ T& re_at(cx<T>* line, int n) {
+  return reinterpret_cast<T*>(&line[pad(n >> 1)])[n & 1];
+}
+
+// load TW table W_{N}^k, k < N, from the master table
+template <typename T, int N>
+__device__ __forceinline__ void load_tw(cx<T>* tw, const cx<T>* __restrict__ twg) {
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = twg[k * (TW_MAX / N)];
+}
+
+// rows of NC components for LPB lines from the half spectrum into shared memory
+template <typename T, int N2, int NC>
+__device__ __forceinline__ void x_load_spec(cx<T>* sm, const cx<T>* __restrict__ spec, long long S, int P,
+                                            int line0) {
+  using C = XCfg<N2>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
+    const int c = cl / C::LPB, l = cl - c * C::LPB;
+    const cx<T>* src = spec + c * S + (long long)(line0 + l) * P;
+    cx<T>* dst = sm + cl * C::LS;
+    for (int k = lane; k <= C::M; k += 32) dst[pad(k)] = src[k];
+  }
+}
+
+template <typename T, int N2, int NC>
+__device__ __forceinline__ void x_store_spec(const cx<T>* sm, cx<T>* __restrict__ spec, long long S, int P,
+                                             int line0) {
+  using C = XCfg<N2>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
+    const int c = cl / C::LPB, l = cl - c * C::LPB;
+    cx<T>* dst = spec + c * S + (long long)(line0 + l) * P;
+    const cx<T>* src = sm + cl * C::LS;
+    for (int k = lane; k <= C::M; k += 32) dst[k] = src[pad(k)];
+  }
+}
+
+// Half spectrum X[0..M] of a real line of length N2 -> Z[0..M-1] whose inverse
+// complex FFT of length M is z_j = N2 * (x_{2j} + i x_{2j+1}).
+template <typename T, int N2, int NC>
+__device__ __forceinline__ void x_c2r_pre(cx<T>* sm, const cx<T>* tw) {
+  using C = XCfg<N2>;
+  constexpr int M = C::M;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
+    cx<T>* s = sm + cl * C::LS;
+    for (int k = lane; k <= M / 2; k += 32) {
+      const cx<T> X = s[pad(k)], Y = s[pad(M - k)];
+      const cx<T> e1 = X + cconj(Y), o1 = cmul(X - cconj(Y), cconj(tw[k]));
+      const cx<T> e2 = Y + cconj(X), o2 = cmul(Y - cconj(X), cconj(tw[M - k]));
+      s[pad(k)] = e1 + mul_i(o1);
+      if (k != 0) s[pad(M - k)] = e2 + mul_i(o2);
+    }
+  }
+}
+
+// Z[0..M-1] = forward FFT of z_j = x_{2j} + i x_{2j+1} -> half spectrum X[0..M].
+template <typename T, int N2, int NC>
+__device__ __forceinline__ void x_r2c_post(cx<T>* sm, const cx<T>* tw) {
+  using C = XCfg<N2>;
+  constexpr int M = C::M;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T half = (T)0.5;
+  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
+    cx<T>* s = sm + cl * C::LS;
+    for (int k = lane; k <= M / 2; k += 32) {
+      const cx<T> Zk = s[pad(k)];
+      if (k == 0) {
+        s[pad(0)] = mk<T>(Zk.x + Zk.y, (T)0);
+        s[pad(M)] = mk<T>(Zk.x - Zk.y, (T)0);
+      } else {
+        const cx<T> Zm = s[pad(M - k)];
+        const cx<T> ak = cscale(Zk + cconj(Zm), half), bk = cscale(Zk - cconj(Zm), half);
+        const cx<T> am = cscale(Zm + cconj(Zk), half), bm = cscale(Zm - cconj(Zk), half);
+        // X_k = a_k - i W^k b_k
+        s[pad(k)] = ak - mul_i(cmul(tw[k], bk));
+        s[pad(M - k)] = am - mul_i(cmul(tw[M - k], bm));
+      }
+    }
+  }
+}
+
+// complex FFT of length M on NC * LPB component lines, TL threads per line
+template <typename T, int N2, int NC, int SIGN>
+__device__ __forceinline__ void x_fft(cx<T>* sm, const cx<T>* tw) {
+  using C = XCfg<N2>;
+  const int job = threadIdx.x / C::TL;
+  const unsigned mask = __ballot_sync(0xffffffffu, job < NC * C::LPB);
+  if (job < NC * C::LPB) fft_line<T, C::M, SIGN, 2>(sm + job * C::LS, threadIdx.x % C::TL, tw, mask);
+}
+
+// ---------------------------------------------------------------------------
+// Stokes x-pass 1: C2R of u^{n+1}, steps 2-3 of ADMM, residual partial sums
+// ---------------------------------------------------------------------------
+template <typename T, int N2>
+__global__ void __launch_bounds__(3 * 64) k_x_stokes_local(const cx<T>* __restrict__ spec, T* __restrict__ u,
+                                                          T* __restrict__ lam, const uint8_t* __restrict__ H,
+                                                          StokesDev* __restrict__ prm, double* __restrict__ part,
+                                                          Geo g, const cx<T>* __restrict__ twg) {
+  using C = XCfg<N2>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = sm + 3 * C::LPB * C::LS;
+  __shared__ double red[5 * 32];
+  const int p = blockIdx.y;
+  StokesDev* P = prm + p;
+  if (P->done) return;
+  const T alpha = (T)P->psi[0], b = (T)P->psi[2];
+  // u~^n on solid voxels = s_prev u^n (s_prev = 1 before the first iteration)
+  const T s_prev = (T)(P->psi_prev[2] / (P->psi_prev[2] + P->psi_prev[0]));
+  const T s_now = b / (b + alpha);
+  const int line0 = blockIdx.x * C::LPB;
+  const cx<T>* sp = spec + (long long)p * 3 * g.S;
+  T* up = u + (long long)p * 3 * g.V;
+  T* lp = lam + (long long)p * 3 * g.V;
+  const uint8_t* Hp = H + (long long)p * g.hs;
+  load_tw<T, N2>(tw, twg);
+  x_load_spec<T, N2, 3>(sm, sp, g.S, g.P, line0);
+  __syncthreads();
+  x_c2r_pre<T, N2, 3>(sm, tw);
+  __syncthreads();
+  x_fft<T, N2, 3, +1>(sm, tw);
+  __syncthreads();
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+  for (int idx = threadIdx.x; idx < C::LPB * N2; idx += blockDim.x) {
+    const int l = idx / N2, n = idx & (N2 - 1);
+    const long long v = (long long)(line0 + l) * N2 + n;
+    const bool solid = Hp[v] != 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T u1 = re_at(sm + (c * C::LPB + l) * C::LS, n);
+      const T u0 = up[c * g.V + v];
+      up[c * g.V + v] = u1;
+      const T du = u1 - u0;
+      a3 += du * du;
+      if (solid) {
+        const T ut1 = s_now * u1;            // step 2 (Eq. 8) with a^n = H lambda^n
+        const T ut0 = s_prev * u0;
+        const T l1 = lp[c * g.V + v] + alpha * ut1;  // step 3 (Eq. 9)
+        lp[c * g.V + v] = l1;
+        const T dut = ut1 - ut0, dd = u1 - ut1;
+        a0 += ut1 * ut1;
+        a1 += dut * dut;
+        a2 += dd * dd;
+        a4 += l1 * l1;
+      }
+    }
+  }
+  double v5[5] = {(double)a0, (double)a1, (double)a2, (double)a3, (double)a4};
+  block_sum_store<5>(v5, red, part + ((long long)p * gridDim.x + blockIdx.x) * 8);
+}
+
+// ---------------------------------------------------------------------------
+// Stokes x-pass 2: w = b u~ - a (Eq. 7 right-hand side), R2C along x
+// ---------------------------------------------------------------------------
+template <typename T, int N2>
+__global__ void __launch_bounds__(3 * 64) k_x_stokes_rhs(cx<T>* __restrict__ spec, const T* __restrict__ u,
+                                                        const T* __restrict__ lam, const uint8_t* __restrict__ H,
+                                                        const StokesDev* __restrict__ prm, Geo g,
+                                                        const cx<T>* __restrict__ twg) {
+  using C = XCfg<N2>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = sm + 3 * C::LPB * C::LS;
+  const int p = blockIdx.y;
+  const StokesDev* P = prm + p;
+  if (P->done) return;
+  const T b = (T)P->psi[2];
+  const T s_prev = (T)(P->psi_prev[2] / (P->psi_prev[2] + P->psi_prev[0]));
+  const int line0 = blockIdx.x * C::LPB;
+  cx<T>* sp = spec + (long long)p * 3 * g.S;
+  const T* up = u + (long long)p * 3 * g.V;
+  const T* lp = lam + (long long)p * 3 * g.V;
+  const uint8_t* Hp = H + (long long)p * g.hs;
+  load_tw<T, N2>(tw, twg);
+  for (int idx = threadIdx.x; idx < C::LPB * N2; idx += blockDim.x) {
+    const int l = idx / N2, n = idx & (N2 - 1);
+    const long long v = (long long)(line0 + l) * N2 + n;
+    const bool solid = Hp[v] != 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T uu = up[c * g.V + v];
+      const T w = solid ? b * (s_prev * uu) - lp[c * g.V + v] : b * uu;
+      re_at(sm + (c * C::LPB + l) * C::LS, n) = w;
+    }
+  }
+  __syncthreads();
+  x_fft<T, N2, 3, -1>(sm, tw);
+  __syncthreads();
+  x_r2c_post<T, N2, 3>(sm, tw);
+  __syncthreads();
+  x_store_spec<T, N2, 3>(sm, sp, g.S, g.P, line0);
+}
+
+// ---------------------------------------------------------------------------
+// Solute x-pass: C2R of grad chi^n (3 components), local terms of Eq. 18:
+//   tau = (A - A0)(grad chi + g),  s = F - (B - B0).(grad chi + g),
+//   A = (1 - H) + eta H,  B = Pe (1 - H) u,  F = Pe (1 - H) ubar.g,
+// then R2C of (tau_0, tau_1, tau_2, s).
+// ---------------------------------------------------------------------------
+template <typename T, int N2>
+__global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, const T* __restrict__ u,
+                                                    const uint8_t* __restrict__ H,
+                                                    const SoluteDev* __restrict__ prm, Geo g,
+                                                    const cx<T>* __restrict__ twg) {
+  using C = XCfg<N2>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = sm + 4 * C::LPB * C::LS;
+  const int p = blockIdx.y;
+  const SoluteDev* P = prm + p;
+  if (P->done) return;
+  const T A0 = (T)P->A0, eta = (T)P->eta, Pe = (T)P->Pe, Fc = (T)P->Fc;
+  const T g0 = (T)P->g[0], g1 = (T)P->g[1], g2 = (T)P->g[2];
+  const T B00 = (T)P->B0[0], B01 = (T)P->B0[1], B02 = (T)P->B0[2];
+  const int line0 = blockIdx.x * C::LPB;
+  cx<T>* sp = spec + (long long)p * 4 * g.S;
+  const T* up = u + (long long)p * g.us;
+  const uint8_t* Hp = H + (long long)p * g.hs;
+  load_tw<T, N2>(tw, twg);
+  x_load_spec<T, N2, 3>(sm, sp, g.S, g.P, line0);
+  __syncthreads();
+  x_c2r_pre<T, N2, 3>(sm, tw);
+  __syncthreads();
+  x_fft<T, N2, 3, +1>(sm, tw);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < C::LPB * N2; idx += blockDim.x) {
+    const int l = idx / N2, n = idx & (N2 - 1);
+    const long long v = (long long)(line0 + l) * N2 + n;
+    const bool solid = Hp[v] != 0;
+    T& r0 = re_at(sm + (0 * C::LPB + l) * C::LS, n);
+    T& r1 = re_at(sm + (1 * C::LPB + l) * C::LS, n);
+    T& r2 = re_at(sm + (2 * C::LPB + l) * C::LS, n);
+    const T e0 = r0 + g0, e1 = r1 + g1, e2 = r2 + g2;
+    const T Am = (solid ? eta : (T)1) - A0;
+    T s = B00 * e0 + B01 * e1 + B02 * e2;
+    if (!solid) s += Fc - Pe * (up[v] * e0 + up[g.V + v] * e1 + up[2 * g.V + v] * e2);
+    r0 = Am * e0;
+    r1 = Am * e1;
+    r2 = Am * e2;
+    re_at(sm + (3 * C::LPB + l) * C::LS, n) = s;
+  }
+  __syncthreads();
+  x_fft<T, N2, 4, -1>(sm, tw);
+  __syncthreads();
+  x_r2c_post<T, N2, 4>(sm, tw);
+  __syncthreads();
+  x_store_spec<T, N2, 4>(sm, sp, g.S, g.P, line0);
+}
+
+// ---------------------------------------------------------------------------
+// plain x-passes (transforms of NC real components)
+// ---------------------------------------------------------------------------
+template <typename T, int N2, int NC>
+__global__ void __launch_bounds__(NC * 64) k_x_r2c(cx<T>* __restrict__ spec, const T* __restrict__ in, Geo g,
+                                                  long long inProbStride, long long specProbStride,
+                                                  const cx<T>* __restrict__ twg) {
+  using C = XCfg<N2>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = sm + NC * C::LPB * C::LS;
+  const int p = blockIdx.y;
+  const int line0 = blockIdx.x * C::LPB;
+  const T* ip = in + p * inProbStride;
+  load_tw<T, N2>(tw, twg);
+  for (int idx = threadIdx.x; idx < NC * C::LPB * N2; idx += blockDim.x) {
+    const int n = idx & (N2 - 1), cl = idx / N2;
+    const int c = cl / C::LPB, l = cl - c * C::LPB;
+    re_at(sm + cl * C::LS, n) = ip[c * g.V + (long long)(line0 + l) * N2 + n];
+  }
+  __syncthreads();
+  x_fft<T, N2, NC, -1>(sm, tw);
+  __syncthreads();
+  x_r2c_post<T, N2, NC>(sm, tw);
+  __syncthreads();
+  x_store_spec<T, N2, NC>(sm, spec + p * specProbStride, g.S, g.P, line0);
+}
+
+template <typename T, int N2, int NC>
+__global__ void __launch_bounds__(NC * 64) k_x_c2r(const cx<T>* __restrict__ spec, T* __restrict__ out, Geo g,
+                                                  long long outProbStride, long long specProbStride,
+                                                  const cx<T>* __restrict__ twg) {
+  using C = XCfg<N2>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = sm + NC * C::LPB * C::LS;
+  const int p = blockIdx.y;
+  const int line0 = blockIdx.x * C::LPB;
+  T* op = out + p * outProbStride;
+  load_tw<T, N2>(tw, twg);
+  x_load_spec<T, N2, NC>(sm, spec + p * specProbStride, g.S, g.P, line0);
+  __syncthreads();
+  x_c2r_pre<T, N2, NC>(sm, tw);
+  __syncthreads();
+  x_fft<T, N2, NC, +1>(sm, tw);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NC * C::LPB * N2; idx += blockDim.x) {
+    const int n = idx & (N2 - 1), cl = idx / N2;
+    const int c = cl / C::LPB, l = cl - c * C::LPB;
+    op[c * g.V + (long long)(line0 + l) * N2 + n] = re_at(sm + cl * C::LS, n);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// strided passes: complex FFTs along y or z on tiles of TX consecutive kx
+// columns, with an optional per-wavevector operator between a forward and an
+// inverse transform (z-pass only).
+// ---------------------------------------------------------------------------
+enum { OP_FWD = 0, OP_INV = 1, OP_INV_SCALE = 2, OP_STOKES = 3, OP_SOLUTE = 4, OP_DERIV = 5 };
+
+template <typename T>
+struct PassArgs {
+  cx<T>* spec;
+  long long probStride, compStride, rowStride, outerStride;
+  int Pu;           // used kx columns
+  int n1;           // for wavevector indexing in the z-pass
+  Sym<T> sym;
+  const cx<T>* twg;
+  // operator state
+  cx<T>* st0;       // Stokes: q^ ; solute: chi^
+  cx<T>* st1;       // Stokes: div^ of the previous iteration
+  StokesDev* sprm;
+  SoluteDev* cprm;
+  double* part;     // per-block partial sums (stride 4 doubles)
+  double invV;
+  int nkx;          // n2 / 2 (Nyquist column index)
+  int dm;           // OP_DERIV: axis of the derivative
+};
+
+template <int OP>
+struct OpComps {
+  static constexpr int IN = (OP == OP_SOLUTE) ? 4 : (OP == OP_STOKES ? 3 : 1);
+  static constexpr int OUT = (OP == OP_SOLUTE) ? 3 : IN;
+};
+
+template <typename T, int N, int OP, int NC, int TX>
+struct SCfg {
+  static constexpr int E = ept(N);
+  static constexpr int TL = N / E;
+  static constexpr int LS = line_stride(N);
+  static constexpr int JOBS = NC * TX;
+  static constexpr int THREADS_ALL = JOBS * TL;
+  static constexpr int ROUNDS = THREADS_ALL > 2048 ? 8 : THREADS_ALL > 1024 ? 4 : THREADS_ALL > 512 ? 2 : 1;
+  // whole warps only: extra threads take no line but help with loads and stores
+  static constexpr int NT = ((THREADS_ALL / ROUNDS) + 31) / 32 * 32;
+  static constexpr int SMEM = (NC * TX * LS + N) * (int)sizeof(cx<T>);
+};
+
+template <typename T, int N, int OP, int NC, int TX, int SIGN, int NLINES>
+__device__ __forceinline__ void s_fft(cx<T>* sm, const cx<T>* tw) {
+  using C = SCfg<T, N, OP, NC, TX>;
+  constexpr int per_round = C::NT / C::TL;
+#pragma unroll 1
+  for (int r = 0; r < C::ROUNDS; ++r) {
+    const int job = r * per_round + threadIdx.x / C::TL;
+    const unsigned mask = __ballot_sync(0xffffffffu, job < NLINES);
+    if (job < NLINES) fft_line<T, N, SIGN, 1>(sm + job * C::LS, threadIdx.x % C::TL, tw, mask);
+  }
+}
+
+template <typename T, int N, int OP, int NC, int TX>
+__global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs<T> a) {
+  using C = SCfg<T, N, OP, NC, TX>;
+  constexpr int NIN = (OP == OP_SOLUTE) ? 4 : NC;
+  constexpr int NOUT = (OP == OP_SOLUTE) ? 3 : NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = sm + NC * TX * C::LS;
+  __shared__ double red[4 * 32];
+  const int p = blockIdx.z, outer = blockIdx.y, kx0 = blockIdx.x * TX;
+  if (a.sprm && a.sprm[p].done) return;
+  if (a.cprm && a.cprm[p].done) return;
+  cx<T>* base = a.spec + p * a.probStride + outer * a.outerStride + kx0;
+  const int w = min(TX, a.Pu - kx0);
+  load_tw<T, N>(tw, a.twg);
+  for (int idx = threadIdx.x; idx < NIN * N * TX; idx += blockDim.x) {
+    const int col = idx % TX, j = (idx / TX) % N, c = idx / (TX * N);
+    if (col < w) sm[(c * TX + col) * C::LS + pad(j)] = base[c * a.compStride + j * a.rowStride + col];
+  }
+  __syncthreads();
+  if constexpr (OP == OP_INV || OP == OP_INV_SCALE) {
+    if constexpr (OP == OP_INV_SCALE) {
+      const T s = (T)a.invV;
+      for (int idx = threadIdx.x; idx < NC * N * TX; idx += blockDim.x) {
+        const int col = idx % TX, j = (idx / TX) % N, c = idx / (TX * N);
+        cx<T>& x = sm[(c * TX + col) * C::LS + pad(j)];
+        x = cscale(x, s);
+      }
+      __syncthreads();
+    }
+    s_fft<T, N, OP, NC, TX, +1, NC * TX>(sm, tw);
+  } else {
+    s_fft<T, N, OP, NC, TX, -1, NIN * TX>(sm, tw);
+  }
+  if constexpr (OP == OP_DERIV) {
+    __syncthreads();
+    const T invV = (T)a.invV;
+    for (int idx = threadIdx.x; idx < NC * N * TX; idx += blockDim.x) {
+      const int col = idx % TX, j = (idx / TX) % N, c = idx / (TX * N);
+      if (col >= w) continue;
+      const T d = a.dm == 0 ? a.sym.d0[j] : (a.dm == 1 ? a.sym.d1[outer] : a.sym.d2[kx0 + col]);
+      cx<T>& x = sm[(c * TX + col) * C::LS + pad(j)];
+      x = cscale(mul_i(x), d * invV);
+    }
+    __syncthreads();
+    s_fft<T, N, OP, NC, TX, +1, NC * TX>(sm, tw);
+  }
+  if constexpr (OP == OP_STOKES || OP == OP_SOLUTE) {
+    __syncthreads();
+    const T invV = (T)a.invV;
+    const int ky = outer;
+    const T d1 = a.sym.d1[ky], l1 = a.sym.l1[ky];
+    T acc0 = 0, acc1 = 0, acc2 = 0;
+    for (int idx = threadIdx.x; idx < N * TX; idx += blockDim.x) {
+      const int col = idx % TX, j = idx / TX, kx = kx0 + col;
+      if (col >= w) continue;
+      const T d0 = a.sym.d0[j], l0 = a.sym.l0[j], d2 = a.sym.d2[kx], l2 = a.sym.l2[kx];
+      const T L = l0 + l1 + l2, dd = d0 * d0 + d1 * d1 + d2 * d2;
+      const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
+      const long long gi = (long long)p * a.compStride + (long long)j * a.rowStride + (long long)outer * a.outerStride + kx;
+      cx<T>* s0 = &sm[(0 * TX + col) * C::LS + pad(j)];
+      cx<T>* s1 = &sm[(1 * TX + col) * C::LS + pad(j)];
+      cx<T>* s2 = &sm[(2 * TX + col) * C::LS + pad(j)];
+      if constexpr (OP == OP_STOKES) {
+        const StokesDev& P = a.sprm[p];
+        const T nu = (T)P.nu, beta = (T)P.psi[1], b = (T)P.psi[2];
+        const cx<T> qh = a.st0[gi];
+        const cx<T> dprev = a.st1[gi];
+        // r = w^ - i d q^ (+ g V at k = 0)
+        const cx<T> iq = mul_i(qh);
+        cx<T> r0 = *s0 - cscale(iq, d0), r1 = *s1 - cscale(iq, d1), r2 = *s2 - cscale(iq, d2);
+        const bool k0 = (j == 0 && ky == 0 && kx == 0);
+        if (k0) {
+          const T Vt = (T)(1.0 / a.invV);
+          r0.x += (T)P.g[0] * Vt;
+          r1.x += (T)P.g[1] * Vt;
+          r2.x += (T)P.g[2] * Vt;
+        }
+        // Eq. 13: (nu L + b) u^ + beta d (d.u^) = r
+        const T c0 = nu * L + b;
+        const T ic0 = (T)1 / c0;
+        const cx<T> dr = cscale(r0, d0) + cscale(r1, d1) + cscale(r2, d2);
+        const cx<T> f = cscale(dr, beta / (c0 + beta * dd));
+        const cx<T> u0 = cscale(r0 - cscale(f, d0), ic0);
+        const cx<T> u1 = cscale(r1 - cscale(f, d1), ic0);
+        const cx<T> u2 = cscale(r2 - cscale(f, d2), ic0);
+        // div u^ = i d.u^ ; Eq. 9: q^ <- q^ - beta div u^
+        const cx<T> dv = mul_i(cscale(u0, d0) + cscale(u1, d1) + cscale(u2, d2));
+        const cx<T> qn = qh - cscale(dv, beta);
+        a.st0[gi] = qn;
+        a.st1[gi] = dv;
+        const cx<T> ddv = dv - dprev;
+        acc0 += wgt * cabs2(dv);
+        acc1 += wgt * cabs2(ddv);
+        acc2 += wgt * cabs2(qn);
+        if (k0) {
+          a.sprm[p].mean_u[0] = (double)u0.x * a.invV;
+          a.sprm[p].mean_u[1] = (double)u1.x * a.invV;
+          a.sprm[p].mean_u[2] = (double)u2.x * a.invV;
+        }
+        *s0 = cscale(u0, invV);
+        *s1 = cscale(u1, invV);
+        *s2 = cscale(u2, invV);
+      } else {
+        const SoluteDev& P = a.cprm[p];
+        cx<T>* s3 = &sm[(3 * TX + col) * C::LS + pad(j)];
+        // F^ = s^ + i d.tau^  (Eq. 18 in Fourier space)
+        const cx<T> F = *s3 + mul_i(cscale(*s0, d0) + cscale(*s1, d1) + cscale(*s2, d2));
+        // Eq. 20: chi^ = F^ / (i B0.d + A0 L), chi^(0) = 0
+        const T dre = (T)P.A0 * L, dim = (T)P.B0[0] * d0 + (T)P.B0[1] * d1 + (T)P.B0[2] * d2;
+        const bool k0 = (j == 0 && ky == 0 && kx == 0);
+        cx<T> chi = mk<T>(0, 0);
+        if (!k0) {
+          const T den = (T)1 / (dre * dre + dim * dim);
+          chi = mk<T>((F.x * dre + F.y * dim) * den, (F.y * dre - F.x * dim) * den);
+        }
+        const cx<T> dch = chi - a.st0[gi];
+        a.st0[gi] = chi;
+        acc0 += wgt * cabs2(dch);
+        acc1 += wgt * dd * cabs2(dch);
+        // grad chi^ = i d chi^, normalised for the inverse transform
+        const cx<T> ic = cscale(mul_i(chi), invV);
+        *s0 = cscale(ic, d0);
+        *s1 = cscale(ic, d1);
+        *s2 = cscale(ic, d2);
+      }
+    }
+    double v3[3] = {(double)acc0, (double)acc1, (double)acc2};
+    const int nb = gridDim.x * gridDim.y;
+    block_sum_store<3>(v3, red, a.part + ((long long)p * nb + blockIdx.y * gridDim.x + blockIdx.x) * 4);
+    __syncthreads();
+    s_fft<T, N, OP, NC, TX, +1, NOUT * TX>(sm, tw);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NOUT * N * TX; idx += blockDim.x) {
+    const int col = idx % TX, j = (idx / TX) % N, c = idx / (TX * N);
+    if (col < w) base[c * a.compStride + j * a.rowStride + col] = sm[(c * TX + col) * C::LS + pad(j)];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions over real fields
+// ---------------------------------------------------------------------------
+// sums[p][0..2] = sum u_c ; [3..5] = sum over pore u_c ; [6] = pore voxels
+template <typename T>
+__global__ void __launch_bounds__(256) k_field_sums(const T* __restrict__ u, const uint8_t* __restrict__ H, long long V,
+                                                   long long us, long long hs, double* __restrict__ part) {
+  __shared__ double red[7 * 32];
+  const int p = blockIdx.y;
+  const T* up = u + (long long)p * us;
+  const uint8_t* Hp = H + (long long)p * hs;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const double a = up[v], b = up[V + v], c = up[2 * V + v];
+    acc[0] += a;
+    acc[1] += b;
+    acc[2] += c;
+    if (Hp[v] == 0) {
+      acc[3] += a;
+      acc[4] += b;
+      acc[5] += c;
+      acc[6] += 1.0;
+    }
+  }
+  block_sum_store<7>(acc, red, part + ((long long)p * gridDim.x + blockIdx.x) * 8);
+}
+
+// Eq. 3 contracted with g, and the extended-domain average:
+// out[0..2] = sum_pore [g_i + Pe (ubar - u)_i chi + d_i chi]
+// out[3..5] = sum_Y A (g_i + d_i chi) + sum_pore Pe (ubar - u)_i chi
+template <typename T>
+__global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ chi, const T* __restrict__ grad,
+                                                    const T* __restrict__ u, const uint8_t* __restrict__ H,
+                                                    long long V, long long us, long long hs,
+                                                    const SoluteDev* __restrict__ prm, double* __restrict__ part) {
+  __shared__ double red[6 * 32];
+  const int p = blockIdx.y;
+  const SoluteDev& P = prm[p];
+  const T* cp = chi + (long long)p * V;
+  const T* gp = grad + (long long)p * 3 * V;
+  const T* up = u + (long long)p * us;
+  const uint8_t* Hp = H + (long long)p * hs;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const double c = cp[v];
+    const bool pore = Hp[v] == 0;
+    const double A = pore ? 1.0 : P.eta;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double gi = P.g[i] + (double)gp[i * V + v];
+      const double pe = pore ? P.Pe * (P.ubar[i] - (double)up[i * V + v]) * c : 0.0;
+      if (pore) acc[i] += gi + pe;
+      acc[3 + i] += A * gi + pe;
+    }
+  }
+  block_sum_store<6>(acc, red, part + ((long long)p * gridDim.x + blockIdx.x) * 8);
+}
+
+// products of three fields f_i (i = load) over the pore voxels:
+// out[0..5] = sum_pore f0 f0, f0 f1, f0 f2, f1 f1, f1 f2, f2 f2
+template <typename T>
+__global__ void __launch_bounds__(256) k_pore_products(const T* __restrict__ f, const uint8_t* __restrict__ H,
+                                                      long long V, double* __restrict__ part) {
+  __shared__ double red[6 * 32];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    if (H[v]) continue;
+    const double a = f[v], b = f[V + v], c = f[2 * V + v];
+    acc[0] += a * a;
+    acc[1] += a * b;
+    acc[2] += a * c;
+    acc[3] += b * b;
+    acc[4] += b * c;
+    acc[5] += c * c;
+  }
+  block_sum_store<6>(acc, red, part + (long long)blockIdx.x * 8);
+}
+
+// state conversion between precisions (mixed-precision continuation)
+template <typename S, typename D>
+__global__ void k_convert(const S* __restrict__ in, D* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (D)in[i];
+}
+
+// x (uint8) broadcast multiply: out = H * in for 3 components (warm-start lambda)
+template <typename T>
+__global__ void k_mask_solid(const T* __restrict__ in, T* __restrict__ out, const uint8_t* __restrict__ H, long long V) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * V; i += (long long)gridDim.x * blockDim.x)
+    out[i] = H[i % V] ? in[i] : (T)0;
+}
+
+// i d.u^ of a 3-component half spectrum into a 1-component one (warm start div^0)
+template <typename T>
+__global__ void k_div_spec(const cx<T>* __restrict__ uh, cx<T>* __restrict__ dv, Geo g, Sym<T> sym) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)g.n0 * g.n1 * g.P;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % g.P);
+    const long long r = i / g.P;
+    const int ky = (int)(r % g.n1), kz = (int)(r / g.n1);
+    if (kx >= g.Pu) {
+      dv[i] = mk<T>(0, 0);
+      continue;
+    }
+    const cx<T> s = cscale(uh[i], sym.d0[kz]) + cscale(uh[g.S + i], sym.d1[ky]) + cscale(uh[2 * g.S + i], sym.d2[kx]);
+    dv[i] = mul_i(s);
+  }
+}
+
+}  // namespace acm

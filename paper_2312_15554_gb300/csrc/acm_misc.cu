@@ -1,0 +1,176 @@
+// acm_misc.cu -- precision-independent kernels: FP64 finalize steps of both
+// iterations, precision conversion and the solid-voxel count.
+#include "acm_fft.cuh"
+#include "acm_kernels.cuh"
+#include "acm_ops.h"
+
+namespace acm {
+// ---------------------------------------------------------------------------
+// finalize kernels: deterministic FP64 sums of the partials, Eq. 10-12, Eq. 22
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sum_partials(const double* __restrict__ part, int nblk, int stride, int nval,
+                                             double* out, double* red) {
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+    for (int k = 0; k < nval; ++k) acc[k] += part[(long long)i * stride + k];
+  block_sum_store<5>(acc, red, out);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_stokes_finalize(StokesDev* __restrict__ prm, const double* __restrict__ part_x,
+                                                        int nbx, const double* __restrict__ part_z, int nbz,
+                                                        double V, double* __restrict__ hist, int hist_cap) {
+  __shared__ double red[5 * 32];
+  __shared__ double sx[5], sz[5];
+  const int p = blockIdx.x;
+  StokesDev* P = prm + p;
+  if (P->done) return;
+  sum_partials(part_x + (long long)p * nbx * 8, nbx, 8, 5, sx, red);
+  sum_partials(part_z + (long long)p * nbz * 4, nbz, 4, 3, sz, red);
+  if (threadIdx.x != 0) return;
+  const double alpha = P->psi[0], beta = P->psi[1], b = P->psi[2];
+  double r[6];
+  r[0] = sqrt(sx[0]);
+  r[1] = alpha * sqrt(sx[1]);
+  r[2] = sqrt(sz[0] / V);
+  r[3] = beta * sqrt(sz[1] / V);
+  r[4] = sqrt(sx[2]);
+  r[5] = b * sqrt(sx[3]);
+  const double nl = sqrt(sx[4]), nq = sqrt(sz[2] / V), na = nl;  // a = H lambda
+  const double e = P->eps, s13 = sqrt(3.0 * V) * e, s2 = sqrt(V) * e;
+  double t[6];
+  t[0] = s13 + e * fmax(r[0], nl);
+  t[1] = s13 + e * nl;
+  t[2] = s2 + e * fmax(r[2], nq);
+  t[3] = s2 + e * nq;
+  t[4] = s13 + e * fmax(r[4], na);
+  t[5] = s13 + e * na;
+  bool conv = true, finite = true;
+  for (int k = 0; k < 6; ++k) {
+    P->res[k] = r[k];
+    P->tol[k] = t[k];
+    conv = conv && (r[k] <= t[k]);
+    finite = finite && isfinite(r[k]);
+  }
+  P->iter += 1;
+  const int it = P->iter;
+  if (hist && it + P->iter_base <= hist_cap) {
+    double* h = hist + ((long long)p * hist_cap + (it + P->iter_base - 1)) * 16;
+    for (int k = 0; k < 6; ++k) h[k] = r[k];
+    for (int k = 0; k < 6; ++k) h[6 + k] = t[k];
+    h[12] = alpha;
+    h[13] = beta;
+    h[14] = b;
+    h[15] = P->mean_u[0] * P->g[0] + P->mean_u[1] * P->g[1] + P->mean_u[2] * P->g[2];
+  }
+  for (int k = 0; k < 3; ++k) {
+    P->psi_last[k] = P->psi[k];
+    P->psi_prev[k] = P->psi[k];
+  }
+  if (P->adaptive) {
+    for (int k = 0; k < 3; ++k) {  // Eq. 22: pair k drives (alpha, beta, b)[k]
+      const double rp = r[2 * k], rd = r[2 * k + 1];
+      if (rp > P->tau[k] * rd) P->psi[k] = P->phi[k] * P->psi[k];
+      else if (rd > P->tau[k] * rp) P->psi[k] = fmax(P->psi[k] / P->phi[k], P->psi_min[k]);
+    }
+  }
+  if (!finite) {
+    P->done = 1;
+    P->status = ST_NONFINITE;
+  } else if (conv) {
+    P->done = 1;
+    P->converged = 1;
+    P->status = ST_OK;
+  } else if (it >= P->max_iter) {
+    P->done = 1;
+    P->status = ST_MAXITER;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_solute_finalize(SoluteDev* __restrict__ prm, const double* __restrict__ part_z,
+                                                        int nbz, double V, double* __restrict__ hist, int hist_cap) {
+  __shared__ double red[5 * 32];
+  __shared__ double sz[5];
+  const int p = blockIdx.x;
+  SoluteDev* P = prm + p;
+  if (P->done) return;
+  sum_partials(part_z + (long long)p * nbz * 4, nbz, 4, 2, sz, red);
+  if (threadIdx.x != 0) return;
+  const double r1 = sqrt(sz[0] / V), r2 = sqrt(sz[1] / V);
+  const double t1 = sqrt(V) * P->eps, t2 = sqrt(3.0 * V) * P->eps;
+  P->res[0] = r1;
+  P->res[1] = r2;
+  P->tol[0] = t1;
+  P->tol[1] = t2;
+  P->iter += 1;
+  const int it = P->iter;
+  if (hist && it + P->iter_base <= hist_cap) {
+    double* h = hist + ((long long)p * hist_cap + (it + P->iter_base - 1)) * 4;
+    h[0] = r1;
+    h[1] = r2;
+    h[2] = t1;
+    h[3] = t2;
+  }
+  const double rn = r1 / (1.0 + t1);
+  if (!(isfinite(r1) && isfinite(r2))) {
+    P->done = 1;
+    P->status = ST_NONFINITE;
+    return;
+  }
+  if (r1 <= t1 && r2 <= t2) {
+    P->done = 1;
+    P->converged = 1;
+    P->status = ST_OK;
+    return;
+  }
+  if (it > 20 && rn > 1e3 * P->rmin) {
+    P->done = 1;
+    P->status = ST_DIVERGED;
+    return;
+  }
+  if (rn < P->rmin) P->rmin = rn;
+  if (it >= P->max_iter) {
+    P->done = 1;
+    P->status = ST_MAXITER;
+  }
+}
+
+__global__ void k_count_solid(const uint8_t* __restrict__ H, long long V, unsigned long long* out) {
+  unsigned long long c = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
+    c += H[i] ? 1ull : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+cudaError_t stokes_finalize(int nprob, StokesDev* prm, const double* part_x, int nbx, const double* part_z,
+                            int nbz, double V, double* hist, int hist_cap, cudaStream_t s) {
+  k_stokes_finalize<<<nprob, 256, 0, s>>>(prm, part_x, nbx, part_z, nbz, V, hist, hist_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t solute_finalize(int nprob, SoluteDev* prm, const double* part_z, int nbz, double V, double* hist,
+                            int hist_cap, cudaStream_t s) {
+  k_solute_finalize<<<nprob, 256, 0, s>>>(prm, part_z, nbz, V, hist, hist_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t count_solid(const uint8_t* H, long long V, unsigned long long* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_count_solid<<<304, 256, 0, s>>>(H, V, out);
+  return cudaGetLastError();
+}
+
+cudaError_t convert_f2d(const float* in, double* out, long long n, cudaStream_t s) {
+  k_convert<float, double><<<608, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t convert_d2f(const double* in, float* out, long long n, cudaStream_t s) {
+  k_convert<double, float><<<608, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace acm

@@ -1,0 +1,252 @@
+// acm_ops_impl.cuh -- definitions of the launch wrappers; included once per
+// precision (acm_f32.cu, acm_f64.cu) followed by an explicit instantiation.
+#pragma once
+#include "acm_kernels.cuh"
+#include "acm_ops.h"
+
+namespace acm {
+
+// Tile width (kx columns) of a strided pass: the widest of 16, 8, 4, 2 whose
+// shared-memory tile lets two blocks share an SM.
+constexpr int pick_tx(int csize, int N, int NC) {
+  return (NC * 16 * line_stride(N) * csize <= 110 * 1024)  ? 16
+         : (NC * 8 * line_stride(N) * csize <= 110 * 1024) ? 8
+         : (NC * 4 * line_stride(N) * csize <= 110 * 1024) ? 4
+                                                           : 2;
+}
+
+template <typename K>
+static cudaError_t set_smem(K* k, int bytes) {
+  return bytes > 48 * 1024 ? cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                           : cudaSuccess;
+}
+
+#define ACM_DISPATCH_N(n, FN, ...)     \
+  switch (n) {                         \
+    case 8: return FN<T, 8>(__VA_ARGS__);     \
+    case 16: return FN<T, 16>(__VA_ARGS__);   \
+    case 32: return FN<T, 32>(__VA_ARGS__);   \
+    case 64: return FN<T, 64>(__VA_ARGS__);   \
+    case 128: return FN<T, 128>(__VA_ARGS__); \
+    case 256: return FN<T, 256>(__VA_ARGS__); \
+    case 512: return FN<T, 512>(__VA_ARGS__); \
+    default: return cudaErrorInvalidValue;    \
+  }
+
+template <typename T, int N2>
+static cudaError_t l_x_local(const Geo& g, int nprob, const void* spec, void* u, void* lam, const uint8_t* H,
+                             StokesDev* prm, double* part, const void* tw, cudaStream_t s) {
+  constexpr int smem = x_smem_bytes<T, N2, 3>();
+  static const cudaError_t attr = set_smem(k_x_stokes_local<T, N2>, smem);
+  if (attr != cudaSuccess) return attr;
+  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  k_x_stokes_local<T, N2><<<grid, 3 * 64, smem, s>>>((const cx<T>*)spec, (T*)u, (T*)lam, H, prm, part, g,
+                                                     (const cx<T>*)tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int N2>
+static cudaError_t l_x_rhs(const Geo& g, int nprob, void* spec, const void* u, const void* lam, const uint8_t* H,
+                           const StokesDev* prm, const void* tw, cudaStream_t s) {
+  constexpr int smem = x_smem_bytes<T, N2, 3>();
+  static const cudaError_t attr = set_smem(k_x_stokes_rhs<T, N2>, smem);
+  if (attr != cudaSuccess) return attr;
+  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  k_x_stokes_rhs<T, N2><<<grid, 3 * 64, smem, s>>>((cx<T>*)spec, (const T*)u, (const T*)lam, H, prm, g,
+                                                   (const cx<T>*)tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int N2>
+static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
+                              const SoluteDev* prm, const void* tw, cudaStream_t s) {
+  constexpr int smem = x_smem_bytes<T, N2, 4>();
+  static const cudaError_t attr = set_smem(k_x_solute<T, N2>, smem);
+  if (attr != cudaSuccess) return attr;
+  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  k_x_solute<T, N2><<<grid, 4 * 64, smem, s>>>((cx<T>*)spec, (const T*)u, H, prm, g, (const cx<T>*)tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int N2, int NC>
+static cudaError_t l_x_r2c_nc(const Geo& g, int nprob, void* spec, long long sps, const void* in, long long ips,
+                              const void* tw, cudaStream_t s) {
+  constexpr int smem = x_smem_bytes<T, N2, NC>();
+  static const cudaError_t attr = set_smem(k_x_r2c<T, N2, NC>, smem);
+  if (attr != cudaSuccess) return attr;
+  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  k_x_r2c<T, N2, NC><<<grid, NC * 64, smem, s>>>((cx<T>*)spec, (const T*)in, g, ips, sps, (const cx<T>*)tw);
+  return cudaGetLastError();
+}
+template <typename T, int N2>
+static cudaError_t l_x_r2c(const Geo& g, int nprob, int nc, void* spec, long long sps, const void* in,
+                           long long ips, const void* tw, cudaStream_t s) {
+  if (nc == 1) return l_x_r2c_nc<T, N2, 1>(g, nprob, spec, sps, in, ips, tw, s);
+  if (nc == 3) return l_x_r2c_nc<T, N2, 3>(g, nprob, spec, sps, in, ips, tw, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int N2, int NC>
+static cudaError_t l_x_c2r_nc(const Geo& g, int nprob, const void* spec, long long sps, void* out, long long ops,
+                              const void* tw, cudaStream_t s) {
+  constexpr int smem = x_smem_bytes<T, N2, NC>();
+  static const cudaError_t attr = set_smem(k_x_c2r<T, N2, NC>, smem);
+  if (attr != cudaSuccess) return attr;
+  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  k_x_c2r<T, N2, NC><<<grid, NC * 64, smem, s>>>((const cx<T>*)spec, (T*)out, g, ops, sps, (const cx<T>*)tw);
+  return cudaGetLastError();
+}
+template <typename T, int N2>
+static cudaError_t l_x_c2r(const Geo& g, int nprob, int nc, const void* spec, long long sps, void* out,
+                           long long ops, const void* tw, cudaStream_t s) {
+  if (nc == 1) return l_x_c2r_nc<T, N2, 1>(g, nprob, spec, sps, out, ops, tw, s);
+  if (nc == 3) return l_x_c2r_nc<T, N2, 3>(g, nprob, spec, sps, out, ops, tw, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int N, int OP, int NC>
+static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
+                            const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
+                            cudaStream_t s, int dm) {
+  constexpr int TX = pick_tx((int)sizeof(cx<T>), N, NC);
+  using C = SCfg<T, N, OP, NC, TX>;
+  static const cudaError_t attr = set_smem(k_strided<T, N, OP, NC, TX>, C::SMEM);
+  if (attr != cudaSuccess) return attr;
+  PassArgs<T> a;
+  a.spec = (cx<T>*)spec;
+  a.probStride = probStride;
+  a.compStride = g.S;
+  if (axis == 1) {
+    a.rowStride = g.P;
+    a.outerStride = (long long)g.n1 * g.P;
+  } else {
+    a.rowStride = (long long)g.n1 * g.P;
+    a.outerStride = g.P;
+  }
+  a.Pu = g.Pu;
+  a.n1 = g.n1;
+  a.sym = sym;
+  a.twg = (const cx<T>*)tw;
+  a.st0 = (cx<T>*)st0;
+  a.st1 = (cx<T>*)st1;
+  a.sprm = sprm;
+  a.cprm = cprm;
+  a.part = part;
+  a.invV = 1.0 / (double)g.V;
+  a.nkx = g.n2 / 2;
+  a.dm = dm;
+  const int nouter = axis == 1 ? g.n0 : g.n1;
+  dim3 grid((g.Pu + TX - 1) / TX, nouter, nprob);
+  k_strided<T, N, OP, NC, TX><<<grid, C::NT, C::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t l_pass(const Geo& g, int axis, int op, int nc, int nprob, void* spec, long long ps,
+                          const Sym<T>& sym, const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm,
+                          double* part, cudaStream_t s, int dm) {
+#define ACM_PASS(OPV, NCV)                                                                                    \
+  if (op == OPV && nc == NCV)                                                                                 \
+    return l_pass_k<T, N, OPV, NCV>(g, axis, nprob, spec, ps, sym, tw, st0, st1, sprm, cprm, part, s, dm);
+  ACM_PASS(OP_FWD, 1)
+  ACM_PASS(OP_FWD, 3)
+  ACM_PASS(OP_FWD, 4)
+  ACM_PASS(OP_INV, 1)
+  ACM_PASS(OP_INV, 3)
+  ACM_PASS(OP_INV_SCALE, 1)
+  ACM_PASS(OP_STOKES, 3)
+  ACM_PASS(OP_SOLUTE, 4)
+  ACM_PASS(OP_DERIV, 1)
+#undef ACM_PASS
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int Ops<T>::x_blocks(const Geo& g) {
+  const int M = g.n2 / 2;
+  const int TL = M / ept(M);
+  return g.n0 * g.n1 / (64 / TL);
+}
+
+template <typename T>
+int Ops<T>::z_blocks(const Geo& g, int op) {
+  const int nc = op == P_SOLUTE ? 4 : 3;
+  const int tx = pick_tx((int)sizeof(cx<T>), g.n0, nc);
+  return ((g.Pu + tx - 1) / tx) * g.n1;
+}
+
+template <typename T>
+cudaError_t Ops<T>::x_stokes_local(const Geo& g, int nprob, const void* spec, void* u, void* lam, const uint8_t* H,
+                                   StokesDev* prm, double* part, const void* tw, cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_local, g, nprob, spec, u, lam, H, prm, part, tw, s)
+}
+
+template <typename T>
+cudaError_t Ops<T>::x_stokes_rhs(const Geo& g, int nprob, void* spec, const void* u, const void* lam,
+                                 const uint8_t* H, const StokesDev* prm, const void* tw, cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_rhs, g, nprob, spec, u, lam, H, prm, tw, s)
+}
+
+template <typename T>
+cudaError_t Ops<T>::x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
+                             const SoluteDev* prm, const void* tw, cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, prm, tw, s)
+}
+
+template <typename T>
+cudaError_t Ops<T>::x_r2c(const Geo& g, int nprob, int nc, void* spec, long long sps, const void* in, long long ips,
+                          const void* tw, cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_r2c, g, nprob, nc, spec, sps, in, ips, tw, s)
+}
+
+template <typename T>
+cudaError_t Ops<T>::x_c2r(const Geo& g, int nprob, int nc, const void* spec, long long sps, void* out,
+                          long long ops, const void* tw, cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_c2r, g, nprob, nc, spec, sps, out, ops, tw, s)
+}
+
+template <typename T>
+cudaError_t Ops<T>::pass(const Geo& g, int axis, int op, int nc, int nprob, void* spec, long long ps,
+                         const Sym<T>& sym, const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm,
+                         double* part, cudaStream_t s, int dm) {
+  const int n = axis == 1 ? g.n1 : g.n0;
+  if ((op == P_STOKES || op == P_SOLUTE || op == P_DERIV) && axis != 0) return cudaErrorInvalidValue;
+  ACM_DISPATCH_N(n, l_pass, g, axis, op, nc, nprob, spec, ps, sym, tw, st0, st1, sprm, cprm, part, s, dm)
+}
+
+template <typename T>
+cudaError_t Ops<T>::pore_products(const Geo& g, const void* f, const uint8_t* H, double* part, int nblk,
+                                  cudaStream_t s) {
+  k_pore_products<T><<<nblk, 256, 0, s>>>((const T*)f, H, g.V, part);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::field_sums(const Geo& g, int nprob, const void* u, const uint8_t* H, double* part, int nblk,
+                               cudaStream_t s) {
+  dim3 grid(nblk, nprob);
+  k_field_sums<T><<<grid, 256, 0, s>>>((const T*)u, H, g.V, g.us, g.hs, part);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::diffusivity(const Geo& g, int nprob, const void* chi, const void* grad, const void* u,
+                                const uint8_t* H, const SoluteDev* prm, double* part, int nblk, cudaStream_t s) {
+  dim3 grid(nblk, nprob);
+  k_diffusivity<T><<<grid, 256, 0, s>>>((const T*)chi, (const T*)grad, (const T*)u, H, g.V, g.us, g.hs, prm, part);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::mask_solid(const Geo& g, const void* in, void* out, const uint8_t* H, cudaStream_t s) {
+  k_mask_solid<T><<<608, 256, 0, s>>>((const T*)in, (T*)out, H, g.V);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Ops<T>::div_spec(const Geo& g, const void* uh, void* dv, const Sym<T>& sym, cudaStream_t s) {
+  k_div_spec<T><<<608, 256, 0, s>>>((const cx<T>*)uh, (cx<T>*)dv, g, sym);
+  return cudaGetLastError();
+}
+
+}  // namespace acm

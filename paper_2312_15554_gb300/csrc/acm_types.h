@@ -1,0 +1,63 @@
+// acm_types.h -- plain data shared by the host driver and the device kernels.
+#pragma once
+
+namespace acm {
+
+constexpr int TW_MAX = 1024;  // master twiddle table length (>= 2 * the largest axis)
+
+// ---------------------------------------------------------------------------
+// device-side per-problem state of a solve
+// ---------------------------------------------------------------------------
+struct StokesDev {
+  // set by the host before the solve
+  double nu, eps, g[3];
+  double phi[3], tau[3], psi_min[3];
+  int adaptive, max_iter;
+  // evolving
+  double psi[3];       // alpha, beta, b used by the coming iteration
+  double psi_prev[3];  // penalties of the iteration that produced the stored u
+  double psi_last[3];  // penalties of the last finalised iteration
+  double res[6], tol[6];
+  double mean_u[3];    // k = 0 tap of the last Green step (volume average of u)
+  int iter, done, status, converged;
+  int iter_base;       // iterations of earlier phases (history indexing)
+  int pad_;
+};
+
+struct SoluteDev {
+  double eps, A0, eta, Pe;
+  double B0[3], g[3], ubar[3];
+  double Fc;           // Pe * ubar . g
+  int max_iter;
+  double res[2], tol[2];
+  double rmin;
+  int iter, done, status, converged;
+  int iter_base, pad_;
+};
+
+// status codes mirrored from acm.h
+enum { ST_OK = 0, ST_MAXITER = -4, ST_DIVERGED = -5, ST_NONFINITE = -6 };
+
+// Geometry of one grid and its half spectrum.
+struct Geo {
+  int n0, n1, n2;
+  int P;        // row pitch of the half spectrum (complex elements), >= n2/2 + 1
+  int Pu;       // used columns n2/2 + 1
+  long long V;  // voxels
+  long long S;  // complex elements of one spectral component: n0 * n1 * P
+  long long hs; // stride of H between problems of a batch (0: one shared H)
+  long long us; // stride of the advecting velocity between problems (0: shared)
+};
+
+// Symbols of one precision: d and L per axis (axis 2 only up to n2/2).
+template <typename T>
+struct Sym {
+  const T* d0;
+  const T* l0;
+  const T* d1;
+  const T* l1;
+  const T* d2;
+  const T* l2;
+};
+
+}  // namespace acm

@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 paths agree with the oracle to 1e-10 relative to the field's
+largest magnitude (rounding order only); FP32 fields to 1e-5 relative; converged
+permeability and diffusivity to 1e-6 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import acm_oracle as O
+from paper_2312_15554_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def dev(x, dtype):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=DEV)
+
+
+def relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def run_stokes(lib, H, g, fp64, **kw):
+    dt = torch.float64 if fp64 else torch.float32
+    shape = H.shape
+    ctx = lib.acm_ctx(shape)
+    u = torch.zeros((3,) + shape, dtype=dt, device=DEV)
+    p = torch.zeros(shape, dtype=dt, device=DEV)
+    lam = torch.zeros((3,) + shape, dtype=dt, device=DEV)
+    init_u = kw.pop("init_u", None)
+    init_l = kw.pop("init_lambda", None)
+    prm = lib.stokes_params(precision=lib.FP64 if fp64 else lib.FP32, **kw)
+    s, K, rep = lib.acm_stokes(ctx, dev(H, torch.uint8), g, prm,
+                               None if init_u is None else dev(init_u, dt),
+                               None if init_l is None else dev(init_l, dt), u, p, lam)
+    torch.cuda.synchronize()
+    ctx.close()
+    return s, K, rep, u.cpu().numpy(), p.cpu().numpy(), lam.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# the 3D real FFT
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(8, 8, 8), (8, 16, 32), (32, 32, 32), (16, 64, 8), (64, 64, 64),
+                                   (16, 8, 512), (256, 16, 16)])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_fft_r2c_c2r_matches_oracle_transform(lib, shape, fp64):
+    x = I.random_field(shape, 7)
+    ref = O.fft3(x)[..., : shape[2] // 2 + 1]
+    dt = torch.float64 if fp64 else torch.float32
+    ctx = lib.acm_ctx(shape)
+    xin = dev(x, dt)
+    out = torch.zeros(shape[:2] + (shape[2] // 2 + 1, 2), dtype=dt, device=DEV)
+    lib.acm_fft_r2c(ctx, xin, out, fp64)
+    got = out.cpu().numpy()
+    got = got[..., 0] + 1j * got[..., 1]
+    tol = 1e-12 if fp64 else 2e-6
+    assert relerr(got, ref) < tol
+    back = torch.zeros(shape, dtype=dt, device=DEV)
+    lib.acm_fft_c2r(ctx, out, back, fp64)
+    assert relerr(back.cpu().numpy(), x) < tol
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# Stokes ADMM: fixed-iteration parity
+# ---------------------------------------------------------------------------
+CASES = [
+    ("sphere16", lambda: I.single_sphere((16, 16, 16), 0.3)),
+    ("rand8x16x32", lambda: I.random_indicator((8, 16, 32), 0.35, 4)),
+    ("pack32", lambda: I.sphere_pack((32, 32, 32), 0.45, 4.0, 11)[0]),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("deriv", [O.EXACT, O.CENTRAL])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_stokes_fixed_iterations_match_oracle(lib, case, deriv, fp64):
+    H = case[1]()
+    g = [1.0, 0.25, -0.5]
+    n_it = 12
+    pen = dict(alpha0=250.0, beta0=180.0, b0=300.0)
+    R = O.stokes(H, g, O.StokesParams(eps=0.0, adaptive=False, max_iter=n_it, deriv=deriv, **pen))
+    s, K, rep, u, p, lam = run_stokes(lib, H, g, fp64, eps=0.0, adaptive=0, max_iter=n_it, deriv=deriv, **pen)
+    assert s == lib.ACM_ERR_MAXITER and rep.iters == n_it
+    tol = 1e-10 if fp64 else 1e-5
+    assert relerr(u, R.state.u) < tol
+    assert relerr(p, R.p) < tol
+    assert relerr(lam, R.state.lam) < tol
+    np.testing.assert_allclose(rep.res[:6], R.residuals[-1], rtol=1e-8 if fp64 else 1e-4)
+    assert relerr(K, R.state.u.reshape(3, -1).mean(axis=1)) < (1e-10 if fp64 else 1e-5)
+
+
+def test_stokes_adaptive_penalties_follow_the_oracle_fp64(lib):
+    H = I.sphere_pack((16, 16, 16), 0.5, 3.0, 5)[0]
+    g = [0.0, 1.0, 0.0]
+    n_it = 60
+    R = O.stokes(H, g, O.StokesParams(eps=0.0, adaptive=True, max_iter=n_it, alpha0=50, beta0=400, b0=120))
+    s, K, rep, u, p, lam = run_stokes(lib, H, g, True, eps=0.0, adaptive=1, max_iter=n_it, alpha0=50,
+                                      beta0=400, b0=120)
+    np.testing.assert_allclose(rep.psi[:3], R.penalties[-1], rtol=1e-12)
+    assert relerr(u, R.state.u) < 1e-9
+    assert relerr(lam, R.state.lam) < 1e-9
+
+
+def test_stokes_warm_start_matches_oracle(lib):
+    H = I.sphere_pack((16, 16, 16), 0.5, 3.0, 6)[0]
+    Hf = H.astype(float)
+    u0 = 0.01 * I.random_field((3, 16, 16, 16), 3)
+    l0 = I.random_field((3, 16, 16, 16), 4) * Hf[None]
+    init = O.StokesState(u=u0, ut=u0.copy(), q=np.zeros(H.shape), a=l0.copy(), lam=l0.copy())
+    g = [1.0, 0.0, 0.0]
+    R = O.stokes(H, g, O.StokesParams(eps=0.0, adaptive=False, max_iter=7, alpha0=200, beta0=200, b0=200),
+                 init=init)
+    s, K, rep, u, p, lam = run_stokes(lib, H, g, True, eps=0.0, adaptive=0, max_iter=7, alpha0=200,
+                                      beta0=200, b0=200, init_u=u0, init_lambda=l0)
+    assert relerr(u, R.state.u) < 1e-10
+    assert relerr(lam, R.state.lam) < 1e-10
+    assert relerr(p, R.p) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Stokes: converged results
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "fp32_then_fp64"])
+def test_stokes_converged_permeability_matches_oracle(lib, precision):
+    H = I.single_sphere((16, 16, 16), 0.3)
+    g = [1.0, 0.0, 0.0]
+    kw = dict(eps=1e-10, adaptive=False, alpha0=300.0, beta0=300.0, b0=300.0, max_iter=20000,
+              deriv=O.CENTRAL)
+    R = O.stokes(H, g, O.StokesParams(**kw))
+    assert R.converged
+    dt = torch.float64
+    ctx = lib.acm_ctx(H.shape)
+    u = torch.zeros((3,) + H.shape, dtype=dt, device=DEV)
+    prm = lib.stokes_params(precision=lib.FP64 if precision == "fp64" else lib.FP32_THEN_FP64,
+                            eps32=1e-5, **{k: v for k, v in kw.items()})
+    s, K, rep = lib.acm_stokes(ctx, dev(H, torch.uint8), g, prm, None, None, u, None, None)
+    ctx.close()
+    assert s == 0 and rep.converged
+    assert abs(K[0] / R.K_col[0] - 1) < 1e-6
+    assert relerr(u.cpu().numpy(), R.state.u) < 1e-6
+    if precision == "fp32_then_fp64":
+        assert 0 < rep.iters_fp64 < rep.iters
+
+
+def test_stokes_tensor_and_gradient_form_match_oracle(lib):
+    H = I.random_indicator((8, 8, 8), 0.3, 33)
+    kw = dict(eps=1e-11, adaptive=False, alpha0=300.0, beta0=300.0, b0=300.0, max_iter=40000, deriv=O.CENTRAL)
+    Km, Kg, _ = O.permeability_tensor(H, O.StokesParams(**kw))
+    ctx = lib.acm_ctx(H.shape)
+    u3 = torch.zeros((3, 3) + H.shape, dtype=torch.float64, device=DEV)
+    s, K, Kgrad, reps = lib.acm_stokes_tensor(ctx, dev(H, torch.uint8), lib.stokes_params(precision=lib.FP64, **kw),
+                                              u3, grad_form=True)
+    ctx.close()
+    assert s == 0
+    assert relerr(K, Km) < 1e-6
+    assert relerr(Kgrad, Kg) < 1e-6
+    assert relerr(K, K.T) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# solute: fixed iterations and converged diffusivity
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("deriv", [O.CENTRAL, O.EXACT])
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("explicit_B0", [False, True])
+def test_solute_fixed_iterations_match_oracle(lib, deriv, fp64, explicit_B0):
+    shape = (16, 8, 32)
+    H = I.random_indicator(shape, 0.4, 8)
+    u = 0.3 * I.random_field((3,) + shape, 9) * (1 - H)[None]
+    Pe, gchi = 7.0, [0.3, 1.0, -0.2]
+    B0 = [1.0, 1.0, 1.0] if explicit_B0 else None
+    R = O.advdiff(H, u, Pe, gchi, O.AdvDiffParams(eta=0.01, A0=0.9, B0=B0, eps=0.0, max_iter=9, deriv=deriv))
+    dt = torch.float64 if fp64 else torch.float32
+    ctx = lib.acm_ctx(shape)
+    chi = torch.zeros(shape, dtype=dt, device=DEV)
+    grad = torch.zeros((3,) + shape, dtype=dt, device=DEV)
+    kw = dict(eta=0.01, A0=0.9, eps=0.0, max_iter=9, deriv=deriv, precision=lib.FP64 if fp64 else lib.FP32)
+    if explicit_B0:
+        kw["B0"] = B0
+    s, Dg, Dx, rep = lib.acm_advdiff(ctx, dev(H, torch.uint8), dev(u, dt), Pe, gchi, lib.advdiff_params(**kw),
+                                     chi, grad)
+    ctx.close()
+    assert s == lib.ACM_ERR_MAXITER and rep.iters == 9
+    tol = 1e-10 if fp64 else 1e-5
+    assert relerr(chi.cpu().numpy(), R.chi) < tol
+    assert relerr(grad.cpu().numpy(), R.grad_chi) < tol
+    assert relerr(Dg, R.Dg) < tol
+    assert relerr(Dx, R.Dg_ext) < tol
+
+
+def test_solute_converged_diffusivity_tensor_matches_oracle(lib):
+    shape = (16, 16, 16)
+    H = I.sphere_pack(shape, 0.5, 3.0, 12)[0]
+    Rs = O.stokes(H, [1.0, 0, 0], O.StokesParams(eps=1e-6, adaptive=False, alpha0=300, beta0=300, b0=300,
+                                                 deriv=O.CENTRAL))
+    u = Rs.state.u
+    u = u / np.abs(u).max()
+    Pe = 10.0
+    P = O.AdvDiffParams(eta=0.01, A0=0.55, eps=1e-10, max_iter=5000)
+    D, Dx, res = O.diffusivity_tensor(H, u, Pe, P)
+    assert all(r.converged for r in res)
+    ctx = lib.acm_ctx(shape)
+    s, Dg, Dgx, reps = lib.acm_advdiff_tensor(ctx, dev(H, torch.uint8), dev(u, torch.float64), Pe,
+                                              lib.advdiff_params(eta=0.01, A0=0.55, eps=1e-10, max_iter=5000,
+                                                                 precision=lib.FP64))
+    ctx.close()
+    assert s == 0
+    assert relerr(Dg, D) < 1e-6
+    assert relerr(Dgx, Dx) < 1e-6
+    assert abs(D[0, 1] - D[1, 0]) > 1e-6 * abs(D).max()   # flow makes D non-symmetric
+
+
+# ---------------------------------------------------------------------------
+# host buffers, edge cases, full-size workload
+# ---------------------------------------------------------------------------
+def test_host_buffers_give_the_device_result(lib):
+    H = I.sphere_pack((16, 16, 16), 0.5, 3.0, 2)[0]
+    g = [1.0, 0.0, 0.0]
+    ctx = lib.acm_ctx(H.shape)
+    prm = lib.stokes_params(precision=lib.FP32, eps=0.0, max_iter=10, adaptive=0)
+    u_h = np.zeros((3,) + H.shape, np.float32)
+    s1, K1, _ = lib.acm_stokes(ctx, H, g, prm, None, None, u_h, None, None)
+    u_d = torch.zeros((3,) + H.shape, dtype=torch.float32, device=DEV)
+    s2, K2, _ = lib.acm_stokes(ctx, dev(H, torch.uint8), g, prm, None, None, u_d, None, None)
+    ctx.close()
+    np.testing.assert_array_equal(u_h, u_d.cpu().numpy())
+    np.testing.assert_array_equal(K1, K2)
+
+
+def test_degenerate_indicators_are_rejected(lib):
+    shape = (8, 8, 8)
+    ctx = lib.acm_ctx(shape)
+    u = torch.zeros((3,) + shape, dtype=torch.float32, device=DEV)
+    for H, code in ((np.zeros(shape, np.uint8), -7), (np.ones(shape, np.uint8), -8)):
+        with pytest.raises(lib.AcmError) as e:
+            lib.acm_stokes(ctx, dev(H, torch.uint8), [1, 0, 0], lib.stokes_params(), None, None, u, None, None)
+        assert e.value.status == code
+    with pytest.raises(lib.AcmError) as e:
+        lib.acm_stokes(ctx, dev(np.eye(8, dtype=np.uint8)[None].repeat(8, 0), torch.uint8), [1, 0, 0],
+                       lib.stokes_params(nu=-1.0), None, None, u, None, None)
+    assert e.value.status == -1
+    ctx.close()
+
+
+def test_no_solid_no_flow_identity_diffusivity(lib):
+    shape = (8, 16, 8)
+    H = np.zeros(shape, np.uint8)
+    u = torch.zeros((3,) + shape, dtype=torch.float64, device=DEV)
+    ctx = lib.acm_ctx(shape)
+    s, D, Dx, reps = lib.acm_advdiff_tensor(ctx, dev(H, torch.uint8), u, 5.0,
+                                            lib.advdiff_params(precision=lib.FP64, eps=1e-12))
+    ctx.close()
+    np.testing.assert_allclose(D, np.eye(3), atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_bench_workload_first_iterations_match_oracle(lib, n):
+    """The bench's Boolean sphere pack (radius 8 voxels at 256^3, porosity 0.35):
+    the FP32 path in the bench's launch configuration against the oracle, two
+    iterations from rest, element by element."""
+    H = I.sphere_pack((n, n, n), 0.35, 8.0 * n / 256, 2024)[0]
+    g = [1.0, 0.0, 0.0]
+    n_it = 2
+    R = O.stokes(H, g, O.StokesParams(eps=0.0, adaptive=True, max_iter=n_it))
+    s, K, rep, u, p, lam = run_stokes(lib, H, g, False, eps=0.0, adaptive=1, max_iter=n_it)
+    assert relerr(u, R.state.u) < 1e-5
+    assert relerr(lam, R.state.lam) < 1e-5
+    assert relerr(p, R.p) < 1e-5
