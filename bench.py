@@ -1,0 +1,312 @@
+"""Throughput of the ACM hot path on one or more GPUs (one process per GPU).
+
+Workload: a 256^3 periodic cell of seeded Boolean (overlapping) spheres of
+radius 8 voxels at porosity 0.35. One step is
+  * Stokes (ADMM, adaptive penalties, FP32 fields, FP64 reductions): the three
+    unit loads solved together, ITERS iterations each, with residuals and stop
+    test every iteration and the permeability tensor at the end;
+  * solute (Lippmann-Schwinger, FP32): for Pe = 1, 10, 100 the three composition
+    loads advected by the e_0 flow, ITERS iterations each, with the effective
+    diffusivity tensor at the end.
+The metric is voxel-iterations per second: V * (3 + 9) * ITERS per step.
+
+Output: one JSON line on rank 0. `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 256
+POROSITY = 0.35
+RADIUS = 8.0
+PECLETS = (1.0, 10.0, 100.0)
+METRIC = "ACM voxel-iterations/s and time-to-permeability (rel err 1e-4) vs HBM roofline"
+UNIT = "voxel-iterations/s"
+WORKLOAD = (f"{N}^3 Boolean sphere pack (radius {RADIUS:g} vox, porosity {POROSITY}); Stokes 3 loads + "
+            f"solute Pe 1/10/100 x 3 loads")
+
+
+def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float) -> float:
+    """Bytes a kernel of the given kind must move per voxel and per problem (FP32).
+
+    cspec: one complex FP32 component of the half spectrum (n2/2 + 1 of n2 columns).
+    Multiplier lambda lives on solid voxels only, the solute velocity on pore voxels only.
+    """
+    cspec = 8.0 * (n2 // 2 + 1) / n2
+    solid = 1.0 - porosity
+    return {
+        "x_stokes_local": 3 * cspec + 24.0 + 24.0 * solid + 1.0,
+        "x_stokes_rhs": 12.0 + 12.0 * solid + 1.0 + 3 * cspec,
+        "y_fwd_stokes": 6 * cspec,
+        "z_stokes": 10 * cspec,
+        "y_inv_stokes": 6 * cspec,
+        "x_solute": 3 * cspec + 12.0 * porosity + 1.0 + 4 * cspec,
+        "y_fwd_solute": 8 * cspec,
+        "z_solute": 9 * cspec,
+        "y_inv_solute": 6 * cspec,
+    }.get(kind, 0.0)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(rank: int):
+    from paper_2312_15554_gb300 import inputs as I
+    H = I.sphere_pack((N, N, N), POROSITY, RADIUS, 2024 + rank)[0]
+    return H
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(H, iters: int = 1):
+    """Oracle Stokes + solute iterations on one load each; returns (voxel-iterations, seconds)."""
+    from oracle import acm_oracle as O
+    V = H.size
+    t0 = time.perf_counter()
+    R = O.stokes(H, [1.0, 0.0, 0.0], O.StokesParams(eps=0.0, max_iter=iters))
+    O.advdiff(H, R.state.u, 10.0, [1.0, 0.0, 0.0], O.AdvDiffParams(eps=0.0, max_iter=iters))
+    dt = time.perf_counter() - t0
+    return 2 * V * iters, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    H = make_inputs(0)
+    for _ in range(args.warmup):
+        oracle_sample(H)
+    vi, secs = 0, 0.0
+    for _ in range(args.steps):
+        a, b = oracle_sample(H)
+        vi += a
+        secs += b
+    value = vi / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "sample": "1 Stokes + 1 solute iteration (1 load each) per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: 1 ADMM iteration (load e_0) + 1 Lippmann-Schwinger iteration "
+                                   "(Pe 10, g_chi e_0) at 256^3, numpy FP64"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world, dist):
+    import torch
+
+    from paper_2312_15554_gb300 import acm
+    from paper_2312_15554_gb300 import build as B
+
+    B.build()
+    acm.load()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H = make_inputs(rank)
+    porosity = 1.0 - float(H.mean())
+    V = H.size
+    iters = args.iters
+    stream = torch.cuda.current_stream(dev)
+    ctx = acm.acm_ctx(H.shape, stream.cuda_stream)
+    Hd = torch.as_tensor(H, device=dev)
+    H_pin = torch.as_tensor(H).pin_memory()
+    u3 = torch.zeros((3, 3) + H.shape, dtype=torch.float32, device=dev)
+    sp = acm.stokes_params(eps=0.0, max_iter=iters, precision=acm.FP32)
+    cp = acm.advdiff_params(eps=0.0, max_iter=iters, precision=acm.FP32)
+
+    def step(Hin):
+        s, K, _, _ = acm.acm_stokes_tensor(ctx, Hin, sp, u3)
+        Ds = []
+        for Pe in PECLETS:
+            s2, D, _, _ = acm.acm_advdiff_tensor(ctx, Hin, u3[0], Pe, cp)
+            Ds.append(D)
+        return K, Ds
+
+    vi_per_step = V * iters * (3 + 3 * len(PECLETS))
+
+    for _ in range(args.warmup):
+        step(Hd)
+    torch.cuda.synchronize()
+    acm.acm_profile_read(ctx)                      # reset counters
+    acm.acm_profile_enable(ctx, True)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        K, Ds = step(Hd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    prof = acm.acm_profile_read(ctx)
+    acm.acm_profile_enable(ctx, False)
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = vi_per_step * args.steps * world / (ms / 1e3)
+
+    # end to end through the public API with host buffers: H from pinned host
+    # memory every call, K and D read back to the host
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        K, Ds = step(H_pin.numpy())
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = vi_per_step * world / e2e_s
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    kinds = {k: v for k, v in prof.items() if k not in ("other", "finalize") and v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    nprob = 3
+    bytes_per_launch = algorithmic_bytes_per_voxel(dom, N, porosity) * V * nprob
+    achieved = bytes_per_launch / (dom_ms / dom_n / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    launches = int(sum(v[1] for v in prof.values()))
+    kern = {k: {"ms": round(v[0], 3), "launches": v[1],
+                "GBps": (round(algorithmic_bytes_per_voxel(k, N, porosity) * V * nprob / (v[0] / v[1] / 1e3) / 1e9, 1)
+                         if v[1] and algorithmic_bytes_per_voxel(k, N, porosity) else None)}
+            for k, v in prof.items() if v[1]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        vi_c, s_c = oracle_sample(H, 1)
+        cpu = {"value": vi_c / s_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "1 ADMM iteration (load e_0) + 1 Lippmann-Schwinger iteration (Pe 10) at 256^3, "
+                         f"numpy FP64, {s_c:.1f} s"}
+    ctx.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "porosity": round(porosity, 4), "iters_per_step": iters,
+                   "problems_per_step": 3 + 3 * len(PECLETS), "l2": "inputs larger than L2 (3.3 GB working set)",
+                   "parallelism": f"independent cells x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": peak_src, "bytes_per_launch": bytes_per_launch},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * V),
+                "d2h_bytes_per_step": int(8 * 9 * (1 + len(PECLETS)))},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "kernels": kern,
+        "K_diag": [float(K[i, i]) for i in range(3)],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=20, help="iterations per problem per step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_gpu(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

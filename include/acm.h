@@ -190,6 +190,44 @@ acm_status acm_advdiff_tensor(acm_ctx* ctx, const uint8_t* H, const void* u, dou
 acm_status acm_fft_r2c(acm_ctx* ctx, int fp64, int nbatch, const void* in, void* out);
 acm_status acm_fft_c2r(acm_ctx* ctx, int fp64, int nbatch, const void* in, void* out);
 
+/* Convergence history of the last solve on this context for problem `index`
+ * (0 for acm_stokes and acm_advdiff; the load index 0..2 for the tensor calls).
+ * Copies up to `cap` records, record-major, into `out` (host) and returns the
+ * number of recorded iterations in *count (nullable) and the record length in
+ * *record_len (nullable); records are kept for the first 20000 iterations.
+ * Stokes records hold 20 doubles: r_p1, r_d1, r_p2, r_d2, r_p3, r_d3 (Eq. 10),
+ * their tolerances (Eq. 11-12), the penalties alpha, beta, b of the iteration,
+ * the volume average of u^{n+1} (3 components, the k = 0 coefficient of the
+ * Fourier solve; with a unit load e_j it is column j of K), and 2 unused.
+ * Solute records hold 4 doubles: r1, r2 (Eq. 19) and their tolerances. */
+acm_status acm_history(acm_ctx* ctx, int index, double* out, int cap, int* count, int* record_len);
+
+/* Kernel kinds of the per-kernel profiler. */
+typedef enum acm_kernel_kind {
+  ACM_K_X_STOKES_LOCAL = 0,  /* C2R along axis 2 + ADMM steps 2-3 (Eq. 8-9) + residual partial sums */
+  ACM_K_X_STOKES_RHS = 1,    /* known part of Eq. 7 + R2C along axis 2 */
+  ACM_K_Y_FWD_STOKES = 2,    /* forward FFT along axis 1, 3 components */
+  ACM_K_Z_STOKES = 3,        /* FFT along axis 0 + Eq. 13 solve + q update + inverse FFT */
+  ACM_K_Y_INV_STOKES = 4,    /* inverse FFT along axis 1, 3 components */
+  ACM_K_X_SOLUTE = 5,        /* C2R of grad chi + Eq. 18 local terms + R2C, axis 2 */
+  ACM_K_Y_FWD_SOLUTE = 6,    /* forward FFT along axis 1, 4 components */
+  ACM_K_Z_SOLUTE = 7,        /* FFT along axis 0 + Eq. 20 solve + inverse FFT */
+  ACM_K_Y_INV_SOLUTE = 8,    /* inverse FFT along axis 1, 3 components */
+  ACM_K_FINALIZE = 9,        /* FP64 residuals, tolerances, stop test, Eq. 22 */
+  ACM_K_OTHER = 10,          /* set-up, outputs, reductions, standalone transforms */
+  ACM_K_COUNT = 11
+} acm_kernel_kind;
+
+/* Per-kernel device timing. While enabled (on = 1), every kernel the context
+ * launches is bracketed by CUDA events recorded on the context's stream.
+ * acm_profile_read synchronises that stream and returns, per acm_kernel_kind,
+ * the summed device time in milliseconds (ms, nullable; zero for kinds launched
+ * while profiling was off) and the number of launches (launches, nullable;
+ * counted whether or not profiling is enabled) since the previous read, then
+ * resets both. Arrays have ACM_K_COUNT entries (host memory). */
+acm_status acm_profile_enable(acm_ctx* ctx, int on);
+acm_status acm_profile_read(acm_ctx* ctx, double* ms, long long* launches);
+
 /* Human-readable name of a status code (static string). */
 const char* acm_status_str(acm_status s);
 

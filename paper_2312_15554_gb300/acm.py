@@ -24,8 +24,11 @@ FP32, FP64, FP32_THEN_FP64 = 0, 1, 2
 EXPORTED = (
     "acm_stokes_default_params", "acm_advdiff_default_params", "acm_create", "acm_destroy",
     "acm_stokes", "acm_stokes_tensor", "acm_advdiff", "acm_advdiff_tensor",
-    "acm_fft_r2c", "acm_fft_c2r", "acm_status_str",
+    "acm_fft_r2c", "acm_fft_c2r", "acm_history", "acm_profile_enable", "acm_profile_read", "acm_status_str",
 )
+
+KERNEL_KINDS = ("x_stokes_local", "x_stokes_rhs", "y_fwd_stokes", "z_stokes", "y_inv_stokes", "x_solute",
+                "y_fwd_solute", "z_solute", "y_inv_solute", "finalize", "other")
 
 
 class acm_stokes_params(C.Structure):
@@ -81,6 +84,9 @@ def load(path: str = None):
                                        C.POINTER(acm_report)]
     lib.acm_fft_r2c.argtypes = [vp, ip, ip, vp, vp]
     lib.acm_fft_c2r.argtypes = [vp, ip, ip, vp, vp]
+    lib.acm_history.argtypes = [vp, ip, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.acm_profile_enable.argtypes = [vp, ip]
+    lib.acm_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
     lib.acm_status_str.argtypes = [ip]
     lib.acm_status_str.restype = cp
     for name in EXPORTED:
@@ -226,3 +232,29 @@ def acm_fft_r2c(ctx, x, out, fp64: bool, nbatch: int = 1):
 
 def acm_fft_c2r(ctx, x, out, fp64: bool, nbatch: int = 1):
     _check(load().acm_fft_c2r(ctx.h, int(fp64), nbatch, _ptr(x), _ptr(out)), "acm_fft_c2r")
+
+
+def acm_profile_enable(ctx, on: bool = True):
+    _check(load().acm_profile_enable(ctx.h, int(bool(on))), "acm_profile_enable")
+
+
+def acm_profile_read(ctx):
+    """Per kernel kind: (device ms, launches) since the previous read."""
+    n = len(KERNEL_KINDS)
+    ms = (C.c_double * n)()
+    cnt = (C.c_longlong * n)()
+    _check(load().acm_profile_read(ctx.h, ms, cnt), "acm_profile_read")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def acm_history(ctx, index: int = 0, cap: int = 20000):
+    """Per-iteration records of the last solve: numpy array (iterations, record length)."""
+    n = C.c_int()
+    ln = C.c_int()
+    _check(load().acm_history(ctx.h, int(index), None, 0, C.byref(n), C.byref(ln)), "acm_history")
+    k = min(cap, n.value)
+    if k == 0 or ln.value == 0:
+        return np.zeros((0, max(ln.value, 1)))
+    buf = (C.c_double * (k * ln.value))()
+    _check(load().acm_history(ctx.h, int(index), buf, k, C.byref(n), C.byref(ln)), "acm_history")
+    return np.array(buf[:]).reshape(k, ln.value)

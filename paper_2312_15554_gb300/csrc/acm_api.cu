@@ -61,6 +61,12 @@ struct acm_ctx {
   int hist_n[BMAX] = {0, 0, 0};
   void* pin = nullptr;  // pinned host scratch
   size_t pin_bytes = 0;
+  // profiler
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> recs;  // (kind, index of the start event)
+  long long launches[ACM_K_COUNT] = {};
 };
 
 namespace {
@@ -78,6 +84,40 @@ namespace {
   do {                                      \
     acm_status s_ = (x);                    \
     if (s_ != ACM_OK) return s_;            \
+  } while (0)
+
+void prof_begin(acm_ctx* c, int kind) {
+  c->launches[kind] += 1;
+  if (!c->prof) return;
+  while (c->ev.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      c->prof = false;
+      return;
+    }
+    c->ev.push_back(e);
+  }
+  cudaEventRecord(c->ev[c->ev_used], c->st);
+  c->recs.push_back({kind, c->ev_used});
+  c->ev_used += 2;
+}
+
+void prof_end(acm_ctx* c) {
+  if (!c->prof || c->recs.empty()) return;
+  cudaEventRecord(c->ev[c->recs.back().second + 1], c->st);
+}
+
+// launch through the profiler: one kernel launch of the given kind
+#define LK(kind, x)                         \
+  do {                                      \
+    prof_begin(c, kind);                    \
+    cudaError_t e_ = (x);                   \
+    prof_end(c);                            \
+    if (e_ != cudaSuccess) {                \
+      cudaGetLastError();                   \
+      return ACM_ERR_CUDA;                  \
+    }                                       \
   } while (0)
 
 bool pow2_in_range(int n) { return n >= 8 && n <= 512 && (n & (n - 1)) == 0; }
@@ -203,13 +243,15 @@ acm_status pin_scratch(acm_ctx* c, size_t bytes) {
 // H to device memory (staged when it is a host buffer); counts solid voxels
 acm_status stage_H(acm_ctx* c, const uint8_t* H, const uint8_t** Hdev, long long* nsolid) {
   const Geo& g = c->g;
-  if (is_device_ptr(H)) {
+  // the kernels stage H with 16-byte asynchronous copies: use a device buffer in
+  // place only when it is 16-byte aligned
+  if (is_device_ptr(H) && ((uintptr_t)H & 15) == 0) {
     *Hdev = H;
   } else {
-    CK(cudaMemcpyAsync(c->Hd, H, (size_t)g.V, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->Hd, H, (size_t)g.V, cudaMemcpyDefault, c->st));
     *Hdev = c->Hd;
   }
-  CK(count_solid(*Hdev, g.V, c->cnt, c->st));
+  LK(ACM_K_OTHER, count_solid(*Hdev, g.V, c->cnt, c->st));
   CKS(pin_scratch(c, 1 << 20));
   CK(cudaMemcpyAsync(c->pin, c->cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -274,14 +316,14 @@ acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
       CK(cudaMemcpyAsync(up, init_u, 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
       // div u^0 in Fourier space for the first dual residual of pair 2
       void* sp = (char*)w.spec;
-      CK(Ops<T>::x_r2c(g, 1, 3, sp, 3 * g.S, up, 3 * g.V, w.tw, c->st));
-      CK(Ops<T>::pass(g, 1, P_FWD, 3, 1, sp, 3 * g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
-      CK(Ops<T>::pass(g, 0, P_FWD, 3, 1, sp, 3 * g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
-      CK(Ops<T>::div_spec(g, sp, (char*)w.st1 + (size_t)p * g.S * cs, sym, c->st));
+      LK(ACM_K_OTHER, Ops<T>::x_r2c(g, 1, 3, sp, 3 * g.S, up, 3 * g.V, w.tw, c->st));
+      LK(ACM_K_OTHER, Ops<T>::pass(g, 1, P_FWD, 3, 1, sp, 3 * g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+      LK(ACM_K_OTHER, Ops<T>::pass(g, 0, P_FWD, 3, 1, sp, 3 * g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+      LK(ACM_K_OTHER, Ops<T>::div_spec(g, sp, (char*)w.st1 + (size_t)p * g.S * cs, sym, c->st));
     }
     if (init_lam) {
       CK(cudaMemcpyAsync(w.aux, init_lam, 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
-      CK(Ops<T>::mask_solid(g, w.aux, lp, Hdev + (size_t)p * hs, c->st));
+      LK(ACM_K_OTHER, Ops<T>::mask_solid(g, w.aux, lp, Hdev + (size_t)p * hs, c->st));
     }
   }
   std::vector<StokesDev> hp(nprob);
@@ -320,15 +362,20 @@ acm_status stokes_step1(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
   Geo g = c->g;
   g.hs = hs;
   const long long ps = 3 * g.S;
-  CK(Ops<T>::x_stokes_rhs(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, w.tw, c->st));
-  CK(Ops<T>::pass(g, 1, P_FWD, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, c->sprm, nullptr, nullptr, c->st));
-  CK(Ops<T>::pass(g, 0, P_STOKES, 3, nprob, w.spec, ps, sym, w.tw, w.st0, w.st1, c->sprm, nullptr, c->part_z, c->st));
-  CK(Ops<T>::pass(g, 1, P_INV, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, c->sprm, nullptr, nullptr, c->st));
+  LK(ACM_K_X_STOKES_RHS, Ops<T>::x_stokes_rhs(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, w.tw, c->st));
+  LK(ACM_K_Y_FWD_STOKES, Ops<T>::pass(g, 1, P_FWD, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, c->sprm, nullptr, nullptr, c->st));
+  LK(ACM_K_Z_STOKES, Ops<T>::pass(g, 0, P_STOKES, 3, nprob, w.spec, ps, sym, w.tw, w.st0, w.st1, c->sprm, nullptr, c->part_z, c->st));
+  LK(ACM_K_Y_INV_STOKES, Ops<T>::pass(g, 1, P_INV, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, c->sprm, nullptr, nullptr, c->st));
   return ACM_OK;
 }
 
+// Iterations of the device-resident loop. `remaining` bounds the iterations the
+// host launches (the finalize kernel also stops each problem at its max_iter),
+// so no launch is issued past the cap; problems that converge earlier turn the
+// rest of their launches into immediate returns.
 template <typename T>
-acm_status stokes_iterate(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int deriv, int check_every) {
+acm_status stokes_iterate(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int deriv, int check_every,
+                          int remaining) {
   Prec& w = prec<T>(c);
   Geo g = c->g;
   g.hs = hs;
@@ -337,12 +384,14 @@ acm_status stokes_iterate(acm_ctx* c, int nprob, const uint8_t* Hdev, long long 
   CKS(stokes_step1<T>(c, nprob, Hdev, hs, sym));
   CKS(pin_scratch(c, BMAX * sizeof(StokesDev)));
   if (check_every < 1) check_every = 1;
-  for (;;) {
-    for (int k = 0; k < check_every; ++k) {
-      CK(Ops<T>::x_stokes_local(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, c->part_x, w.tw, c->st));
-      CK(stokes_finalize(nprob, c->sprm, c->part_x, nbx, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
-      CKS(stokes_step1<T>(c, nprob, Hdev, hs, sym));
+  while (remaining > 0) {
+    const int chunk = check_every < remaining ? check_every : remaining;
+    for (int k = 0; k < chunk; ++k) {
+      LK(ACM_K_X_STOKES_LOCAL, Ops<T>::x_stokes_local(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, c->part_x, w.tw, c->st));
+      LK(ACM_K_FINALIZE, stokes_finalize(nprob, c->sprm, c->part_x, nbx, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
+      if (remaining - k > 1) CKS(stokes_step1<T>(c, nprob, Hdev, hs, sym));
     }
+    remaining -= chunk;
     CK(cudaMemcpyAsync(c->pin, c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     const StokesDev* hp = (const StokesDev*)c->pin;
@@ -359,10 +408,10 @@ acm_status stokes_promote(acm_ctx* c, int nprob, double eps) {
   Prec& f = c->pf;
   Prec& d = c->pd;
   const Geo& g = c->g;
-  CK(convert_f2d((const float*)f.u, (double*)d.u, (long long)nprob * 3 * g.V, c->st));
-  CK(convert_f2d((const float*)f.lam, (double*)d.lam, (long long)nprob * 3 * g.V, c->st));
-  CK(convert_f2d((const float*)f.st0, (double*)d.st0, (long long)nprob * 2 * g.S, c->st));
-  CK(convert_f2d((const float*)f.st1, (double*)d.st1, (long long)nprob * 2 * g.S, c->st));
+  LK(ACM_K_OTHER, convert_f2d((const float*)f.u, (double*)d.u, (long long)nprob * 3 * g.V, c->st));
+  LK(ACM_K_OTHER, convert_f2d((const float*)f.lam, (double*)d.lam, (long long)nprob * 3 * g.V, c->st));
+  LK(ACM_K_OTHER, convert_f2d((const float*)f.st0, (double*)d.st0, (long long)nprob * 2 * g.S, c->st));
+  LK(ACM_K_OTHER, convert_f2d((const float*)f.st1, (double*)d.st1, (long long)nprob * 2 * g.S, c->st));
   std::vector<StokesDev> hp(nprob);
   CK(cudaMemcpyAsync(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -394,15 +443,15 @@ acm_status stokes_outputs(acm_ctx* c, int nprob, void* u_out, long long u_stride
   if (p_out) {
     // p = q - mean(q): inverse transform of q^ (its k = 0 coefficient is 0)
     const Sym<T> sym = sym_of<T>(c, 0);
-    CK(Ops<T>::pass(g, 0, P_INV_SCALE, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr,
+    LK(ACM_K_OTHER, Ops<T>::pass(g, 0, P_INV_SCALE, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr,
                     c->st));
-    CK(Ops<T>::pass(g, 1, P_INV, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
-    CK(Ops<T>::x_c2r(g, nprob, 1, w.st0, g.S, w.aux, g.V, w.tw, c->st));
+    LK(ACM_K_OTHER, Ops<T>::pass(g, 1, P_INV, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+    LK(ACM_K_OTHER, Ops<T>::x_c2r(g, nprob, 1, w.st0, g.S, w.aux, g.V, w.tw, c->st));
     CK(cudaMemcpyAsync(p_out, w.aux, (size_t)nprob * g.V * sizeof(T), cudaMemcpyDefault, c->st));
   }
   if (Kcol) {
     g.hs = 0;
-    CK(Ops<T>::field_sums(g, nprob, w.u, c->Hd, c->part_r, NRED, c->st));
+    LK(ACM_K_OTHER, Ops<T>::field_sums(g, nprob, w.u, c->Hd, c->part_r, NRED, c->st));
     std::vector<double> s;
     CKS(read_partials(c, nprob, 3, s));
     for (int p = 0; p < nprob; ++p)
@@ -467,12 +516,12 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
   acm_status st = ACM_OK;
   if (P.precision == ACM_FP32) {
     CKS(stokes_setup<float>(c, nprob, Hdev, 0, gs, P, P.eps, init_u, init_lam));
-    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, P.deriv, P.check_every));
+    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, P.deriv, P.check_every, P.max_iter));
     CKS(stokes_outputs<float>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
     st = stokes_reports(c, nprob, rep, -1, t0);
   } else if (P.precision == ACM_FP64) {
     CKS(stokes_setup<double>(c, nprob, Hdev, 0, gs, P, P.eps, init_u, init_lam));
-    CKS(stokes_iterate<double>(c, nprob, Hdev, 0, P.deriv, P.check_every));
+    CKS(stokes_iterate<double>(c, nprob, Hdev, 0, P.deriv, P.check_every, P.max_iter));
     CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
     st = stokes_reports(c, nprob, rep, -2, t0);
   } else {
@@ -480,7 +529,7 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
     const double e32 = P.eps < P.eps32 ? P.eps32 : P.eps;
     if (init_u || init_lam) return ACM_ERR_ARG;  // warm starts are taken in the FP32 or FP64 modes
     CKS(stokes_setup<float>(c, nprob, Hdev, 0, gs, P, e32, nullptr, nullptr));
-    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, P.deriv, P.check_every));
+    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, P.deriv, P.check_every, P.max_iter));
     std::vector<StokesDev> hp(nprob);
     CK(cudaMemcpy(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost));
     int it32 = hp[0].iter;
@@ -488,7 +537,7 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
     for (auto& x : hp) ok = ok && x.status == ACM_OK;
     if (ok && P.eps < e32) {
       CKS(stokes_promote(c, nprob, P.eps));
-      CKS(stokes_iterate<double>(c, nprob, Hdev, 0, P.deriv, P.check_every));
+      CKS(stokes_iterate<double>(c, nprob, Hdev, 0, P.deriv, P.check_every, P.max_iter - it32));
       CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
       st = stokes_reports(c, nprob, rep, it32, t0);
     } else {
@@ -514,14 +563,14 @@ acm_status perm_grad(acm_ctx* c, const uint8_t* Hdev, int deriv, double Kg[9]) {
   T* f = (T*)w.aux;
   double K[6] = {0, 0, 0, 0, 0, 0};
   for (int l = 0; l < 3; ++l) {
-    CK(Ops<T>::x_r2c(g, 3, 1, w.st0, g.S, (T*)w.u + (size_t)l * g.V, 3 * g.V, w.tw, c->st));
-    CK(Ops<T>::pass(g, 1, P_FWD, 1, 3, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+    LK(ACM_K_OTHER, Ops<T>::x_r2c(g, 3, 1, w.st0, g.S, (T*)w.u + (size_t)l * g.V, 3 * g.V, w.tw, c->st));
+    LK(ACM_K_OTHER, Ops<T>::pass(g, 1, P_FWD, 1, 3, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
     for (int m = 0; m < 3; ++m) {
       CK(cudaMemcpyAsync(w.spec, w.st0, 3 * g.S * cs, cudaMemcpyDeviceToDevice, c->st));
-      CK(Ops<T>::pass(g, 0, P_DERIV, 1, 3, w.spec, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st, m));
-      CK(Ops<T>::pass(g, 1, P_INV, 1, 3, w.spec, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
-      CK(Ops<T>::x_c2r(g, 3, 1, w.spec, g.S, f, g.V, w.tw, c->st));
-      CK(Ops<T>::pore_products(g, f, Hdev, c->part_r, NRED, c->st));
+      LK(ACM_K_OTHER, Ops<T>::pass(g, 0, P_DERIV, 1, 3, w.spec, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st, m));
+      LK(ACM_K_OTHER, Ops<T>::pass(g, 1, P_INV, 1, 3, w.spec, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+      LK(ACM_K_OTHER, Ops<T>::x_c2r(g, 3, 1, w.spec, g.S, f, g.V, w.tw, c->st));
+      LK(ACM_K_OTHER, Ops<T>::pore_products(g, f, Hdev, c->part_r, NRED, c->st));
       std::vector<double> s;
       CKS(read_partials(c, 1, 6, s));
       for (int k = 0; k < 6; ++k) K[k] += s[k];
@@ -539,7 +588,7 @@ acm_status perm_grad(acm_ctx* c, const uint8_t* Hdev, int deriv, double Kg[9]) {
 template <typename T>
 acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us,
                       const double (*gchi)[3], double Pe, const acm_advdiff_params& P, double eps, bool setup,
-                      const double* B0, const double* ubar) {
+                      const double* B0, const double* ubar, int iters_done = 0) {
   CKS(ensure_prec<T>(c));
   Prec& w = prec<T>(c);
   Geo g = c->g;
@@ -575,16 +624,19 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
   const long long ps = 4 * g.S;
   CKS(pin_scratch(c, BMAX * sizeof(SoluteDev)));
   const int ce = P.check_every < 1 ? 1 : P.check_every;
-  for (;;) {
-    for (int k = 0; k < ce; ++k) {
-      CK(Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->cprm, w.tw, c->st));
-      CK(Ops<T>::pass(g, 1, P_FWD, 4, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm, nullptr,
+  int remaining = P.max_iter - (setup ? 0 : iters_done);
+  while (remaining > 0) {
+    const int chunk = ce < remaining ? ce : remaining;
+    remaining -= chunk;
+    for (int k = 0; k < chunk; ++k) {
+      LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->cprm, w.tw, c->st));
+      LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD, 4, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm, nullptr,
                       c->st));
-      CK(Ops<T>::pass(g, 0, P_SOLUTE, 4, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm, c->part_z,
+      LK(ACM_K_Z_SOLUTE, Ops<T>::pass(g, 0, P_SOLUTE, 4, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm, c->part_z,
                       c->st));
-      CK(Ops<T>::pass(g, 1, P_INV, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm, nullptr,
+      LK(ACM_K_Y_INV_SOLUTE, Ops<T>::pass(g, 1, P_INV, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm, nullptr,
                       c->st));
-      CK(solute_finalize(nprob, c->cprm, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
+      LK(ACM_K_FINALIZE, solute_finalize(nprob, c->cprm, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
     }
     CK(cudaMemcpyAsync(c->pin, c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -607,13 +659,13 @@ acm_status solute_outputs(acm_ctx* c, int nprob, const uint8_t* Hdev, const void
   T* grad = (T*)w.aux;
   T* chi = (T*)w.aux + (size_t)BMAX * 3 * g.V;
   // grad chi^{n+1}: the last pass left i d chi^ (inverse along z and y) in components 0..2
-  CK(Ops<T>::x_c2r(g, nprob, 3, w.spec, 4 * g.S, grad, 3 * g.V, w.tw, c->st));
+  LK(ACM_K_OTHER, Ops<T>::x_c2r(g, nprob, 3, w.spec, 4 * g.S, grad, 3 * g.V, w.tw, c->st));
   // chi^{n+1}
-  CK(Ops<T>::pass(g, 0, P_INV_SCALE, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr,
+  LK(ACM_K_OTHER, Ops<T>::pass(g, 0, P_INV_SCALE, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr,
                   c->st));
-  CK(Ops<T>::pass(g, 1, P_INV, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
-  CK(Ops<T>::x_c2r(g, nprob, 1, w.st0, g.S, chi, g.V, w.tw, c->st));
-  CK(Ops<T>::diffusivity(g, nprob, chi, grad, udev, Hdev, c->cprm, c->part_r, NRED, c->st));
+  LK(ACM_K_OTHER, Ops<T>::pass(g, 1, P_INV, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+  LK(ACM_K_OTHER, Ops<T>::x_c2r(g, nprob, 1, w.st0, g.S, chi, g.V, w.tw, c->st));
+  LK(ACM_K_OTHER, Ops<T>::diffusivity(g, nprob, chi, grad, udev, Hdev, c->cprm, c->part_r, NRED, c->st));
   std::vector<double> s;
   CKS(read_partials(c, nprob, 6, s));
   for (int p = 0; p < nprob; ++p)
@@ -636,8 +688,8 @@ acm_status solute_outputs(acm_ctx* c, int nprob, const uint8_t* Hdev, const void
 acm_status solute_promote(acm_ctx* c, int nprob, double eps) {
   CKS(ensure_prec<double>(c));
   const Geo& g = c->g;
-  CK(convert_f2d((const float*)c->pf.st0, (double*)c->pd.st0, (long long)nprob * 2 * g.S, c->st));
-  CK(convert_f2d((const float*)c->pf.spec, (double*)c->pd.spec, (long long)nprob * 4 * 2 * g.S, c->st));
+  LK(ACM_K_OTHER, convert_f2d((const float*)c->pf.st0, (double*)c->pd.st0, (long long)nprob * 2 * g.S, c->st));
+  LK(ACM_K_OTHER, convert_f2d((const float*)c->pf.spec, (double*)c->pd.spec, (long long)nprob * 4 * 2 * g.S, c->st));
   std::vector<SoluteDev> hp(nprob);
   CK(cudaMemcpyAsync(hp.data(), c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -697,17 +749,19 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
   const size_t rs = fp32 ? sizeof(float) : sizeof(double);
   const Geo& g0 = c->g;
   // the advecting velocity in device memory of the working precision
+  // used in place when it is a device buffer aligned to its element size
   const void* ud = u;
+  const bool in_place = is_device_ptr(u) && ((uintptr_t)u % rs) == 0;
   if (fp32) {
     CKS(ensure_prec<float>(c));
-    if (!is_device_ptr(u)) {
-      CK(cudaMemcpyAsync(c->pf.u, u, 3 * g0.V * rs, cudaMemcpyHostToDevice, c->st));
+    if (!in_place) {
+      CK(cudaMemcpyAsync(c->pf.u, u, 3 * g0.V * rs, cudaMemcpyDefault, c->st));
       ud = c->pf.u;
     }
   } else {
     CKS(ensure_prec<double>(c));
-    if (!is_device_ptr(u)) {
-      CK(cudaMemcpyAsync(c->pd.u, u, 3 * g0.V * rs, cudaMemcpyHostToDevice, c->st));
+    if (!in_place) {
+      CK(cudaMemcpyAsync(c->pd.u, u, 3 * g0.V * rs, cudaMemcpyDefault, c->st));
       ud = c->pd.u;
     }
   }
@@ -716,8 +770,8 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
   g.us = 0;
   g.hs = 0;
   std::vector<double> s;
-  if (fp32) CK(Ops<float>::field_sums(g, 1, ud, Hdev, c->part_r, NRED, c->st));
-  else CK(Ops<double>::field_sums(g, 1, ud, Hdev, c->part_r, NRED, c->st));
+  if (fp32) LK(ACM_K_OTHER, Ops<float>::field_sums(g, 1, ud, Hdev, c->part_r, NRED, c->st));
+  else LK(ACM_K_OTHER, Ops<double>::field_sums(g, 1, ud, Hdev, c->part_r, NRED, c->st));
   {
     CKS(pin_scratch(c, (size_t)NRED * 8 * sizeof(double)));
     CK(cudaMemcpyAsync(c->pin, c->part_r, (size_t)NRED * 8 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -745,7 +799,7 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
   } else {
     // FP32 phase needs the velocity in FP32
     CKS(ensure_prec<float>(c));
-    CK(convert_d2f((const double*)ud, (float*)c->pf.u, 3 * g.V, c->st));
+    LK(ACM_K_OTHER, convert_d2f((const double*)ud, (float*)c->pf.u, 3 * g.V, c->st));
     const double e32 = P.eps < 1e-5 ? 1e-5 : P.eps;
     CKS(solute_run<float>(c, nprob, Hdev, c->pf.u, 0, gchi, Pe, P, e32, true, B0, ubar));
     std::vector<SoluteDev> hp(nprob);
@@ -754,7 +808,7 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
     bool ok = true;
     for (auto& x : hp) ok = ok && x.status == ACM_OK;
     CKS(solute_promote(c, nprob, P.eps));
-    if (ok && P.eps < e32) CKS(solute_run<double>(c, nprob, Hdev, ud, 0, gchi, Pe, P, P.eps, false, B0, ubar));
+    if (ok && P.eps < e32) CKS(solute_run<double>(c, nprob, Hdev, ud, 0, gchi, Pe, P, P.eps, false, B0, ubar, it32));
     else CK(cudaMemcpy(c->cprm, hp.data(), nprob * sizeof(SoluteDev), cudaMemcpyHostToDevice));
     CKS(solute_outputs<double>(c, nprob, Hdev, ud, 0, chi_out, grad_out, Dg, Dx));
     st = solute_reports(c, nprob, rep, it32, false, t0);
@@ -835,7 +889,7 @@ acm_status acm_create(acm_ctx** out, int n0, int n1, int n2, void* stream) {
             cudaMalloc(&c->part_r, (size_t)BMAX * NRED * 8 * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->Hd, (size_t)g.V) == cudaSuccess &&
             cudaMalloc(&c->cnt, sizeof(unsigned long long)) == cudaSuccess &&
-            cudaMalloc(&c->hist, (size_t)BMAX * HIST_CAP * 16 * sizeof(double)) == cudaSuccess;
+            cudaMalloc(&c->hist, (size_t)BMAX * HIST_CAP * STOKES_HIST * sizeof(double)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     acm_destroy(c);
@@ -861,6 +915,7 @@ acm_status acm_destroy(acm_ctx* c) {
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->pin) cudaFreeHost(c->pin);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   cudaGetLastError();
   delete c;
   return ACM_OK;
@@ -946,14 +1001,14 @@ static acm_status fft_impl(acm_ctx* c, int fp64, int nbatch, const void* in, voi
       }
       if (fp64) {
         const Sym<double> sym = sym_of<double>(c, 0);
-        CK(Ops<double>::x_r2c(g, 1, 1, w.st0, g.S, src, g.V, w.tw, c->st));
-        CK(Ops<double>::pass(g, 1, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
-        CK(Ops<double>::pass(g, 0, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        LK(ACM_K_OTHER, Ops<double>::x_r2c(g, 1, 1, w.st0, g.S, src, g.V, w.tw, c->st));
+        LK(ACM_K_OTHER, Ops<double>::pass(g, 1, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        LK(ACM_K_OTHER, Ops<double>::pass(g, 0, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
       } else {
         const Sym<float> sym = sym_of<float>(c, 0);
-        CK(Ops<float>::x_r2c(g, 1, 1, w.st0, g.S, src, g.V, w.tw, c->st));
-        CK(Ops<float>::pass(g, 1, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
-        CK(Ops<float>::pass(g, 0, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        LK(ACM_K_OTHER, Ops<float>::x_r2c(g, 1, 1, w.st0, g.S, src, g.V, w.tw, c->st));
+        LK(ACM_K_OTHER, Ops<float>::pass(g, 1, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        LK(ACM_K_OTHER, Ops<float>::pass(g, 0, P_FWD, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
       }
       CK(cudaMemcpy2DAsync((char*)out + (size_t)b * g.n0 * g.n1 * g.Pu * cs, g.Pu * cs, w.st0, g.P * cs, g.Pu * cs,
                            (size_t)g.n0 * g.n1, cudaMemcpyDefault, c->st));
@@ -965,14 +1020,14 @@ static acm_status fft_impl(acm_ctx* c, int fp64, int nbatch, const void* in, voi
       void* tgt = dev ? dst : w.aux;
       if (fp64) {
         const Sym<double> sym = sym_of<double>(c, 0);
-        CK(Ops<double>::pass(g, 0, P_INV_SCALE, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
-        CK(Ops<double>::pass(g, 1, P_INV, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
-        CK(Ops<double>::x_c2r(g, 1, 1, w.st0, g.S, tgt, g.V, w.tw, c->st));
+        LK(ACM_K_OTHER, Ops<double>::pass(g, 0, P_INV_SCALE, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        LK(ACM_K_OTHER, Ops<double>::pass(g, 1, P_INV, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        LK(ACM_K_OTHER, Ops<double>::x_c2r(g, 1, 1, w.st0, g.S, tgt, g.V, w.tw, c->st));
       } else {
         const Sym<float> sym = sym_of<float>(c, 0);
-        CK(Ops<float>::pass(g, 0, P_INV_SCALE, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
-        CK(Ops<float>::pass(g, 1, P_INV, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
-        CK(Ops<float>::x_c2r(g, 1, 1, w.st0, g.S, tgt, g.V, w.tw, c->st));
+        LK(ACM_K_OTHER, Ops<float>::pass(g, 0, P_INV_SCALE, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        LK(ACM_K_OTHER, Ops<float>::pass(g, 1, P_INV, 1, 1, w.st0, g.S, sym, w.tw, 0, 0, 0, 0, 0, c->st));
+        LK(ACM_K_OTHER, Ops<float>::x_c2r(g, 1, 1, w.st0, g.S, tgt, g.V, w.tw, c->st));
       }
       if (!dev) CK(cudaMemcpyAsync(dst, w.aux, g.V * rs, cudaMemcpyDeviceToHost, c->st));
     }
@@ -987,6 +1042,46 @@ acm_status acm_fft_r2c(acm_ctx* c, int fp64, int nbatch, const void* in, void* o
 
 acm_status acm_fft_c2r(acm_ctx* c, int fp64, int nbatch, const void* in, void* out) {
   return fft_impl(c, fp64, nbatch, in, out, false);
+}
+
+acm_status acm_history(acm_ctx* c, int index, double* out, int cap, int* count, int* record_len) {
+  if (!c || index < 0 || index >= BMAX || cap < 0 || (cap > 0 && !out)) return ACM_ERR_ARG;
+  const int len = c->hist_kind == 2 ? SOLUTE_HIST : STOKES_HIST;
+  const int n = c->hist_kind == 0 ? 0 : std::min(cap, c->hist_n[index]);
+  if (record_len) *record_len = c->hist_kind == 0 ? 0 : len;
+  if (count) *count = c->hist_kind == 0 ? 0 : c->hist_n[index];
+  if (n > 0) {
+    if (c->st) CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemcpy(out, c->hist + (size_t)index * HIST_CAP * len, (size_t)n * len * sizeof(double),
+                  cudaMemcpyDeviceToHost));
+  }
+  return ACM_OK;
+}
+
+acm_status acm_profile_enable(acm_ctx* c, int on) {
+  if (!c) return ACM_ERR_ARG;
+  c->prof = on != 0;
+  return ACM_OK;
+}
+
+acm_status acm_profile_read(acm_ctx* c, double* ms, long long* launches) {
+  if (!c) return ACM_ERR_ARG;
+  if (c->st) CK(cudaStreamSynchronize(c->st));
+  else CK(cudaDeviceSynchronize());
+  if (ms) {
+    for (int k = 0; k < ACM_K_COUNT; ++k) ms[k] = 0.0;
+    for (auto& r : c->recs) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, c->ev[r.second], c->ev[r.second + 1]) == cudaSuccess) ms[r.first] += t;
+      else cudaGetLastError();
+    }
+  }
+  if (launches)
+    for (int k = 0; k < ACM_K_COUNT; ++k) launches[k] = c->launches[k];
+  for (int k = 0; k < ACM_K_COUNT; ++k) c->launches[k] = 0;
+  c->recs.clear();
+  c->ev_used = 0;
+  return ACM_OK;
 }
 
 const char* acm_status_str(acm_status s) {

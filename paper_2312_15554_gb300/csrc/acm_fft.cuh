@@ -51,11 +51,27 @@ __device__ __forceinline__ T cabs2(cx<T> a) { return a.x * a.x + a.y * a.y; }
 
 // padded shared-memory index: one spare slot after every 16 elements
 __host__ __device__ constexpr int pad(int i) { return i + (i >> 4); }
-// stride between lines that hold L + 1 complex values (index L is used by the
-// real-to-complex post-processing for the Nyquist bin)
-__host__ __device__ constexpr int line_stride(int L) { return L + (L >> 4) + 1; }
-
 __host__ __device__ constexpr int ept(int n) { return n < 16 ? n : 16; }  // elements per thread
+
+// Stride (complex elements) between padded lines of length L in shared memory.
+// One shared-memory wavefront serves W = 128 bytes / element size threads (16
+// for FP32 complex, 8 for FP64 complex), each touching one slot. When a line's
+// transform uses TL < W threads, a wavefront spans W/TL lines and each line
+// covers TL consecutive slots, so the lines must start TL slots apart modulo W:
+// stride = TL * odd (mod W). When lines are loaded as the TX columns of a tile
+// (TX threads per row, W/TX rows per wavefront) the columns must start W/TX
+// slots apart. The first stride at or above the padded length that meets the
+// active constraint is used; with TL < W the transform's constraint wins (it
+// is accessed more often).
+__host__ __device__ constexpr int line_stride(int L, int TL, int TX, int W) {
+  int ls = (L - 1) + ((L - 1) >> 4) + 1;
+  const int q = TL < W ? TL : (TX >= 1 && TX < W ? W / TX : 1);
+  while (((ls / q) % 2) == 0 || (ls % q) != 0) ++ls;
+  return ls;
+}
+
+template <typename T>
+__host__ __device__ constexpr int wave_slots() { return 128 / (2 * (int)sizeof(T)); }
 
 // multiply by exp(SIGN * i * pi / 2): SIGN = -1 -> -i, SIGN = +1 -> +i
 template <int SIGN, typename T>
@@ -169,11 +185,44 @@ __device__ __forceinline__ void dft(cx<T>* v) {
 }
 
 // ---------------------------------------------------------------------------
-// Stockham stage: radix R, Ns = product of the previous radices
-// tw: table of W_{N * TWS}^k = exp(-2 pi i k / (N * TWS)) in shared memory;
-//     W_N^k is tw[k * TWS].
+// Stage twiddles. The stage that starts at span Ns (> 1) with radix R needs
+// W_N^{jm r N / (Ns R)} for r in [1, R) and jm in [0, Ns); they are stored as
+// [r - 1][jm] so that the threads of a line read consecutive entries.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int R, int Ns, int SIGN, int TWS>
+__host__ __device__ constexpr int stage_radix(int N, int Ns) { return (N / Ns >= ept(N)) ? ept(N) : N / Ns; }
+
+__host__ __device__ constexpr int tw_offset(int N, int Ns) {
+  int off = 0;
+  for (int s = 1; s < Ns; s *= stage_radix(N, s))
+    if (s > 1) off += (stage_radix(N, s) - 1) * s;
+  return off;
+}
+
+__host__ __device__ constexpr int tw_total(int N) { return tw_offset(N, N) > 0 ? tw_offset(N, N) : 1; }
+
+// fill the stage tables of a length-N transform from W_TWM^k, k < TWM (TWM a multiple of N)
+template <typename T, int N, int Ns, int TWM>
+struct FillTw {
+  static __device__ __forceinline__ void run(cx<T>* tw, const cx<T>* __restrict__ master) {
+    if constexpr (Ns < N) {
+      constexpr int R = stage_radix(N, Ns);
+      if constexpr (Ns > 1) {
+        constexpr int off = tw_offset(N, Ns);
+        for (int e = threadIdx.x; e < (R - 1) * Ns; e += blockDim.x) {
+          const int r = e / Ns + 1, jm = e - (r - 1) * Ns;
+          tw[off + e] = master[(jm * r * (N / (Ns * R))) * (TWM / N)];
+        }
+      }
+      FillTw<T, N, Ns * R, TWM>::run(tw, master);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Stockham stage: radix R, Ns = product of the previous radices
+// tw: the per-stage twiddle tables of this transform length (see FillTw)
+// ---------------------------------------------------------------------------
+template <typename T, int N, int R, int Ns, int SIGN>
 __device__ __forceinline__ void stockham_stage(cx<T>* s, int t, const cx<T>* __restrict__ tw, unsigned mask) {
   constexpr int E = ept(N);
   constexpr int TT = N / E;
@@ -191,9 +240,10 @@ __device__ __forceinline__ void stockham_stage(cx<T>* s, int t, const cx<T>* __r
     const int j = t + i * TT;
     const int jm = j & (Ns - 1);
     if constexpr (Ns > 1) {
+      const cx<T>* tws = tw + tw_offset(N, Ns) + jm;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        cx<T> w = tw[(jm * r * (N / (Ns * R))) * TWS];
+        cx<T> w = tws[(r - 1) * Ns];
         if constexpr (SIGN > 0) w.y = -w.y;
         v[i][r] = cmul(v[i][r], w);
       }
@@ -206,14 +256,13 @@ __device__ __forceinline__ void stockham_stage(cx<T>* s, int t, const cx<T>* __r
   if constexpr (TT > 1) __syncwarp(mask);
 }
 
-template <typename T, int N, int Ns, int SIGN, int TWS>
+template <typename T, int N, int Ns, int SIGN>
 struct Stockham {
   static __device__ __forceinline__ void run(cx<T>* s, int t, const cx<T>* tw, unsigned mask) {
     if constexpr (Ns < N) {
-      constexpr int E = ept(N);
-      constexpr int R = (N / Ns >= E) ? E : (N / Ns);
-      stockham_stage<T, N, R, Ns, SIGN, TWS>(s, t, tw, mask);
-      Stockham<T, N, Ns * R, SIGN, TWS>::run(s, t, tw, mask);
+      constexpr int R = stage_radix(N, Ns);
+      stockham_stage<T, N, R, Ns, SIGN>(s, t, tw, mask);
+      Stockham<T, N, Ns * R, SIGN>::run(s, t, tw, mask);
     }
   }
 };
@@ -221,10 +270,34 @@ struct Stockham {
 // Transform one padded shared-memory line of length N with thread t of N/E.
 // mask: the lanes of the calling warp that are transforming lines (each line's
 // N/E threads are consecutive lanes of one warp).
-template <typename T, int N, int SIGN, int TWS = 1>
+template <typename T, int N, int SIGN>
 __device__ __forceinline__ void fft_line(cx<T>* s, int t, const cx<T>* tw, unsigned mask) {
-  Stockham<T, N, 1, SIGN, TWS>::run(s, t, tw, mask);
+  Stockham<T, N, 1, SIGN>::run(s, t, tw, mask);
 }
+
+// ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (cp.async): the loads of a tile are all
+// in flight at once and do not pass through registers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "n"(BYTES));
+}
+
+// copy BYTES when pred, else write zeros to shared memory (no global access)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_pred(void* smem, const void* gmem, bool pred) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(smem)), "l"(gmem), "n"(BYTES),
+               "r"(pred ? BYTES : 0));
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // ---------------------------------------------------------------------------
 // reductions

@@ -26,22 +26,35 @@
 
 namespace acm {
 
-// dynamic shared memory of an x-pass kernel with NC component lines per line
-template <typename T, int N2, int NC>
-constexpr int x_smem_bytes() {
-  return (NC * (64 / ((N2 / 2) / ept(N2 / 2))) * line_stride(N2 / 2) + N2) * (int)sizeof(cx<T>);
-}
-
 // ---------------------------------------------------------------------------
 // x-pass configuration (real lines of length N2, complex FFT of length M = N2/2)
 // ---------------------------------------------------------------------------
-template <int N2>
+template <typename T, int N2>
 struct XCfg {
   static constexpr int M = N2 / 2;
   static constexpr int E = ept(M);
   static constexpr int TL = M / E;          // threads per line transform
   static constexpr int LPB = 64 / TL;       // lines per block
-  static constexpr int LS = line_stride(M); // complex slots per component line
+  static constexpr int LS = line_stride(M, TL, 0, wave_slots<T>());  // complex slots per component line
+};
+
+// dynamic shared memory of an x-pass kernel with NC component lines per line
+template <typename T, int N2, int NC>
+constexpr int x_smem_bytes() {
+  return (NC * XCfg<T, N2>::LPB * XCfg<T, N2>::LS + tw_total(N2 / 2) + N2 / 2 + 1) * (int)sizeof(cx<T>);
+}
+
+// Shared-memory layout of an x-pass block: NC component lines, the twiddle
+// tables, then (16-byte aligned) NR staged real fields of LPB*N2 values and
+// the staged indicator bytes.
+template <typename T, int N2, int NC, int NR>
+struct XLayout {
+  using C = XCfg<T, N2>;
+  static constexpr int TOT = C::LPB * N2;
+  static constexpr int TW = NC * C::LPB * C::LS;                         // complex offset of the twiddles
+  static constexpr int RB = ((TW + tw_total(C::M) + C::M + 1) * (int)sizeof(cx<T>) + 15) / 16 * 16;  // bytes
+  static constexpr int HB = RB + NR * TOT * (int)sizeof(T);              // byte offset of H
+  static constexpr int BYTES = HB + (NR > 0 ? TOT : 0);
 };
 
 template <typename T>
@@ -49,50 +62,46 @@ __device__ __forceinline__ T& re_at(cx<T>* line, int n) {
   return reinterpret_cast<T*>(&line[pad(n >> 1)])[n & 1];
 }
 
-// load TW table W_{N}^k, k < N, from the master table
-template <typename T, int N>
-__device__ __forceinline__ void load_tw(cx<T>* tw, const cx<T>* __restrict__ twg) {
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = twg[k * (TW_MAX / N)];
+// x-pass twiddles: stage tables of the length-N2/2 transform, then W_N2^k for
+// k in [0, N2/2] (real-to-complex post-processing) at tw + tw_total(N2/2)
+template <typename T, int N2>
+__device__ __forceinline__ void load_tw_x(cx<T>* tw, const cx<T>* __restrict__ twg) {
+  FillTw<T, N2 / 2, 1, TW_MAX>::run(tw, twg);
+  cx<T>* post = tw + tw_total(N2 / 2);
+  for (int k = threadIdx.x; k <= N2 / 2; k += blockDim.x) post[k] = twg[k * (TW_MAX / N2)];
 }
 
-// rows of NC components for LPB lines from the half spectrum into shared memory
+// contiguous real segment of n values (n * sizeof(T) a multiple of 16) into shared memory
+template <typename T>
+__device__ __forceinline__ void stage_real(T* dst, const T* __restrict__ src, int n) {
+  constexpr int V = 16 / (int)sizeof(T);
+  for (int i = threadIdx.x; i < n / V; i += blockDim.x) cp_async<16>(dst + i * V, src + i * V);
+}
+
+// Real transforms of length N2 run as complex transforms of length M = N2/2 on
+// z_j = x_{2j} + i x_{2j+1}, with W = exp(-2 pi i / N2):
+//   inverse: from the half spectrum X[0..M],
+//     Z_k = (X_k + conj X_{M-k}) + i (X_k - conj X_{M-k}) W^{-k},
+//     and the unnormalised inverse length-M transform of Z is N2 * z;
+//   forward: from Z = forward length-M transform of z,
+//     X_k = (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2, k = 0..M (Z_M = Z_0).
+//
+// x_load_spec_pre: rows of NC half-spectrum components read from global memory
+// and turned into Z[0..M-1] on the way into shared memory; each pair (k, M-k)
+// is loaded once and written once.
 template <typename T, int N2, int NC>
-__device__ __forceinline__ void x_load_spec(cx<T>* sm, const cx<T>* __restrict__ spec, long long S, int P,
-                                            int line0) {
-  using C = XCfg<N2>;
+__device__ __forceinline__ void x_load_spec_pre(cx<T>* sm, const cx<T>* __restrict__ spec, long long S, int P,
+                                                int line0, const cx<T>* twx) {
+  using C = XCfg<T, N2>;
+  constexpr int M = C::M;
+  const cx<T>* tw = twx + tw_total(M);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int cl = warp; cl < NC * C::LPB; cl += nw) {
     const int c = cl / C::LPB, l = cl - c * C::LPB;
     const cx<T>* src = spec + c * S + (long long)(line0 + l) * P;
-    cx<T>* dst = sm + cl * C::LS;
-    for (int k = lane; k <= C::M; k += 32) dst[pad(k)] = src[k];
-  }
-}
-
-template <typename T, int N2, int NC>
-__device__ __forceinline__ void x_store_spec(const cx<T>* sm, cx<T>* __restrict__ spec, long long S, int P,
-                                             int line0) {
-  using C = XCfg<N2>;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
-    const int c = cl / C::LPB, l = cl - c * C::LPB;
-    cx<T>* dst = spec + c * S + (long long)(line0 + l) * P;
-    const cx<T>* src = sm + cl * C::LS;
-    for (int k = lane; k <= C::M; k += 32) dst[k] = src[pad(k)];
-  }
-}
-
-// Half spectrum X[0..M] of a real line of length N2 -> Z[0..M-1] whose inverse
-// complex FFT of length M is z_j = N2 * (x_{2j} + i x_{2j+1}).
-template <typename T, int N2, int NC>
-__device__ __forceinline__ void x_c2r_pre(cx<T>* sm, const cx<T>* tw) {
-  using C = XCfg<N2>;
-  constexpr int M = C::M;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
     cx<T>* s = sm + cl * C::LS;
     for (int k = lane; k <= M / 2; k += 32) {
-      const cx<T> X = s[pad(k)], Y = s[pad(M - k)];
+      const cx<T> X = src[k], Y = src[M - k];
       const cx<T> e1 = X + cconj(Y), o1 = cmul(X - cconj(Y), cconj(tw[k]));
       const cx<T> e2 = Y + cconj(X), o2 = cmul(Y - cconj(X), cconj(tw[M - k]));
       s[pad(k)] = e1 + mul_i(o1);
@@ -101,27 +110,31 @@ __device__ __forceinline__ void x_c2r_pre(cx<T>* sm, const cx<T>* tw) {
   }
 }
 
-// Z[0..M-1] = forward FFT of z_j = x_{2j} + i x_{2j+1} -> half spectrum X[0..M].
+// x_post_store_spec: Z[0..M-1] in shared memory -> half spectrum X[0..M]
+// written to global memory.
 template <typename T, int N2, int NC>
-__device__ __forceinline__ void x_r2c_post(cx<T>* sm, const cx<T>* tw) {
-  using C = XCfg<N2>;
+__device__ __forceinline__ void x_post_store_spec(const cx<T>* sm, cx<T>* __restrict__ spec, long long S, int P,
+                                                  int line0, const cx<T>* twx) {
+  using C = XCfg<T, N2>;
   constexpr int M = C::M;
+  const cx<T>* tw = twx + tw_total(M);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const T half = (T)0.5;
   for (int cl = warp; cl < NC * C::LPB; cl += nw) {
-    cx<T>* s = sm + cl * C::LS;
+    const int c = cl / C::LPB, l = cl - c * C::LPB;
+    cx<T>* dst = spec + c * S + (long long)(line0 + l) * P;
+    const cx<T>* s = sm + cl * C::LS;
     for (int k = lane; k <= M / 2; k += 32) {
       const cx<T> Zk = s[pad(k)];
       if (k == 0) {
-        s[pad(0)] = mk<T>(Zk.x + Zk.y, (T)0);
-        s[pad(M)] = mk<T>(Zk.x - Zk.y, (T)0);
+        dst[0] = mk<T>(Zk.x + Zk.y, (T)0);
+        dst[M] = mk<T>(Zk.x - Zk.y, (T)0);
       } else {
         const cx<T> Zm = s[pad(M - k)];
         const cx<T> ak = cscale(Zk + cconj(Zm), half), bk = cscale(Zk - cconj(Zm), half);
         const cx<T> am = cscale(Zm + cconj(Zk), half), bm = cscale(Zm - cconj(Zk), half);
-        // X_k = a_k - i W^k b_k
-        s[pad(k)] = ak - mul_i(cmul(tw[k], bk));
-        s[pad(M - k)] = am - mul_i(cmul(tw[M - k], bm));
+        dst[k] = ak - mul_i(cmul(tw[k], bk));
+        dst[M - k] = am - mul_i(cmul(tw[M - k], bm));
       }
     }
   }
@@ -130,24 +143,33 @@ __device__ __forceinline__ void x_r2c_post(cx<T>* sm, const cx<T>* tw) {
 // complex FFT of length M on NC * LPB component lines, TL threads per line
 template <typename T, int N2, int NC, int SIGN>
 __device__ __forceinline__ void x_fft(cx<T>* sm, const cx<T>* tw) {
-  using C = XCfg<N2>;
+  using C = XCfg<T, N2>;
   const int job = threadIdx.x / C::TL;
   const unsigned mask = __ballot_sync(0xffffffffu, job < NC * C::LPB);
-  if (job < NC * C::LPB) fft_line<T, C::M, SIGN, 2>(sm + job * C::LS, threadIdx.x % C::TL, tw, mask);
+  if (job < NC * C::LPB) fft_line<T, C::M, SIGN>(sm + job * C::LS, threadIdx.x % C::TL, tw, mask);
 }
 
 // ---------------------------------------------------------------------------
 // Stokes x-pass 1: C2R of u^{n+1}, steps 2-3 of ADMM, residual partial sums
+//
+// The block's spectrum rows, u^n and H are staged into shared memory with
+// asynchronous copies; H lambda^n is then staged for the solid voxels only,
+// overlapping the inverse transform. The local step reads shared memory only.
 // ---------------------------------------------------------------------------
 template <typename T, int N2>
 __global__ void __launch_bounds__(3 * 64) k_x_stokes_local(const cx<T>* __restrict__ spec, T* __restrict__ u,
                                                           T* __restrict__ lam, const uint8_t* __restrict__ H,
                                                           StokesDev* __restrict__ prm, double* __restrict__ part,
                                                           Geo g, const cx<T>* __restrict__ twg) {
-  using C = XCfg<N2>;
+  using C = XCfg<T, N2>;
+  using Lay = XLayout<T, N2, 3, 6>;
+  constexpr int TOT = Lay::TOT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* tw = sm + 3 * C::LPB * C::LS;
+  cx<T>* tw = sm + Lay::TW;
+  T* su = reinterpret_cast<T*>(smem_raw + Lay::RB);   // [3][TOT] u^n
+  T* sl = su + 3 * TOT;                                // [3][TOT] H lambda^n
+  uint8_t* sh = smem_raw + Lay::HB;                    // [TOT] H
   __shared__ double red[5 * 32];
   const int p = blockIdx.y;
   StokesDev* P = prm + p;
@@ -157,34 +179,44 @@ __global__ void __launch_bounds__(3 * 64) k_x_stokes_local(const cx<T>* __restri
   const T s_prev = (T)(P->psi_prev[2] / (P->psi_prev[2] + P->psi_prev[0]));
   const T s_now = b / (b + alpha);
   const int line0 = blockIdx.x * C::LPB;
+  const long long v0 = (long long)line0 * N2;
   const cx<T>* sp = spec + (long long)p * 3 * g.S;
   T* up = u + (long long)p * 3 * g.V;
   T* lp = lam + (long long)p * 3 * g.V;
   const uint8_t* Hp = H + (long long)p * g.hs;
-  load_tw<T, N2>(tw, twg);
-  x_load_spec<T, N2, 3>(sm, sp, g.S, g.P, line0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) stage_real(su + c * TOT, up + c * g.V + v0, TOT);
+  for (int i = threadIdx.x; i < TOT / 16; i += blockDim.x) cp_async<16>(sh + 16 * i, Hp + v0 + 16 * i);
+  cp_async_commit();
+  load_tw_x<T, N2>(tw, twg);
   __syncthreads();
-  x_c2r_pre<T, N2, 3>(sm, tw);
+  x_load_spec_pre<T, N2, 3>(sm, sp, g.S, g.P, line0, tw);
+  cp_async_wait<0>();
   __syncthreads();
+  for (int i = threadIdx.x; i < 3 * TOT; i += blockDim.x) {
+    const int c = i / TOT, e = i - c * TOT;
+    cp_async_pred<(int)sizeof(T)>(sl + i, lp + c * g.V + v0 + e, sh[e] != 0);
+  }
+  cp_async_commit();
   x_fft<T, N2, 3, +1>(sm, tw);
+  cp_async_wait<0>();
   __syncthreads();
   T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-  for (int idx = threadIdx.x; idx < C::LPB * N2; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < TOT; idx += blockDim.x) {
     const int l = idx / N2, n = idx & (N2 - 1);
-    const long long v = (long long)(line0 + l) * N2 + n;
-    const bool solid = Hp[v] != 0;
+    const bool solid = sh[idx] != 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const T u1 = re_at(sm + (c * C::LPB + l) * C::LS, n);
-      const T u0 = up[c * g.V + v];
-      up[c * g.V + v] = u1;
+      const T u0 = su[c * TOT + idx];
+      up[c * g.V + v0 + idx] = u1;
       const T du = u1 - u0;
       a3 += du * du;
       if (solid) {
-        const T ut1 = s_now * u1;            // step 2 (Eq. 8) with a^n = H lambda^n
+        const T ut1 = s_now * u1;                 // step 2 (Eq. 8) with a^n = H lambda^n
         const T ut0 = s_prev * u0;
-        const T l1 = lp[c * g.V + v] + alpha * ut1;  // step 3 (Eq. 9)
-        lp[c * g.V + v] = l1;
+        const T l1 = sl[c * TOT + idx] + alpha * ut1;  // step 3 (Eq. 9)
+        lp[c * g.V + v0 + idx] = l1;
         const T dut = ut1 - ut0, dd = u1 - ut1;
         a0 += ut1 * ut1;
         a1 += dut * dut;
@@ -205,7 +237,7 @@ __global__ void __launch_bounds__(3 * 64) k_x_stokes_rhs(cx<T>* __restrict__ spe
                                                         const T* __restrict__ lam, const uint8_t* __restrict__ H,
                                                         const StokesDev* __restrict__ prm, Geo g,
                                                         const cx<T>* __restrict__ twg) {
-  using C = XCfg<N2>;
+  using C = XCfg<T, N2>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = sm + 3 * C::LPB * C::LS;
@@ -219,7 +251,7 @@ __global__ void __launch_bounds__(3 * 64) k_x_stokes_rhs(cx<T>* __restrict__ spe
   const T* up = u + (long long)p * 3 * g.V;
   const T* lp = lam + (long long)p * 3 * g.V;
   const uint8_t* Hp = H + (long long)p * g.hs;
-  load_tw<T, N2>(tw, twg);
+  load_tw_x<T, N2>(tw, twg);
   for (int idx = threadIdx.x; idx < C::LPB * N2; idx += blockDim.x) {
     const int l = idx / N2, n = idx & (N2 - 1);
     const long long v = (long long)(line0 + l) * N2 + n;
@@ -234,9 +266,7 @@ __global__ void __launch_bounds__(3 * 64) k_x_stokes_rhs(cx<T>* __restrict__ spe
   __syncthreads();
   x_fft<T, N2, 3, -1>(sm, tw);
   __syncthreads();
-  x_r2c_post<T, N2, 3>(sm, tw);
-  __syncthreads();
-  x_store_spec<T, N2, 3>(sm, sp, g.S, g.P, line0);
+  x_post_store_spec<T, N2, 3>(sm, sp, g.S, g.P, line0, tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -250,10 +280,14 @@ __global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, c
                                                     const uint8_t* __restrict__ H,
                                                     const SoluteDev* __restrict__ prm, Geo g,
                                                     const cx<T>* __restrict__ twg) {
-  using C = XCfg<N2>;
+  using C = XCfg<T, N2>;
+  using Lay = XLayout<T, N2, 4, 3>;
+  constexpr int TOT = Lay::TOT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* tw = sm + 4 * C::LPB * C::LS;
+  cx<T>* tw = sm + Lay::TW;
+  T* su = reinterpret_cast<T*>(smem_raw + Lay::RB);   // [3][TOT] u on pore voxels, 0 on solid ones
+  uint8_t* sh = smem_raw + Lay::HB;                    // [TOT] H
   const int p = blockIdx.y;
   const SoluteDev* P = prm + p;
   if (P->done) return;
@@ -261,27 +295,35 @@ __global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, c
   const T g0 = (T)P->g[0], g1 = (T)P->g[1], g2 = (T)P->g[2];
   const T B00 = (T)P->B0[0], B01 = (T)P->B0[1], B02 = (T)P->B0[2];
   const int line0 = blockIdx.x * C::LPB;
+  const long long v0 = (long long)line0 * N2;
   cx<T>* sp = spec + (long long)p * 4 * g.S;
   const T* up = u + (long long)p * g.us;
   const uint8_t* Hp = H + (long long)p * g.hs;
-  load_tw<T, N2>(tw, twg);
-  x_load_spec<T, N2, 3>(sm, sp, g.S, g.P, line0);
+  for (int i = threadIdx.x; i < TOT / 16; i += blockDim.x) cp_async<16>(sh + 16 * i, Hp + v0 + 16 * i);
+  cp_async_commit();
+  load_tw_x<T, N2>(tw, twg);
   __syncthreads();
-  x_c2r_pre<T, N2, 3>(sm, tw);
+  x_load_spec_pre<T, N2, 3>(sm, sp, g.S, g.P, line0, tw);
+  cp_async_wait<0>();
   __syncthreads();
+  for (int i = threadIdx.x; i < 3 * TOT; i += blockDim.x) {
+    const int c = i / TOT, e = i - c * TOT;
+    cp_async_pred<(int)sizeof(T)>(su + i, up + c * g.V + v0 + e, sh[e] == 0);
+  }
+  cp_async_commit();
   x_fft<T, N2, 3, +1>(sm, tw);
+  cp_async_wait<0>();
   __syncthreads();
-  for (int idx = threadIdx.x; idx < C::LPB * N2; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < TOT; idx += blockDim.x) {
     const int l = idx / N2, n = idx & (N2 - 1);
-    const long long v = (long long)(line0 + l) * N2 + n;
-    const bool solid = Hp[v] != 0;
+    const bool solid = sh[idx] != 0;
     T& r0 = re_at(sm + (0 * C::LPB + l) * C::LS, n);
     T& r1 = re_at(sm + (1 * C::LPB + l) * C::LS, n);
     T& r2 = re_at(sm + (2 * C::LPB + l) * C::LS, n);
     const T e0 = r0 + g0, e1 = r1 + g1, e2 = r2 + g2;
     const T Am = (solid ? eta : (T)1) - A0;
     T s = B00 * e0 + B01 * e1 + B02 * e2;
-    if (!solid) s += Fc - Pe * (up[v] * e0 + up[g.V + v] * e1 + up[2 * g.V + v] * e2);
+    if (!solid) s += Fc - Pe * (su[idx] * e0 + su[TOT + idx] * e1 + su[2 * TOT + idx] * e2);
     r0 = Am * e0;
     r1 = Am * e1;
     r2 = Am * e2;
@@ -290,9 +332,7 @@ __global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, c
   __syncthreads();
   x_fft<T, N2, 4, -1>(sm, tw);
   __syncthreads();
-  x_r2c_post<T, N2, 4>(sm, tw);
-  __syncthreads();
-  x_store_spec<T, N2, 4>(sm, sp, g.S, g.P, line0);
+  x_post_store_spec<T, N2, 4>(sm, sp, g.S, g.P, line0, tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -302,14 +342,14 @@ template <typename T, int N2, int NC>
 __global__ void __launch_bounds__(NC * 64) k_x_r2c(cx<T>* __restrict__ spec, const T* __restrict__ in, Geo g,
                                                   long long inProbStride, long long specProbStride,
                                                   const cx<T>* __restrict__ twg) {
-  using C = XCfg<N2>;
+  using C = XCfg<T, N2>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = sm + NC * C::LPB * C::LS;
   const int p = blockIdx.y;
   const int line0 = blockIdx.x * C::LPB;
   const T* ip = in + p * inProbStride;
-  load_tw<T, N2>(tw, twg);
+  load_tw_x<T, N2>(tw, twg);
   for (int idx = threadIdx.x; idx < NC * C::LPB * N2; idx += blockDim.x) {
     const int n = idx & (N2 - 1), cl = idx / N2;
     const int c = cl / C::LPB, l = cl - c * C::LPB;
@@ -318,26 +358,23 @@ __global__ void __launch_bounds__(NC * 64) k_x_r2c(cx<T>* __restrict__ spec, con
   __syncthreads();
   x_fft<T, N2, NC, -1>(sm, tw);
   __syncthreads();
-  x_r2c_post<T, N2, NC>(sm, tw);
-  __syncthreads();
-  x_store_spec<T, N2, NC>(sm, spec + p * specProbStride, g.S, g.P, line0);
+  x_post_store_spec<T, N2, NC>(sm, spec + p * specProbStride, g.S, g.P, line0, tw);
 }
 
 template <typename T, int N2, int NC>
 __global__ void __launch_bounds__(NC * 64) k_x_c2r(const cx<T>* __restrict__ spec, T* __restrict__ out, Geo g,
                                                   long long outProbStride, long long specProbStride,
                                                   const cx<T>* __restrict__ twg) {
-  using C = XCfg<N2>;
+  using C = XCfg<T, N2>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = sm + NC * C::LPB * C::LS;
   const int p = blockIdx.y;
   const int line0 = blockIdx.x * C::LPB;
   T* op = out + p * outProbStride;
-  load_tw<T, N2>(tw, twg);
-  x_load_spec<T, N2, NC>(sm, spec + p * specProbStride, g.S, g.P, line0);
+  load_tw_x<T, N2>(tw, twg);
   __syncthreads();
-  x_c2r_pre<T, N2, NC>(sm, tw);
+  x_load_spec_pre<T, N2, NC>(sm, spec + p * specProbStride, g.S, g.P, line0, tw);
   __syncthreads();
   x_fft<T, N2, NC, +1>(sm, tw);
   __syncthreads();
@@ -384,13 +421,13 @@ template <typename T, int N, int OP, int NC, int TX>
 struct SCfg {
   static constexpr int E = ept(N);
   static constexpr int TL = N / E;
-  static constexpr int LS = line_stride(N);
+  static constexpr int LS = line_stride(N, TL, TX, wave_slots<T>());
   static constexpr int JOBS = NC * TX;
   static constexpr int THREADS_ALL = JOBS * TL;
   static constexpr int ROUNDS = THREADS_ALL > 2048 ? 8 : THREADS_ALL > 1024 ? 4 : THREADS_ALL > 512 ? 2 : 1;
   // whole warps only: extra threads take no line but help with loads and stores
   static constexpr int NT = ((THREADS_ALL / ROUNDS) + 31) / 32 * 32;
-  static constexpr int SMEM = (NC * TX * LS + N) * (int)sizeof(cx<T>);
+  static constexpr int SMEM = (NC * TX * LS + tw_total(N)) * (int)sizeof(cx<T>);
 };
 
 template <typename T, int N, int OP, int NC, int TX, int SIGN, int NLINES>
@@ -401,7 +438,7 @@ __device__ __forceinline__ void s_fft(cx<T>* sm, const cx<T>* tw) {
   for (int r = 0; r < C::ROUNDS; ++r) {
     const int job = r * per_round + threadIdx.x / C::TL;
     const unsigned mask = __ballot_sync(0xffffffffu, job < NLINES);
-    if (job < NLINES) fft_line<T, N, SIGN, 1>(sm + job * C::LS, threadIdx.x % C::TL, tw, mask);
+    if (job < NLINES) fft_line<T, N, SIGN>(sm + job * C::LS, threadIdx.x % C::TL, tw, mask);
   }
 }
 
@@ -419,11 +456,14 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
   if (a.cprm && a.cprm[p].done) return;
   cx<T>* base = a.spec + p * a.probStride + outer * a.outerStride + kx0;
   const int w = min(TX, a.Pu - kx0);
-  load_tw<T, N>(tw, a.twg);
   for (int idx = threadIdx.x; idx < NIN * N * TX; idx += blockDim.x) {
     const int col = idx % TX, j = (idx / TX) % N, c = idx / (TX * N);
-    if (col < w) sm[(c * TX + col) * C::LS + pad(j)] = base[c * a.compStride + j * a.rowStride + col];
+    if (col < w)
+      cp_async<(int)sizeof(cx<T>)>(&sm[(c * TX + col) * C::LS + pad(j)], &base[c * a.compStride + j * a.rowStride + col]);
   }
+  cp_async_commit();
+  FillTw<T, N, 1, TW_MAX>::run(tw, a.twg);
+  cp_async_wait<0>();
   __syncthreads();
   if constexpr (OP == OP_INV || OP == OP_INV_SCALE) {
     if constexpr (OP == OP_INV_SCALE) {
@@ -458,78 +498,110 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
     const int ky = outer;
     const T d1 = a.sym.d1[ky], l1 = a.sym.l1[ky];
     T acc0 = 0, acc1 = 0, acc2 = 0;
-    for (int idx = threadIdx.x; idx < N * TX; idx += blockDim.x) {
-      const int col = idx % TX, j = idx / TX, kx = kx0 + col;
-      if (col >= w) continue;
-      const T d0 = a.sym.d0[j], l0 = a.sym.l0[j], d2 = a.sym.d2[kx], l2 = a.sym.l2[kx];
-      const T L = l0 + l1 + l2, dd = d0 * d0 + d1 * d1 + d2 * d2;
-      const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
-      const long long gi = (long long)p * a.compStride + (long long)j * a.rowStride + (long long)outer * a.outerStride + kx;
-      cx<T>* s0 = &sm[(0 * TX + col) * C::LS + pad(j)];
-      cx<T>* s1 = &sm[(1 * TX + col) * C::LS + pad(j)];
-      cx<T>* s2 = &sm[(2 * TX + col) * C::LS + pad(j)];
-      if constexpr (OP == OP_STOKES) {
-        const StokesDev& P = a.sprm[p];
-        const T nu = (T)P.nu, beta = (T)P.psi[1], b = (T)P.psi[2];
-        const cx<T> qh = a.st0[gi];
-        const cx<T> dprev = a.st1[gi];
-        // r = w^ - i d q^ (+ g V at k = 0)
-        const cx<T> iq = mul_i(qh);
-        cx<T> r0 = *s0 - cscale(iq, d0), r1 = *s1 - cscale(iq, d1), r2 = *s2 - cscale(iq, d2);
+    // hoisted parameters of the operator
+    T nu = 0, beta = 0, b = 0, A0 = 0, B00 = 0, B01 = 0, B02 = 0;
+    if constexpr (OP == OP_STOKES) {
+      nu = (T)a.sprm[p].nu;
+      beta = (T)a.sprm[p].psi[1];
+      b = (T)a.sprm[p].psi[2];
+    } else {
+      A0 = (T)a.cprm[p].A0;
+      B00 = (T)a.cprm[p].B0[0];
+      B01 = (T)a.cprm[p].B0[1];
+      B02 = (T)a.cprm[p].B0[2];
+    }
+    // The operator state (q^ and div^, or chi^) is read and rewritten in place:
+    // each chunk loads its state before any store (see k_x_stokes_local).
+    constexpr int TOT = N * TX, CH = 4;
+#pragma unroll 1
+    for (int base = 0; base < TOT; base += CH * C::NT) {
+      bool ok[CH];
+      long long gis[CH];
+      cx<T> sa[CH], sb[CH];
+#pragma unroll
+      for (int k = 0; k < CH; ++k) {
+        const int idx = base + k * C::NT + threadIdx.x;
+        const int col = idx % TX, j = idx / TX;
+        ok[k] = idx < TOT && col < w;
+        gis[k] = (long long)p * a.compStride + (long long)j * a.rowStride + (long long)outer * a.outerStride + kx0 + col;
+        sa[k] = ok[k] ? a.st0[gis[k]] : mk<T>(0, 0);
+        if constexpr (OP == OP_STOKES) sb[k] = ok[k] ? a.st1[gis[k]] : mk<T>(0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < CH; ++k) {
+        if (!ok[k]) continue;
+        const int idx = base + k * C::NT + threadIdx.x;
+        const int col = idx % TX, j = idx / TX, kx = kx0 + col;
+        const long long gi = gis[k];
+        const T d0 = a.sym.d0[j], l0 = a.sym.l0[j], d2 = a.sym.d2[kx], l2 = a.sym.l2[kx];
+        const T L = l0 + l1 + l2, dd = d0 * d0 + d1 * d1 + d2 * d2;
+        const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
         const bool k0 = (j == 0 && ky == 0 && kx == 0);
-        if (k0) {
-          const T Vt = (T)(1.0 / a.invV);
-          r0.x += (T)P.g[0] * Vt;
-          r1.x += (T)P.g[1] * Vt;
-          r2.x += (T)P.g[2] * Vt;
+        cx<T>* s0 = &sm[(0 * TX + col) * C::LS + pad(j)];
+        cx<T>* s1 = &sm[(1 * TX + col) * C::LS + pad(j)];
+        cx<T>* s2 = &sm[(2 * TX + col) * C::LS + pad(j)];
+        if constexpr (OP == OP_STOKES) {
+          const cx<T> qh = sa[k];
+          const cx<T> dprev = sb[k];
+          // r = w^ - i d q^ (+ g V at k = 0)
+          const cx<T> iq = mul_i(qh);
+          cx<T> r0 = *s0 - cscale(iq, d0), r1 = *s1 - cscale(iq, d1), r2 = *s2 - cscale(iq, d2);
+          if (k0) {
+            const StokesDev& P = a.sprm[p];
+            const T Vt = (T)(1.0 / a.invV);
+            r0.x += (T)P.g[0] * Vt;
+            r1.x += (T)P.g[1] * Vt;
+            r2.x += (T)P.g[2] * Vt;
+          }
+          // Eq. 13: (nu L + b) u^ + beta d (d.u^) = r, solved as
+          //   d.u^ = d.r / (c + beta |d|^2),  u^ = (r - beta d (d.u^)) / c,  c = nu L + b
+          const T c0 = nu * L + b;
+          const T ic0 = (T)1 / c0;
+          const cx<T> dr = cscale(r0, d0) + cscale(r1, d1) + cscale(r2, d2);
+          const cx<T> du = cscale(dr, (T)1 / (c0 + beta * dd));
+          const cx<T> f = cscale(du, beta);
+          const cx<T> u0 = cscale(r0 - cscale(f, d0), ic0);
+          const cx<T> u1 = cscale(r1 - cscale(f, d1), ic0);
+          const cx<T> u2 = cscale(r2 - cscale(f, d2), ic0);
+          // div u^ = i d.u^ (taken from the solve, free of the cancellation of
+          // summing d_c u^_c when beta is large); Eq. 9: q^ <- q^ - beta div u^
+          const cx<T> dv = mul_i(du);
+          const cx<T> qn = qh - cscale(dv, beta);
+          a.st0[gi] = qn;
+          a.st1[gi] = dv;
+          const cx<T> ddv = dv - dprev;
+          acc0 += wgt * cabs2(dv);
+          acc1 += wgt * cabs2(ddv);
+          acc2 += wgt * cabs2(qn);
+          if (k0) {
+            a.sprm[p].mean_u[0] = (double)u0.x * a.invV;
+            a.sprm[p].mean_u[1] = (double)u1.x * a.invV;
+            a.sprm[p].mean_u[2] = (double)u2.x * a.invV;
+          }
+          *s0 = cscale(u0, invV);
+          *s1 = cscale(u1, invV);
+          *s2 = cscale(u2, invV);
+        } else {
+          cx<T>* s3 = &sm[(3 * TX + col) * C::LS + pad(j)];
+          // F^ = s^ + i d.tau^  (Eq. 18 in Fourier space)
+          const cx<T> F = *s3 + mul_i(cscale(*s0, d0) + cscale(*s1, d1) + cscale(*s2, d2));
+          // Eq. 20: chi^ = F^ / (i B0.d + A0 L), chi^(0) = 0
+          const T dre = A0 * L, dim = B00 * d0 + B01 * d1 + B02 * d2;
+          cx<T> chi = mk<T>(0, 0);
+          if (!k0) {
+            const T den = (T)1 / (dre * dre + dim * dim);
+            chi = mk<T>((F.x * dre + F.y * dim) * den, (F.y * dre - F.x * dim) * den);
+          }
+          const cx<T> dch = chi - sa[k];
+          a.st0[gi] = chi;
+          acc0 += wgt * cabs2(dch);
+          acc1 += wgt * dd * cabs2(dch);
+          // grad chi^ = i d chi^, normalised for the inverse transform
+          const cx<T> ic = cscale(mul_i(chi), invV);
+          *s0 = cscale(ic, d0);
+          *s1 = cscale(ic, d1);
+          *s2 = cscale(ic, d2);
         }
-        // Eq. 13: (nu L + b) u^ + beta d (d.u^) = r
-        const T c0 = nu * L + b;
-        const T ic0 = (T)1 / c0;
-        const cx<T> dr = cscale(r0, d0) + cscale(r1, d1) + cscale(r2, d2);
-        const cx<T> f = cscale(dr, beta / (c0 + beta * dd));
-        const cx<T> u0 = cscale(r0 - cscale(f, d0), ic0);
-        const cx<T> u1 = cscale(r1 - cscale(f, d1), ic0);
-        const cx<T> u2 = cscale(r2 - cscale(f, d2), ic0);
-        // div u^ = i d.u^ ; Eq. 9: q^ <- q^ - beta div u^
-        const cx<T> dv = mul_i(cscale(u0, d0) + cscale(u1, d1) + cscale(u2, d2));
-        const cx<T> qn = qh - cscale(dv, beta);
-        a.st0[gi] = qn;
-        a.st1[gi] = dv;
-        const cx<T> ddv = dv - dprev;
-        acc0 += wgt * cabs2(dv);
-        acc1 += wgt * cabs2(ddv);
-        acc2 += wgt * cabs2(qn);
-        if (k0) {
-          a.sprm[p].mean_u[0] = (double)u0.x * a.invV;
-          a.sprm[p].mean_u[1] = (double)u1.x * a.invV;
-          a.sprm[p].mean_u[2] = (double)u2.x * a.invV;
-        }
-        *s0 = cscale(u0, invV);
-        *s1 = cscale(u1, invV);
-        *s2 = cscale(u2, invV);
-      } else {
-        const SoluteDev& P = a.cprm[p];
-        cx<T>* s3 = &sm[(3 * TX + col) * C::LS + pad(j)];
-        // F^ = s^ + i d.tau^  (Eq. 18 in Fourier space)
-        const cx<T> F = *s3 + mul_i(cscale(*s0, d0) + cscale(*s1, d1) + cscale(*s2, d2));
-        // Eq. 20: chi^ = F^ / (i B0.d + A0 L), chi^(0) = 0
-        const T dre = (T)P.A0 * L, dim = (T)P.B0[0] * d0 + (T)P.B0[1] * d1 + (T)P.B0[2] * d2;
-        const bool k0 = (j == 0 && ky == 0 && kx == 0);
-        cx<T> chi = mk<T>(0, 0);
-        if (!k0) {
-          const T den = (T)1 / (dre * dre + dim * dim);
-          chi = mk<T>((F.x * dre + F.y * dim) * den, (F.y * dre - F.x * dim) * den);
-        }
-        const cx<T> dch = chi - a.st0[gi];
-        a.st0[gi] = chi;
-        acc0 += wgt * cabs2(dch);
-        acc1 += wgt * dd * cabs2(dch);
-        // grad chi^ = i d chi^, normalised for the inverse transform
-        const cx<T> ic = cscale(mul_i(chi), invV);
-        *s0 = cscale(ic, d0);
-        *s1 = cscale(ic, d1);
-        *s2 = cscale(ic, d2);
       }
     }
     double v3[3] = {(double)acc0, (double)acc1, (double)acc2};

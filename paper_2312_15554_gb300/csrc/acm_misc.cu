@@ -55,13 +55,15 @@ __global__ void __launch_bounds__(256) k_stokes_finalize(StokesDev* __restrict__
   P->iter += 1;
   const int it = P->iter;
   if (hist && it + P->iter_base <= hist_cap) {
-    double* h = hist + ((long long)p * hist_cap + (it + P->iter_base - 1)) * 16;
+    double* h = hist + ((long long)p * hist_cap + (it + P->iter_base - 1)) * STOKES_HIST;
     for (int k = 0; k < 6; ++k) h[k] = r[k];
     for (int k = 0; k < 6; ++k) h[6 + k] = t[k];
     h[12] = alpha;
     h[13] = beta;
     h[14] = b;
-    h[15] = P->mean_u[0] * P->g[0] + P->mean_u[1] * P->g[1] + P->mean_u[2] * P->g[2];
+    for (int k = 0; k < 3; ++k) h[15 + k] = P->mean_u[k];
+    h[18] = 0.0;
+    h[19] = 0.0;
   }
   for (int k = 0; k < 3; ++k) {
     P->psi_last[k] = P->psi[k];
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(256) k_solute_finalize(SoluteDev* __restrict__
   P->iter += 1;
   const int it = P->iter;
   if (hist && it + P->iter_base <= hist_cap) {
-    double* h = hist + ((long long)p * hist_cap + (it + P->iter_base - 1)) * 4;
+    double* h = hist + ((long long)p * hist_cap + (it + P->iter_base - 1)) * SOLUTE_HIST;
     h[0] = r1;
     h[1] = r2;
     h[2] = t1;

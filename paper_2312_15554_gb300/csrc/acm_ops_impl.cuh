@@ -6,13 +6,14 @@
 
 namespace acm {
 
-// Tile width (kx columns) of a strided pass: the widest of 16, 8, 4, 2 whose
-// shared-memory tile lets two blocks share an SM.
+// Tile width (kx columns) of a strided pass: about 256 threads per block (many
+// resident blocks hide the memory latency better than wide tiles), at least 2
+// columns, and at most 64 KB of shared memory.
 constexpr int pick_tx(int csize, int N, int NC) {
-  return (NC * 16 * line_stride(N) * csize <= 110 * 1024)  ? 16
-         : (NC * 8 * line_stride(N) * csize <= 110 * 1024) ? 8
-         : (NC * 4 * line_stride(N) * csize <= 110 * 1024) ? 4
-                                                           : 2;
+  int tl = N / ept(N);
+  int tx = 16;
+  while (tx > 2 && (NC * tx * tl > 256 || NC * tx * line_stride(N, tl, tx, 128 / csize) * csize > 64 * 1024)) tx /= 2;
+  return tx;
 }
 
 template <typename K>
@@ -36,10 +37,10 @@ static cudaError_t set_smem(K* k, int bytes) {
 template <typename T, int N2>
 static cudaError_t l_x_local(const Geo& g, int nprob, const void* spec, void* u, void* lam, const uint8_t* H,
                              StokesDev* prm, double* part, const void* tw, cudaStream_t s) {
-  constexpr int smem = x_smem_bytes<T, N2, 3>();
+  constexpr int smem = XLayout<T, N2, 3, 6>::BYTES;
   static const cudaError_t attr = set_smem(k_x_stokes_local<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
-  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  dim3 grid(g.n0 * g.n1 / XCfg<T, N2>::LPB, nprob);
   k_x_stokes_local<T, N2><<<grid, 3 * 64, smem, s>>>((const cx<T>*)spec, (T*)u, (T*)lam, H, prm, part, g,
                                                      (const cx<T>*)tw);
   return cudaGetLastError();
@@ -51,7 +52,7 @@ static cudaError_t l_x_rhs(const Geo& g, int nprob, void* spec, const void* u, c
   constexpr int smem = x_smem_bytes<T, N2, 3>();
   static const cudaError_t attr = set_smem(k_x_stokes_rhs<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
-  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  dim3 grid(g.n0 * g.n1 / XCfg<T, N2>::LPB, nprob);
   k_x_stokes_rhs<T, N2><<<grid, 3 * 64, smem, s>>>((cx<T>*)spec, (const T*)u, (const T*)lam, H, prm, g,
                                                    (const cx<T>*)tw);
   return cudaGetLastError();
@@ -60,10 +61,10 @@ static cudaError_t l_x_rhs(const Geo& g, int nprob, void* spec, const void* u, c
 template <typename T, int N2>
 static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
                               const SoluteDev* prm, const void* tw, cudaStream_t s) {
-  constexpr int smem = x_smem_bytes<T, N2, 4>();
+  constexpr int smem = XLayout<T, N2, 4, 3>::BYTES;
   static const cudaError_t attr = set_smem(k_x_solute<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
-  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  dim3 grid(g.n0 * g.n1 / XCfg<T, N2>::LPB, nprob);
   k_x_solute<T, N2><<<grid, 4 * 64, smem, s>>>((cx<T>*)spec, (const T*)u, H, prm, g, (const cx<T>*)tw);
   return cudaGetLastError();
 }
@@ -74,7 +75,7 @@ static cudaError_t l_x_r2c_nc(const Geo& g, int nprob, void* spec, long long sps
   constexpr int smem = x_smem_bytes<T, N2, NC>();
   static const cudaError_t attr = set_smem(k_x_r2c<T, N2, NC>, smem);
   if (attr != cudaSuccess) return attr;
-  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  dim3 grid(g.n0 * g.n1 / XCfg<T, N2>::LPB, nprob);
   k_x_r2c<T, N2, NC><<<grid, NC * 64, smem, s>>>((cx<T>*)spec, (const T*)in, g, ips, sps, (const cx<T>*)tw);
   return cudaGetLastError();
 }
@@ -92,7 +93,7 @@ static cudaError_t l_x_c2r_nc(const Geo& g, int nprob, const void* spec, long lo
   constexpr int smem = x_smem_bytes<T, N2, NC>();
   static const cudaError_t attr = set_smem(k_x_c2r<T, N2, NC>, smem);
   if (attr != cudaSuccess) return attr;
-  dim3 grid(g.n0 * g.n1 / XCfg<N2>::LPB, nprob);
+  dim3 grid(g.n0 * g.n1 / XCfg<T, N2>::LPB, nprob);
   k_x_c2r<T, N2, NC><<<grid, NC * 64, smem, s>>>((const cx<T>*)spec, (T*)out, g, ops, sps, (const cx<T>*)tw);
   return cudaGetLastError();
 }

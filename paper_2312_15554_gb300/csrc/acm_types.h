@@ -3,6 +3,9 @@
 
 namespace acm {
 
+constexpr int STOKES_HIST = 20;  // doubles per Stokes history record
+constexpr int SOLUTE_HIST = 4;   // doubles per solute history record
+
 constexpr int TW_MAX = 1024;  // master twiddle table length (>= 2 * the largest axis)
 
 // ---------------------------------------------------------------------------

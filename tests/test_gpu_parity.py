@@ -21,8 +21,9 @@ def dev(x, dtype):
 
 
 def relerr(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
+    """Largest absolute difference relative to the largest magnitude of b."""
+    a = np.asarray(a)
+    b = np.asarray(b)
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
@@ -93,7 +94,9 @@ def test_stokes_fixed_iterations_match_oracle(lib, case, deriv, fp64):
     assert relerr(u, R.state.u) < tol
     assert relerr(p, R.p) < tol
     assert relerr(lam, R.state.lam) < tol
-    np.testing.assert_allclose(rep.res[:6], R.residuals[-1], rtol=1e-8 if fp64 else 1e-4)
+    # residuals are norms of differences of consecutive iterates: FP32 cancellation
+    # leaves them at ~1e-4 relative, FP64 at rounding level
+    np.testing.assert_allclose(rep.res[:6], R.residuals[-1], rtol=1e-8 if fp64 else 2e-3)
     assert relerr(K, R.state.u.reshape(3, -1).mean(axis=1)) < (1e-10 if fp64 else 1e-5)
 
 
@@ -274,3 +277,24 @@ def test_bench_workload_first_iterations_match_oracle(lib, n):
     assert relerr(u, R.state.u) < 1e-5
     assert relerr(lam, R.state.lam) < 1e-5
     assert relerr(p, R.p) < 1e-5
+
+
+def test_history_records_the_oracle_residuals_and_mean_velocity(lib):
+    H = I.sphere_pack((16, 16, 16), 0.5, 3.0, 7)[0]
+    g = [1.0, 0.0, 0.0]
+    n_it = 25
+    R = O.stokes(H, g, O.StokesParams(eps=0.0, adaptive=True, max_iter=n_it, alpha0=80, beta0=300, b0=150),
+                 record_mean_u=True)
+    ctx = lib.acm_ctx(H.shape)
+    u = torch.zeros((3,) + H.shape, dtype=torch.float64, device=DEV)
+    prm = lib.stokes_params(precision=lib.FP64, eps=0.0, max_iter=n_it, alpha0=80, beta0=300, b0=150,
+                            check_every=7)
+    s, K, rep = lib.acm_stokes(ctx, dev(H, torch.uint8), g, prm, None, None, u, None, None)
+    hist = lib.acm_history(ctx, 0)
+    ctx.close()
+    assert hist.shape == (n_it, 20)
+    np.testing.assert_allclose(hist[:, :6], R.residuals, rtol=1e-8, atol=1e-300)
+    np.testing.assert_allclose(hist[:, 6:12], R.tolerances, rtol=1e-10)
+    np.testing.assert_allclose(hist[:, 12:15], R.penalties, rtol=1e-12)
+    np.testing.assert_allclose(hist[:, 15:18], R.mean_u_hist, rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(hist[-1, 15:18], K, rtol=1e-9, atol=1e-14)
