@@ -161,6 +161,39 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def time_to_permeability(acm, ctx, Hd, stream, n_long):
+    """Seconds until the permeability tensor is within 1e-4 (Frobenius, relative) of
+    the tensor after n_long iterations, for the plain solve with default parameters.
+
+    The k = 0 Fourier coefficient of each Green solve gives the volume average of
+    u for every iteration (history), so the crossing iteration n* is found from one
+    long run; then exactly n* iterations are timed with CUDA events.
+    """
+    import torch
+    u3 = torch.zeros((3, 3) + tuple(Hd.shape), dtype=torch.float32, device=Hd.device)
+    prm = acm.stokes_params(eps=0.0, max_iter=n_long, precision=acm.FP32, check_every=500)
+    acm.acm_stokes_tensor(ctx, Hd, prm, u3)
+    hs = [acm.acm_history(ctx, j) for j in range(3)]
+    m = min(len(h) for h in hs)
+    Kn = np.stack([np.stack([hs[j][:m, 15 + i] for j in range(3)], axis=-1) for i in range(3)], axis=1)
+    Kref = Kn[-1]
+    err = np.linalg.norm(Kn - Kref, axis=(1, 2)) / np.linalg.norm(Kref)
+    bad = np.nonzero(err > 1e-4)[0]
+    n_star = int(bad[-1]) + 2 if len(bad) else 1
+    tail = float(np.linalg.norm(Kn[-1] - Kn[max(0, m - 1 - m // 10)]) / np.linalg.norm(Kref))
+    prm = acm.stokes_params(eps=0.0, max_iter=n_star, precision=acm.FP32, check_every=500)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    acm.acm_stokes_tensor(ctx, Hd, prm, u3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return {"seconds": e0.elapsed_time(e1) / 1e3, "iterations": n_star, "rel_err_target": 1e-4,
+            "reference_iterations": n_long, "reference_last10pct_change": tail,
+            "K_ref": Kref.tolist(), "form": "plain (FP32, adaptive penalties of Eq. 22, library defaults)"}
+
+
 def run_gpu(args, rank, world, dist):
     import torch
 
@@ -252,6 +285,8 @@ def run_gpu(args, rank, world, dist):
                          if v[1] and algorithmic_bytes_per_voxel(k, N, porosity) else None)}
             for k, v in prof.items() if v[1]}
 
+    ttk = time_to_permeability(acm, ctx, Hd, stream, args.ttk_long) if args.ttk else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         vi_c, s_c = oracle_sample(H, 1)
@@ -279,6 +314,8 @@ def run_gpu(args, rank, world, dist):
         "kernels": kern,
         "K_diag": [float(K[i, i]) for i in range(3)],
     }
+    if ttk is not None:
+        line["time_to_permeability"] = ttk
     print(json.dumps(line), flush=True)
 
 
@@ -290,6 +327,9 @@ def main():
     ap.add_argument("--iters", type=int, default=20, help="iterations per problem per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttk", action="store_true",
+                    help="also measure time-to-permeability (K within 1e-4 of a long-run reference)")
+    ap.add_argument("--ttk-long", type=int, default=20000, help="iterations of the reference run")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
