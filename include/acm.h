@@ -228,6 +228,35 @@ typedef enum acm_kernel_kind {
 acm_status acm_profile_enable(acm_ctx* ctx, int on);
 acm_status acm_profile_read(acm_ctx* ctx, double* ms, long long* launches);
 
+/* Size of the fixed device scratch array used by acm_fft_r2c_static. */
+#define ACM_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* acm_fft_r2c_static: the transform of acm_fft_r2c for one field, for callers
+ * that cannot let a library allocate device memory (an application that gives
+ * each component a fixed device-memory budget under its own allocator, or a
+ * latency-critical loop that must not call cudaMalloc/cudaFree, which can
+ * synchronise the device). It needs no context and allocates nothing: its
+ * working spectrum lives in a fixed __device__ array of
+ * ACM_STATIC_SCRATCH_BYTES that every GPU loading this library holds until the
+ * process exits. The paper has no counterpart; it is a deployment variant.
+ *   n0, n1, n2   grid, powers of two in [8, 512], with
+ *                n0 * n1 * (n2/2 + 4) * (8 or 16 bytes) <= ACM_STATIC_SCRATCH_BYTES
+ *                (128^3 in FP32, 128 x 128 x 64 in FP64); larger grids return
+ *                ACM_ERR_UNSUPPORTED_SIZE before any device work.
+ *   fp64         0: float input, 1: double input.
+ *   in           device pointer, real [n0][n1][n2]; out: device pointer,
+ *                complex interleaved [n0][n1][n2/2 + 1]; host pointers return
+ *                ACM_ERR_ARG.
+ *   cuda_stream  stream of the work (NULL = default stream); the call returns
+ *                once the work is enqueued.
+ * The first call on a device (with that device current) resolves the array's
+ * device address with cudaGetSymbolAddress and uploads a twiddle table with a
+ * synchronous copy; make that first call before any stream capture. Every call
+ * on a device shares the one array and overwrites every part of it that it
+ * later reads, so nothing has to start at zero; calls whose work overlaps on the
+ * GPU (other streams, other host threads) race on the array. */
+acm_status acm_fft_r2c_static(int n0, int n1, int n2, int fp64, const void* in, void* out, void* cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char* acm_status_str(acm_status s);
 

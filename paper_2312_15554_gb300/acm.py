@@ -24,7 +24,7 @@ FP32, FP64, FP32_THEN_FP64 = 0, 1, 2
 EXPORTED = (
     "acm_stokes_default_params", "acm_advdiff_default_params", "acm_create", "acm_destroy",
     "acm_stokes", "acm_stokes_tensor", "acm_advdiff", "acm_advdiff_tensor",
-    "acm_fft_r2c", "acm_fft_c2r", "acm_history", "acm_profile_enable", "acm_profile_read", "acm_status_str",
+    "acm_fft_r2c", "acm_fft_c2r", "acm_fft_r2c_static", "acm_history", "acm_profile_enable", "acm_profile_read", "acm_status_str",
 )
 
 KERNEL_KINDS = ("x_stokes_local", "x_stokes_rhs", "y_fwd_stokes", "z_stokes", "y_inv_stokes", "x_solute",
@@ -84,6 +84,7 @@ def load(path: str = None):
                                        C.POINTER(acm_report)]
     lib.acm_fft_r2c.argtypes = [vp, ip, ip, vp, vp]
     lib.acm_fft_c2r.argtypes = [vp, ip, ip, vp, vp]
+    lib.acm_fft_r2c_static.argtypes = [ip, ip, ip, ip, vp, vp, vp]
     lib.acm_history.argtypes = [vp, ip, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.acm_profile_enable.argtypes = [vp, ip]
     lib.acm_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
@@ -258,3 +259,10 @@ def acm_history(ctx, index: int = 0, cap: int = 20000):
     buf = (C.c_double * (k * ln.value))()
     _check(load().acm_history(ctx.h, int(index), buf, k, C.byref(n), C.byref(ln)), "acm_history")
     return np.array(buf[:]).reshape(k, ln.value)
+
+
+def acm_fft_r2c_static(x, out, fp64: bool, stream: int = 0):
+    """The allocation-free transform (no context; device buffers only)."""
+    n0, n1, n2 = (int(s) for s in x.shape[-3:])
+    _check(load().acm_fft_r2c_static(n0, n1, n2, int(fp64), _ptr(x), _ptr(out), C.c_void_p(stream)),
+           "acm_fft_r2c_static")
