@@ -54,7 +54,8 @@ struct XLayout {
   static constexpr int TW = NC * C::LPB * C::LS;                         // complex offset of the twiddles
   static constexpr int RB = ((TW + tw_total(C::M) + C::M + 1) * (int)sizeof(cx<T>) + 15) / 16 * 16;  // bytes
   static constexpr int HB = RB + NR * TOT * (int)sizeof(T);              // byte offset of H
-  static constexpr int BYTES = HB + (NR > 0 ? TOT : 0);
+  static constexpr int QB = (HB + (NR > 0 ? TOT : 0) + 15) / 16 * 16;    // byte offset of the Nyquist bins
+  static constexpr int BYTES = QB + NC * C::LPB * (int)sizeof(cx<T>);
 };
 
 template <typename T>
@@ -102,6 +103,42 @@ __device__ __forceinline__ void x_load_spec_pre(cx<T>* sm, const cx<T>* __restri
     cx<T>* s = sm + cl * C::LS;
     for (int k = lane; k <= M / 2; k += 32) {
       const cx<T> X = src[k], Y = src[M - k];
+      const cx<T> e1 = X + cconj(Y), o1 = cmul(X - cconj(Y), cconj(tw[k]));
+      const cx<T> e2 = Y + cconj(X), o2 = cmul(Y - cconj(X), cconj(tw[M - k]));
+      s[pad(k)] = e1 + mul_i(o1);
+      if (k != 0) s[pad(M - k)] = e2 + mul_i(o2);
+    }
+  }
+}
+
+// x_load_spec_raw_async: rows of NC half-spectrum components copied as they are
+// (cp.async) into the lines, X[M] into nyq[component line]; x_pre_smem then
+// turns them into Z[0..M-1] in place.
+template <typename T, int N2, int NC>
+__device__ __forceinline__ void x_load_spec_raw_async(cx<T>* sm, cx<T>* nyq, const cx<T>* __restrict__ spec,
+                                                      long long S, int P, int line0) {
+  using C = XCfg<T, N2>;
+  constexpr int M = C::M;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
+    const int c = cl / C::LPB, l = cl - c * C::LPB;
+    const cx<T>* src = spec + c * S + (long long)(line0 + l) * P;
+    cx<T>* dst = sm + cl * C::LS;
+    for (int k = lane; k < M; k += 32) cp_async<(int)sizeof(cx<T>)>(&dst[pad(k)], &src[k]);
+    if (lane == 0) cp_async<(int)sizeof(cx<T>)>(&nyq[cl], &src[M]);
+  }
+}
+
+template <typename T, int N2, int NC>
+__device__ __forceinline__ void x_pre_smem(cx<T>* sm, const cx<T>* nyq, const cx<T>* twx) {
+  using C = XCfg<T, N2>;
+  constexpr int M = C::M;
+  const cx<T>* tw = twx + tw_total(M);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
+    cx<T>* s = sm + cl * C::LS;
+    for (int k = lane; k <= M / 2; k += 32) {
+      const cx<T> X = s[pad(k)], Y = (k == 0) ? nyq[cl] : s[pad(M - k)];
       const cx<T> e1 = X + cconj(Y), o1 = cmul(X - cconj(Y), cconj(tw[k]));
       const cx<T> e2 = Y + cconj(X), o2 = cmul(Y - cconj(X), cconj(tw[M - k]));
       s[pad(k)] = e1 + mul_i(o1);
@@ -184,13 +221,13 @@ __global__ void __launch_bounds__(3 * 64) k_x_stokes_local(const cx<T>* __restri
   T* up = u + (long long)p * 3 * g.V;
   T* lp = lam + (long long)p * 3 * g.V;
   const uint8_t* Hp = H + (long long)p * g.hs;
+  cx<T>* nyq = reinterpret_cast<cx<T>*>(smem_raw + Lay::QB);
+  x_load_spec_raw_async<T, N2, 3>(sm, nyq, sp, g.S, g.P, line0);
 #pragma unroll
   for (int c = 0; c < 3; ++c) stage_real(su + c * TOT, up + c * g.V + v0, TOT);
   for (int i = threadIdx.x; i < TOT / 16; i += blockDim.x) cp_async<16>(sh + 16 * i, Hp + v0 + 16 * i);
   cp_async_commit();
   load_tw_x<T, N2>(tw, twg);
-  __syncthreads();
-  x_load_spec_pre<T, N2, 3>(sm, sp, g.S, g.P, line0, tw);
   cp_async_wait<0>();
   __syncthreads();
   for (int i = threadIdx.x; i < 3 * TOT; i += blockDim.x) {
@@ -198,6 +235,8 @@ __global__ void __launch_bounds__(3 * 64) k_x_stokes_local(const cx<T>* __restri
     cp_async_pred<(int)sizeof(T)>(sl + i, lp + c * g.V + v0 + e, sh[e] != 0);
   }
   cp_async_commit();
+  x_pre_smem<T, N2, 3>(sm, nyq, tw);
+  __syncthreads();
   x_fft<T, N2, 3, +1>(sm, tw);
   cp_async_wait<0>();
   __syncthreads();
@@ -299,11 +338,11 @@ __global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, c
   cx<T>* sp = spec + (long long)p * 4 * g.S;
   const T* up = u + (long long)p * g.us;
   const uint8_t* Hp = H + (long long)p * g.hs;
+  cx<T>* nyq = reinterpret_cast<cx<T>*>(smem_raw + Lay::QB);
+  x_load_spec_raw_async<T, N2, 3>(sm, nyq, sp, g.S, g.P, line0);
   for (int i = threadIdx.x; i < TOT / 16; i += blockDim.x) cp_async<16>(sh + 16 * i, Hp + v0 + 16 * i);
   cp_async_commit();
   load_tw_x<T, N2>(tw, twg);
-  __syncthreads();
-  x_load_spec_pre<T, N2, 3>(sm, sp, g.S, g.P, line0, tw);
   cp_async_wait<0>();
   __syncthreads();
   for (int i = threadIdx.x; i < 3 * TOT; i += blockDim.x) {
@@ -311,6 +350,8 @@ __global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, c
     cp_async_pred<(int)sizeof(T)>(su + i, up + c * g.V + v0 + e, sh[e] == 0);
   }
   cp_async_commit();
+  x_pre_smem<T, N2, 3>(sm, nyq, tw);
+  __syncthreads();
   x_fft<T, N2, 3, +1>(sm, tw);
   cp_async_wait<0>();
   __syncthreads();
@@ -620,26 +661,38 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
 // ---------------------------------------------------------------------------
 // FP64 reductions over real fields
 // ---------------------------------------------------------------------------
-// sums[p][0..2] = sum u_c ; [3..5] = sum over pore u_c ; [6] = pore voxels
+// sums[p][0..2] = sum u_c ; [3..5] = sum over pore u_c ; [6] = pore voxels.
+// FP64 arithmetic is scarce on this GPU: each thread sums chunks of CHK
+// elements in the field's precision and folds every chunk into FP64.
 template <typename T>
 __global__ void __launch_bounds__(256) k_field_sums(const T* __restrict__ u, const uint8_t* __restrict__ H, long long V,
                                                    long long us, long long hs, double* __restrict__ part) {
+  constexpr int CHK = 16;
   __shared__ double red[7 * 32];
   const int p = blockIdx.y;
   const T* up = u + (long long)p * us;
   const uint8_t* Hp = H + (long long)p * hs;
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-    const double a = up[v], b = up[V + v], c = up[2 * V + v];
-    acc[0] += a;
-    acc[1] += b;
-    acc[2] += c;
-    if (Hp[v] == 0) {
-      acc[3] += a;
-      acc[4] += b;
-      acc[5] += c;
-      acc[6] += 1.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; v0 < V; v0 += stride * CHK) {
+    T c[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int k = 0; k < CHK; ++k) {
+      const long long v = v0 + k * stride;
+      if (v >= V) break;
+      const T a = up[v], b = up[V + v], cc = up[2 * V + v];
+      c[0] += a;
+      c[1] += b;
+      c[2] += cc;
+      if (Hp[v] == 0) {
+        c[3] += a;
+        c[4] += b;
+        c[5] += cc;
+        c[6] += (T)1;
+      }
     }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) acc[k] += (double)c[k];
   }
   block_sum_store<7>(acc, red, part + ((long long)p * gridDim.x + blockIdx.x) * 8);
 }
@@ -652,6 +705,7 @@ __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ chi, 
                                                     const T* __restrict__ u, const uint8_t* __restrict__ H,
                                                     long long V, long long us, long long hs,
                                                     const SoluteDev* __restrict__ prm, double* __restrict__ part) {
+  constexpr int CHK = 16;
   __shared__ double red[6 * 32];
   const int p = blockIdx.y;
   const SoluteDev& P = prm[p];
@@ -659,18 +713,30 @@ __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ chi, 
   const T* gp = grad + (long long)p * 3 * V;
   const T* up = u + (long long)p * us;
   const uint8_t* Hp = H + (long long)p * hs;
+  const T Pe = (T)P.Pe, eta = (T)P.eta;
+  const T gg[3] = {(T)P.g[0], (T)P.g[1], (T)P.g[2]};
+  const T ub[3] = {(T)P.ubar[0], (T)P.ubar[1], (T)P.ubar[2]};
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-    const double c = cp[v];
-    const bool pore = Hp[v] == 0;
-    const double A = pore ? 1.0 : P.eta;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; v0 < V; v0 += stride * CHK) {
+    T c[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int k = 0; k < CHK; ++k) {
+      const long long v = v0 + k * stride;
+      if (v >= V) break;
+      const T ch = cp[v];
+      const bool pore = Hp[v] == 0;
+      const T A = pore ? (T)1 : eta;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const double gi = P.g[i] + (double)gp[i * V + v];
-      const double pe = pore ? P.Pe * (P.ubar[i] - (double)up[i * V + v]) * c : 0.0;
-      if (pore) acc[i] += gi + pe;
-      acc[3 + i] += A * gi + pe;
+      for (int i = 0; i < 3; ++i) {
+        const T gi = gg[i] + gp[i * V + v];
+        const T pe = pore ? Pe * (ub[i] - up[i * V + v]) * ch : (T)0;
+        if (pore) c[i] += gi + pe;
+        c[3 + i] += A * gi + pe;
+      }
     }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] += (double)c[k];
   }
   block_sum_store<6>(acc, red, part + ((long long)p * gridDim.x + blockIdx.x) * 8);
 }
@@ -680,17 +746,27 @@ __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ chi, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_pore_products(const T* __restrict__ f, const uint8_t* __restrict__ H,
                                                       long long V, double* __restrict__ part) {
+  constexpr int CHK = 16;
   __shared__ double red[6 * 32];
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-    if (H[v]) continue;
-    const double a = f[v], b = f[V + v], c = f[2 * V + v];
-    acc[0] += a * a;
-    acc[1] += a * b;
-    acc[2] += a * c;
-    acc[3] += b * b;
-    acc[4] += b * c;
-    acc[5] += c * c;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; v0 < V; v0 += stride * CHK) {
+    T c[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int k = 0; k < CHK; ++k) {
+      const long long v = v0 + k * stride;
+      if (v >= V) break;
+      if (H[v]) continue;
+      const T a = f[v], b = f[V + v], d = f[2 * V + v];
+      c[0] += a * a;
+      c[1] += a * b;
+      c[2] += a * d;
+      c[3] += b * b;
+      c[4] += b * d;
+      c[5] += d * d;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] += (double)c[k];
   }
   block_sum_store<6>(acc, red, part + (long long)blockIdx.x * 8);
 }
