@@ -93,6 +93,8 @@ typedef struct acm_stokes_params {
   int deriv;           /* acm_deriv (default ACM_DERIV_EXACT) */
   int precision;       /* acm_precision (default ACM_FP32) */
   int check_every;     /* iterations between host checks of the stop flag (default 16) */
+  int device_loop;     /* 1: the whole iteration loop is one device-resident CUDA graph
+                          launch (default); 0: host-launched chunks of check_every */
 } acm_stokes_params;
 
 /* Solute (Lippmann-Schwinger) parameters, Section 3.2. */
@@ -190,6 +192,31 @@ acm_status acm_advdiff_tensor(acm_ctx* ctx, const uint8_t* H, const void* u, dou
 acm_status acm_fft_r2c(acm_ctx* ctx, int fp64, int nbatch, const void* in, void* out);
 acm_status acm_fft_c2r(acm_ctx* ctx, int fp64, int nbatch, const void* in, void* out);
 
+/* Batched Stokes (the unit-cell problem of Section 2 for many cells at once):
+ * the three unit loads of every cell, solved in one device-resident loop. Cells
+ * of one shape share every kernel launch; each problem keeps its own penalties
+ * (Eq. 22) and stop flag, and converged problems stop doing work.
+ *   acm_batch_create  ncells cells with shapes dims[ncells][3] (host), each a
+ *                     power of two in [8, 512]; the workspace of all cells is
+ *                     allocated here (about 95 MB per 128^3 cell in FP32).
+ *   acm_batch_stokes  H: host array of ncells indicator pointers (device or
+ *                     host); prm: precision ACM_FP32 or ACM_FP64 (the mixed
+ *                     mode is not batched); u_out: nullable host array of
+ *                     ncells nullable pointers to [3 loads][3][V] (real type);
+ *                     K: host [ncells][9], row-major K[i][j] of each cell (NaN
+ *                     for a cell without solid or without pore voxels, whose
+ *                     reports carry ACM_ERR_NO_SOLID / ACM_ERR_NO_FLUID);
+ *                     rep: nullable host [ncells][3].
+ * Returns ACM_OK when every problem ran (check the per-problem statuses in rep). */
+typedef struct acm_batch acm_batch;
+acm_status acm_batch_create(acm_batch** batch, int ncells, const int* dims, void* cuda_stream);
+acm_status acm_batch_destroy(acm_batch* batch);
+acm_status acm_batch_stokes(acm_batch* batch, const uint8_t* const* H, const acm_stokes_params* prm,
+                            void* const* u_out, double* K, acm_report* rep);
+/* The profiler of acm_profile_enable / acm_profile_read over all cells of a batch. */
+acm_status acm_batch_profile_enable(acm_batch* batch, int on);
+acm_status acm_batch_profile_read(acm_batch* batch, double* ms, long long* launches);
+
 /* Convergence history of the last solve on this context for problem `index`
  * (0 for acm_stokes and acm_advdiff; the load index 0..2 for the tensor calls).
  * Copies up to `cap` records, record-major, into `out` (host) and returns the
@@ -256,6 +283,11 @@ acm_status acm_profile_read(acm_ctx* ctx, double* ms, long long* launches);
  * later reads, so nothing has to start at zero; calls whose work overlaps on the
  * GPU (other streams, other host threads) race on the array. */
 acm_status acm_fft_r2c_static(int n0, int n1, int n2, int fp64, const void* in, void* out, void* cuda_stream);
+
+/* Description of the last CUDA runtime failure seen by this thread in the
+ * library (empty if none): error name, message and the failing call. The
+ * string is thread-local and stays valid until the next failure. */
+const char* acm_last_error(void);
 
 /* Human-readable name of a status code (static string). */
 const char* acm_status_str(acm_status s);

@@ -24,7 +24,9 @@ FP32, FP64, FP32_THEN_FP64 = 0, 1, 2
 EXPORTED = (
     "acm_stokes_default_params", "acm_advdiff_default_params", "acm_create", "acm_destroy",
     "acm_stokes", "acm_stokes_tensor", "acm_advdiff", "acm_advdiff_tensor",
-    "acm_fft_r2c", "acm_fft_c2r", "acm_fft_r2c_static", "acm_history", "acm_profile_enable", "acm_profile_read", "acm_status_str",
+    "acm_fft_r2c", "acm_fft_c2r", "acm_fft_r2c_static", "acm_history",
+    "acm_batch_create", "acm_batch_destroy", "acm_batch_stokes", "acm_batch_profile_enable",
+    "acm_batch_profile_read", "acm_profile_enable", "acm_profile_read", "acm_last_error", "acm_status_str",
 )
 
 KERNEL_KINDS = ("x_stokes_local", "x_stokes_rhs", "y_fwd_stokes", "z_stokes", "y_inv_stokes", "x_solute",
@@ -35,7 +37,8 @@ class acm_stokes_params(C.Structure):
     _fields_ = [("nu", C.c_double), ("eps", C.c_double), ("alpha0", C.c_double), ("beta0", C.c_double),
                 ("b0", C.c_double), ("phi", C.c_double * 3), ("tau", C.c_double * 3),
                 ("psi_min_frac", C.c_double), ("eps32", C.c_double), ("max_iter", C.c_int),
-                ("adaptive", C.c_int), ("deriv", C.c_int), ("precision", C.c_int), ("check_every", C.c_int)]
+                ("adaptive", C.c_int), ("deriv", C.c_int), ("precision", C.c_int), ("check_every", C.c_int),
+                ("device_loop", C.c_int)]
 
 
 class acm_advdiff_params(C.Structure):
@@ -57,7 +60,10 @@ class acm_report(C.Structure):
 
 class AcmError(RuntimeError):
     def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: {status_str(status)} ({status})")
+        detail = ""
+        if status == -3:
+            detail = " [" + load().acm_last_error().decode(errors="replace") + "]"
+        super().__init__(f"{where}: {status_str(status)} ({status}){detail}")
         self.status = status
 
 
@@ -85,13 +91,21 @@ def load(path: str = None):
     lib.acm_fft_r2c.argtypes = [vp, ip, ip, vp, vp]
     lib.acm_fft_c2r.argtypes = [vp, ip, ip, vp, vp]
     lib.acm_fft_r2c_static.argtypes = [ip, ip, ip, ip, vp, vp, vp]
+    lib.acm_batch_create.argtypes = [C.POINTER(vp), ip, C.POINTER(C.c_int), vp]
+    lib.acm_batch_destroy.argtypes = [vp]
+    lib.acm_batch_stokes.argtypes = [vp, C.POINTER(vp), C.POINTER(acm_stokes_params), C.POINTER(vp), dp,
+                                     C.POINTER(acm_report)]
+    lib.acm_batch_profile_enable.argtypes = [vp, ip]
+    lib.acm_batch_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
     lib.acm_history.argtypes = [vp, ip, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.acm_profile_enable.argtypes = [vp, ip]
     lib.acm_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
+    lib.acm_last_error.argtypes = []
+    lib.acm_last_error.restype = cp
     lib.acm_status_str.argtypes = [ip]
     lib.acm_status_str.restype = cp
     for name in EXPORTED:
-        if name not in ("acm_status_str",):
+        if name not in ("acm_status_str", "acm_last_error"):
             getattr(lib, name).restype = C.c_int
     _LIB = lib
     return lib
@@ -266,3 +280,50 @@ def acm_fft_r2c_static(x, out, fp64: bool, stream: int = 0):
     n0, n1, n2 = (int(s) for s in x.shape[-3:])
     _check(load().acm_fft_r2c_static(n0, n1, n2, int(fp64), _ptr(x), _ptr(out), C.c_void_p(stream)),
            "acm_fft_r2c_static")
+
+
+class acm_batch:
+    """Owns an acm_batch* for cells of the given shapes (list of (n0, n1, n2))."""
+
+    def __init__(self, shapes, stream: int = 0):
+        lib = load()
+        self.shapes = [tuple(int(a) for a in sh) for sh in shapes]
+        dims = (C.c_int * (3 * len(self.shapes)))(*[a for sh in self.shapes for a in sh])
+        h = C.c_void_p()
+        _check(lib.acm_batch_create(C.byref(h), len(self.shapes), dims, C.c_void_p(stream)), "acm_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().acm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def acm_batch_stokes(batch, Hs, params=None, u_out=None):
+    """Returns (status, K [ncells, 3, 3], reports [ncells][3])."""
+    n = len(batch.shapes)
+    hp = (C.c_void_p * n)(*[_ptr(h) for h in Hs])
+    up = None if u_out is None else (C.c_void_p * n)(*[_ptr(u) for u in u_out])
+    K = (C.c_double * (9 * n))()
+    reps = (acm_report * (3 * n))()
+    s = load().acm_batch_stokes(batch.h, hp, C.byref(params or stokes_params()), up, K, reps)
+    _check(s, "acm_batch_stokes", allow_maxiter=True)
+    return s, np.array(K[:]).reshape(n, 3, 3), [list(reps[3 * i:3 * i + 3]) for i in range(n)]
+
+
+def acm_batch_profile_enable(batch, on: bool = True):
+    _check(load().acm_batch_profile_enable(batch.h, int(bool(on))), "acm_batch_profile_enable")
+
+
+def acm_batch_profile_read(batch):
+    k = len(KERNEL_KINDS)
+    ms = (C.c_double * k)()
+    cnt = (C.c_longlong * k)()
+    _check(load().acm_batch_profile_read(batch.h, ms, cnt), "acm_batch_profile_read")
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(KERNEL_KINDS)}

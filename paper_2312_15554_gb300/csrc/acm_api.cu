@@ -20,7 +20,7 @@ using namespace acm;
 
 namespace {
 
-constexpr int BMAX = 3;          // problems solved together by one context
+constexpr int BMAX = 3;          // problems of the single-cell entry points (three loads)
 constexpr int HIST_CAP = 20000;  // per-problem history records
 constexpr int NRED = 304;        // blocks of the FP64 field reductions
 
@@ -43,10 +43,21 @@ struct CxT {
 
 }  // namespace
 
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  int prec = -1, nprob = -1, deriv = -1, kind = -1;
+  unsigned cap = 0;
+  unsigned int* counter = nullptr;  // device iteration counter of the loop
+};
+
 struct acm_ctx {
   int n0, n1, n2;
   Geo g;
   cudaStream_t st;
+  int B = BMAX;       // problem capacity of the workspace
+  int ncells = 1;     // indicator slots in Hd (cells of a batch)
+  GraphCache graph;
+  cudaStream_t cap = nullptr;  // non-blocking stream used only to capture graphs
   Prec pf, pd;
   StokesDev* sprm = nullptr;
   SoluteDev* cprm = nullptr;
@@ -71,10 +82,18 @@ struct acm_ctx {
 
 namespace {
 
+thread_local char g_last_error[512] = "";
+
+void note_error(cudaError_t e, const char* what, int line) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at acm_api.cu:%d: %s", cudaGetErrorName(e),
+                cudaGetErrorString(e), line, what);
+}
+
 #define CK(x)                               \
   do {                                      \
     cudaError_t e_ = (x);                   \
     if (e_ != cudaSuccess) {                \
+      note_error(e_, #x, __LINE__);         \
       cudaGetLastError();                   \
       return ACM_ERR_CUDA;                  \
     }                                       \
@@ -115,6 +134,7 @@ void prof_end(acm_ctx* c) {
     cudaError_t e_ = (x);                   \
     prof_end(c);                            \
     if (e_ != cudaSuccess) {                \
+      note_error(e_, #x, __LINE__);         \
       cudaGetLastError();                   \
       return ACM_ERR_CUDA;                  \
     }                                       \
@@ -184,17 +204,17 @@ acm_status ensure_prec(acm_ctx* c) {
   const Geo& g = c->g;
   const size_t cs = 2 * sizeof(T);
   auto alloc = [&](void** p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
-  if (!alloc(&w.spec, (size_t)BMAX * 4 * g.S * cs) || !alloc(&w.st0, (size_t)BMAX * g.S * cs) ||
-      !alloc(&w.st1, (size_t)BMAX * g.S * cs) || !alloc(&w.u, (size_t)BMAX * 3 * g.V * sizeof(T)) ||
-      !alloc(&w.lam, (size_t)BMAX * 3 * g.V * sizeof(T)) || !alloc(&w.aux, (size_t)BMAX * 4 * g.V * sizeof(T)) ||
+  if (!alloc(&w.spec, (size_t)c->B * 4 * g.S * cs) || !alloc(&w.st0, (size_t)c->B * g.S * cs) ||
+      !alloc(&w.st1, (size_t)c->B * g.S * cs) || !alloc(&w.u, (size_t)c->B * 3 * g.V * sizeof(T)) ||
+      !alloc(&w.lam, (size_t)c->B * 3 * g.V * sizeof(T)) || !alloc(&w.aux, (size_t)c->B * 4 * g.V * sizeof(T)) ||
       !alloc(&w.tw, (size_t)TW_MAX * cs) || !alloc(&w.sym, 2 * sym_count<T>(g) * sizeof(T))) {
     cudaGetLastError();
     return ACM_ERR_NOMEM;
   }
   // zero the spectral padding columns once (they are never written by the passes)
-  CK(cudaMemset(w.spec, 0, (size_t)BMAX * 4 * g.S * cs));
-  CK(cudaMemset(w.st0, 0, (size_t)BMAX * g.S * cs));
-  CK(cudaMemset(w.st1, 0, (size_t)BMAX * g.S * cs));
+  CK(cudaMemset(w.spec, 0, (size_t)c->B * 4 * g.S * cs));
+  CK(cudaMemset(w.st0, 0, (size_t)c->B * g.S * cs));
+  CK(cudaMemset(w.st1, 0, (size_t)c->B * g.S * cs));
   std::vector<T> tw(2 * TW_MAX);
   const double PI = 3.14159265358979323846;
   for (int k = 0; k < TW_MAX; ++k) {
@@ -297,12 +317,14 @@ double default_penalty(const Geo& g, double nu) {
 }
 
 template <typename T>
-acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, const double (*gs)[3],
-                        const acm_stokes_params& P, double eps, const void* init_u, const void* init_lam) {
+acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int lph, const double (*gs)[3],
+                        const acm_stokes_params& P, double eps, const void* init_u, const void* init_lam,
+                        const int* preset_status = nullptr) {
   CKS(ensure_prec<T>(c));
   Prec& w = prec<T>(c);
   Geo g = c->g;
   g.hs = hs;
+  g.lph = lph;
   const size_t cs = 2 * sizeof(T);
   CK(cudaMemsetAsync(w.u, 0, (size_t)nprob * 3 * g.V * sizeof(T), c->st));
   CK(cudaMemsetAsync(w.lam, 0, (size_t)nprob * 3 * g.V * sizeof(T), c->st));
@@ -323,7 +345,7 @@ acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
     }
     if (init_lam) {
       CK(cudaMemcpyAsync(w.aux, init_lam, 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
-      LK(ACM_K_OTHER, Ops<T>::mask_solid(g, w.aux, lp, Hdev + (size_t)p * hs, c->st));
+      LK(ACM_K_OTHER, Ops<T>::mask_solid(g, w.aux, lp, Hdev + (size_t)(p / lph) * hs, c->st));
     }
   }
   std::vector<StokesDev> hp(nprob);
@@ -349,6 +371,10 @@ acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
     for (int k = 0; k < 3; ++k) d.psi_last[k] = d.psi[k];
     d.adaptive = P.adaptive;
     d.max_iter = P.max_iter;
+    if (preset_status && preset_status[p] != ACM_OK) {  // degenerate cell: not iterated
+      d.done = 1;
+      d.status = preset_status[p];
+    }
   }
   CK(cudaMemcpyAsync(c->sprm, hp.data(), nprob * sizeof(StokesDev), cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -357,10 +383,11 @@ acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
 
 // step 1 of the coming iteration (Eq. 7 / Eq. 13): w -> u^ -> u (up to the x-pass)
 template <typename T>
-acm_status stokes_step1(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, const Sym<T>& sym) {
+acm_status stokes_step1(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int lph, const Sym<T>& sym) {
   Prec& w = prec<T>(c);
   Geo g = c->g;
   g.hs = hs;
+  g.lph = lph;
   const long long ps = 3 * g.S;
   LK(ACM_K_X_STOKES_RHS, Ops<T>::x_stokes_rhs(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, w.tw, c->st));
   LK(ACM_K_Y_FWD_STOKES, Ops<T>::pass(g, 1, P_FWD, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, c->sprm, nullptr, nullptr, c->st));
@@ -369,28 +396,170 @@ acm_status stokes_step1(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
   return ACM_OK;
 }
 
-// Iterations of the device-resident loop. `remaining` bounds the iterations the
-// host launches (the finalize kernel also stops each problem at its max_iter),
-// so no launch is issued past the cap; problems that converge earlier turn the
-// rest of their launches into immediate returns.
+// One ADMM iteration of nprob problems after the previous one's step 1:
+// steps 2-4 (x pass + finalize), then step 1 of the next iteration.
 template <typename T>
-acm_status stokes_iterate(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int deriv, int check_every,
-                          int remaining) {
+acm_status stokes_body(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int lph, const Sym<T>& sym,
+                       bool last) {
   Prec& w = prec<T>(c);
   Geo g = c->g;
   g.hs = hs;
-  const Sym<T> sym = sym_of<T>(c, deriv);
+  g.lph = lph;
   const int nbx = Ops<T>::x_blocks(g), nbz = Ops<T>::z_blocks(g, P_STOKES);
-  CKS(stokes_step1<T>(c, nprob, Hdev, hs, sym));
-  CKS(pin_scratch(c, BMAX * sizeof(StokesDev)));
+  double* hist = nprob <= BMAX ? c->hist : nullptr;
+  LK(ACM_K_X_STOKES_LOCAL, Ops<T>::x_stokes_local(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, c->part_x, w.tw, c->st));
+  LK(ACM_K_FINALIZE, stokes_finalize(nprob, c->sprm, c->part_x, nbx, c->part_z, nbz, (double)g.V, hist, HIST_CAP, c->st));
+  if (!last) CKS(stokes_step1<T>(c, nprob, Hdev, hs, lph, sym));
+  return ACM_OK;
+}
+
+struct StokesGroup {
+  acm_ctx* c;
+  int nprob;
+  const uint8_t* H;
+  long long hs;
+  int lph;
+};
+
+// Device-resident loop: a CUDA graph whose while node repeats [step 1, steps
+// 2-4] of every group until all stop flags are set (or `cap` iterations); the
+// host launches it once and waits. The graph is cached in `cache` for reuse
+// while the key (precision, problems, symbols, kind) and the buffers are the same.
+template <typename T>
+acm_status stokes_graph_run(std::vector<StokesGroup>& grp, int deriv, unsigned cap, GraphCache& cache,
+                            cudaStream_t st) {
+  const int key_prec = (int)sizeof(T);
+  int total = 0;
+  for (auto& x : grp) total += x.nprob;
+  const bool valid = cache.exec && cache.prec == key_prec && cache.nprob == total && cache.deriv == deriv &&
+                     cache.kind == 1;
+  if (!valid) {
+    if (cache.exec) {
+      cudaGraphExecDestroy(cache.exec);
+      cache.exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    const cudaError_t eh = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    if (eh != cudaSuccess) {
+      note_error(eh, "cudaGraphConditionalHandleCreate", __LINE__);
+      cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return ACM_ERR_CUDA;
+    }
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = handle;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    const cudaError_t en = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (en != cudaSuccess) {
+      note_error(en, "cudaGraphAddNode(conditional while)", __LINE__);
+      cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return ACM_ERR_CUDA;
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    // capture on a private non-blocking stream (the caller's stream may be the
+    // legacy default stream, which cannot be captured); every group launches
+    // on it during the capture
+    cudaStream_t capst = grp[0].c->cap;
+    if (!capst) {
+      cudaGraphDestroy(graph);
+      return ACM_ERR_CUDA;
+    }
+    std::vector<cudaStream_t> saved;
+    for (auto& x : grp) {
+      saved.push_back(x.c->st);
+      x.c->st = capst;
+    }
+    const cudaError_t eb = cudaStreamBeginCaptureToGraph(capst, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (eb != cudaSuccess) {
+      for (size_t i = 0; i < grp.size(); ++i) grp[i].c->st = saved[i];
+      note_error(eb, "cudaStreamBeginCaptureToGraph", __LINE__);
+      cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return ACM_ERR_CUDA;
+    }
+    acm_status s = ACM_OK;
+    LoopCtl lc = {};
+    for (size_t i = 0; i < grp.size() && s == ACM_OK; ++i) {
+      StokesGroup& x = grp[i];
+      const Sym<T> sym = sym_of<T>(x.c, deriv);
+      s = stokes_step1<T>(x.c, x.nprob, x.H, x.hs, x.lph, sym);
+      if (s == ACM_OK) s = stokes_body<T>(x.c, x.nprob, x.H, x.hs, x.lph, sym, true);
+      lc.base[i] = (const char*)x.c->sprm;
+      lc.n[i] = x.nprob;
+      lc.stride[i] = (int)sizeof(StokesDev);
+    }
+    lc.ngroups = (int)grp.size();
+    lc.done_off = (int)offsetof(StokesDev, done);
+    lc.counter = cache.counter;
+    lc.cap = cap;
+    lc.handle = handle;
+    if (s == ACM_OK) {
+      const cudaError_t el = loop_control(lc, capst);
+      if (el != cudaSuccess) {
+        note_error(el, "loop_control", __LINE__);
+        s = ACM_ERR_CUDA;
+      }
+    }
+    cudaGraph_t captured = body;
+    const cudaError_t e = cudaStreamEndCapture(capst, &captured);
+    for (size_t i = 0; i < grp.size(); ++i) grp[i].c->st = saved[i];
+    if (s != ACM_OK || e != cudaSuccess) {
+      if (e != cudaSuccess) note_error(e, "cudaStreamEndCapture", __LINE__);
+      cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return s != ACM_OK ? s : ACM_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&cache.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      note_error(ei, "cudaGraphInstantiate", __LINE__);
+      cudaGetLastError();
+      cache.exec = nullptr;
+      return ACM_ERR_CUDA;
+    }
+    cache.prec = key_prec;
+    cache.nprob = total;
+    cache.deriv = deriv;
+    cache.kind = 1;
+    cache.cap = cap;
+  }
+  if (cache.cap != cap) {
+    // the cap is a kernel argument: rebuild with the new one
+    cache.nprob = -1;
+    return stokes_graph_run<T>(grp, deriv, cap, cache, st);
+  }
+  CK(cudaMemsetAsync(cache.counter, 0, sizeof(unsigned int), st));
+  CK(cudaGraphLaunch(cache.exec, st));
+  CK(cudaStreamSynchronize(st));
+  return ACM_OK;
+}
+
+// Iterations of the device-resident loop. With device_loop (and the profiler
+// off) the whole loop is one graph launch; otherwise the host launches chunks
+// of `check_every` iterations, reads the stop flags between chunks and never
+// launches past `remaining`; problems that converge earlier turn the rest of
+// their launches into immediate returns.
+template <typename T>
+acm_status stokes_iterate(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int lph, int deriv,
+                          int check_every, int remaining, bool device_loop) {
+  if (remaining <= 0) return ACM_OK;
+  if (device_loop && !c->prof) {
+    std::vector<StokesGroup> grp = {{c, nprob, Hdev, hs, lph}};
+    return stokes_graph_run<T>(grp, deriv, (unsigned)remaining, c->graph, c->st);
+  }
+  const Sym<T> sym = sym_of<T>(c, deriv);
+  CKS(stokes_step1<T>(c, nprob, Hdev, hs, lph, sym));
+  CKS(pin_scratch(c, (size_t)c->B * sizeof(StokesDev)));
   if (check_every < 1) check_every = 1;
   while (remaining > 0) {
     const int chunk = check_every < remaining ? check_every : remaining;
-    for (int k = 0; k < chunk; ++k) {
-      LK(ACM_K_X_STOKES_LOCAL, Ops<T>::x_stokes_local(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, c->part_x, w.tw, c->st));
-      LK(ACM_K_FINALIZE, stokes_finalize(nprob, c->sprm, c->part_x, nbx, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
-      if (remaining - k > 1) CKS(stokes_step1<T>(c, nprob, Hdev, hs, sym));
-    }
+    for (int k = 0; k < chunk; ++k) CKS(stokes_body<T>(c, nprob, Hdev, hs, lph, sym, remaining - k <= 1));
     remaining -= chunk;
     CK(cudaMemcpyAsync(c->pin, c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -491,7 +660,7 @@ acm_status stokes_reports(acm_ctx* c, int nprob, acm_report* rep, int fp64_from,
 }
 
 acm_status check_stokes_args(const acm_stokes_params& P) {
-  if (!(P.nu > 0) || !(P.eps >= 0) || P.max_iter < 1 || (P.deriv != 0 && P.deriv != 1) || P.precision < 0 ||
+  if (!(P.nu > 0) || !(P.eps >= 0) || P.max_iter < 1 || (P.device_loop != 0 && P.device_loop != 1) || (P.deriv != 0 && P.deriv != 1) || P.precision < 0 ||
       P.precision > 2 || !(P.psi_min_frac > 0) || !(P.eps32 > 0))
     return ACM_ERR_ARG;
   for (int k = 0; k < 3; ++k)
@@ -513,23 +682,25 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
   if (nsolid == 0) return ACM_ERR_NO_SOLID;
   if (nsolid == c->g.V) return ACM_ERR_NO_FLUID;
   if (Hdev != c->Hd) CK(cudaMemcpyAsync(c->Hd, Hdev, (size_t)c->g.V, cudaMemcpyDeviceToDevice, c->st));
+  Hdev = c->Hd;  // one stable buffer, so a cached device loop stays valid
+  const bool dl = P.device_loop != 0;
   acm_status st = ACM_OK;
   if (P.precision == ACM_FP32) {
-    CKS(stokes_setup<float>(c, nprob, Hdev, 0, gs, P, P.eps, init_u, init_lam));
-    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, P.deriv, P.check_every, P.max_iter));
+    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, P.eps, init_u, init_lam));
+    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     CKS(stokes_outputs<float>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
     st = stokes_reports(c, nprob, rep, -1, t0);
   } else if (P.precision == ACM_FP64) {
-    CKS(stokes_setup<double>(c, nprob, Hdev, 0, gs, P, P.eps, init_u, init_lam));
-    CKS(stokes_iterate<double>(c, nprob, Hdev, 0, P.deriv, P.check_every, P.max_iter));
+    CKS(stokes_setup<double>(c, nprob, Hdev, 0, 1, gs, P, P.eps, init_u, init_lam));
+    CKS(stokes_iterate<double>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
     st = stokes_reports(c, nprob, rep, -2, t0);
   } else {
     // FP32 iterations to eps32 (warm start given in double is cast on the host side by the caller)
     const double e32 = P.eps < P.eps32 ? P.eps32 : P.eps;
     if (init_u || init_lam) return ACM_ERR_ARG;  // warm starts are taken in the FP32 or FP64 modes
-    CKS(stokes_setup<float>(c, nprob, Hdev, 0, gs, P, e32, nullptr, nullptr));
-    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, P.deriv, P.check_every, P.max_iter));
+    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, e32, nullptr, nullptr));
+    CKS(stokes_iterate<float>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     std::vector<StokesDev> hp(nprob);
     CK(cudaMemcpy(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost));
     int it32 = hp[0].iter;
@@ -537,7 +708,7 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
     for (auto& x : hp) ok = ok && x.status == ACM_OK;
     if (ok && P.eps < e32) {
       CKS(stokes_promote(c, nprob, P.eps));
-      CKS(stokes_iterate<double>(c, nprob, Hdev, 0, P.deriv, P.check_every, P.max_iter - it32));
+      CKS(stokes_iterate<double>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter - it32, dl));
       CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
       st = stokes_reports(c, nprob, rep, it32, t0);
     } else {
@@ -622,7 +793,7 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
   }
   const int nbz = Ops<T>::z_blocks(g, P_SOLUTE);
   const long long ps = 4 * g.S;
-  CKS(pin_scratch(c, BMAX * sizeof(SoluteDev)));
+  CKS(pin_scratch(c, (size_t)c->B * sizeof(SoluteDev)));
   const int ce = P.check_every < 1 ? 1 : P.check_every;
   int remaining = P.max_iter - (setup ? 0 : iters_done);
   while (remaining > 0) {
@@ -657,7 +828,7 @@ acm_status solute_outputs(acm_ctx* c, int nprob, const uint8_t* Hdev, const void
   g.us = us;
   const Sym<T> sym = sym_of<T>(c, 0);
   T* grad = (T*)w.aux;
-  T* chi = (T*)w.aux + (size_t)BMAX * 3 * g.V;
+  T* chi = (T*)w.aux + (size_t)c->B * 3 * g.V;
   // grad chi^{n+1}: the last pass left i d chi^ (inverse along z and y) in components 0..2
   LK(ACM_K_OTHER, Ops<T>::x_c2r(g, nprob, 3, w.spec, 4 * g.S, grad, 3 * g.V, w.tw, c->st));
   // chi^{n+1}
@@ -816,6 +987,172 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
   return st;
 }
 
+
+// ---------------------------------------------------------------------------
+// batched Stokes: many cells, three loads each; cells of one shape share every
+// launch (one context per shape with room for 3 x cells problems)
+// ---------------------------------------------------------------------------
+struct BatchGroup {
+  int n[3];
+  std::vector<int> cells;
+  acm_ctx* c = nullptr;
+};
+
+}  // namespace
+
+struct acm_batch {
+  cudaStream_t st = nullptr;
+  int ncells = 0;
+  std::vector<BatchGroup> groups;
+  GraphCache graph;
+  unsigned long long* counts = nullptr;  // device [ncells] solid voxels
+};
+
+namespace {
+
+template <typename T>
+acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_stokes_params& P, void* const* u_out,
+                            double* K, acm_report* rep) {
+  const double t0 = now_ms();
+  // indicators into each group's cell slots, solid counts per cell
+  CK(cudaMemsetAsync(b->counts, 0, (size_t)b->ncells * sizeof(unsigned long long), b->st));
+  for (auto& gr : b->groups) {
+    const long long V = gr.c->g.V;
+    for (size_t i = 0; i < gr.cells.size(); ++i) {
+      const int cell = gr.cells[i];
+      if (!H[cell]) return ACM_ERR_ARG;
+      CK(cudaMemcpyAsync(gr.c->Hd + i * V, H[cell], (size_t)V, cudaMemcpyDefault, b->st));
+      CK(count_solid_add(gr.c->Hd + i * V, V, b->counts + cell, b->st));
+    }
+  }
+  std::vector<unsigned long long> cnt(b->ncells);
+  CK(cudaMemcpyAsync(cnt.data(), b->counts, cnt.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  // per-problem set-up (degenerate cells are reported, not iterated)
+  std::vector<StokesGroup> grp;
+  for (auto& gr : b->groups) {
+    const int nc = (int)gr.cells.size(), np = 3 * nc;
+    const long long V = gr.c->g.V;
+    std::vector<int> preset(np, ACM_OK);
+    std::vector<double> gs((size_t)np * 3, 0.0);
+    for (int p = 0; p < np; ++p) {
+      const unsigned long long ns = cnt[gr.cells[p / 3]];
+      preset[p] = ns == 0 ? ACM_ERR_NO_SOLID : (ns == (unsigned long long)V ? ACM_ERR_NO_FLUID : ACM_OK);
+      gs[(size_t)p * 3 + p % 3] = 1.0;
+    }
+    CKS(stokes_setup<T>(gr.c, np, gr.c->Hd, V, 3, reinterpret_cast<const double(*)[3]>(gs.data()), P, P.eps,
+                        nullptr, nullptr, preset.data()));
+    grp.push_back({gr.c, np, gr.c->Hd, V, 3});
+  }
+  bool prof = false;
+  for (auto& gr : b->groups) prof = prof || gr.c->prof;
+  if (P.device_loop && !prof) {
+    CKS(stokes_graph_run<T>(grp, P.deriv, (unsigned)P.max_iter, b->graph, b->st));
+  } else {
+    for (auto& x : grp)
+      CKS(stokes_iterate<T>(x.c, x.nprob, x.H, x.hs, x.lph, P.deriv, P.check_every, P.max_iter, false));
+  }
+  // outputs: K per cell (volume averages of the three loads), fields, reports
+  const double t1 = now_ms();
+  for (auto& gr : b->groups) {
+    acm_ctx* c = gr.c;
+    Prec& w = prec<T>(c);
+    Geo g = c->g;
+    g.us = 3 * g.V;
+    g.hs = 0;
+    const int nc = (int)gr.cells.size(), np = 3 * nc;
+    LK(ACM_K_OTHER, Ops<T>::field_sums(g, np, w.u, c->Hd, c->part_r, NRED, c->st));
+    std::vector<double> sums;
+    CKS(read_partials(c, np, 3, sums));
+    std::vector<StokesDev> hp(np);
+    CK(cudaMemcpyAsync(hp.data(), c->sprm, np * sizeof(StokesDev), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < nc; ++i) {
+      const int cell = gr.cells[i];
+      for (int j = 0; j < 3; ++j) {
+        const int p = 3 * i + j;
+        for (int r = 0; r < 3; ++r)
+          K[(size_t)cell * 9 + r * 3 + j] =
+              hp[p].status == ACM_ERR_NO_SOLID || hp[p].status == ACM_ERR_NO_FLUID ? NAN : sums[(size_t)p * 3 + r] / (double)g.V;
+        if (rep) {
+          acm_report& R = rep[(size_t)cell * 3 + j];
+          std::memset(&R, 0, sizeof(R));
+          R.iters = hp[p].iter;
+          R.iters_fp64 = sizeof(T) == 8 ? hp[p].iter : 0;
+          R.converged = hp[p].converged;
+          R.status = hp[p].status;
+          for (int k = 0; k < 6; ++k) {
+            R.res[k] = hp[p].res[k];
+            R.tol[k] = hp[p].tol[k];
+          }
+          for (int k = 0; k < 3; ++k) R.psi[k] = hp[p].psi_last[k];
+          R.time_ms = t1 - t0;
+        }
+      }
+      if (u_out && u_out[cell])
+        CK(cudaMemcpyAsync(u_out[cell], (T*)w.u + (size_t)3 * i * 3 * g.V, (size_t)9 * g.V * sizeof(T),
+                           cudaMemcpyDefault, c->st));
+    }
+  }
+  CK(cudaStreamSynchronize(b->st));
+  return ACM_OK;
+}
+
+// A context for grids of one shape with room for B problems (loads) and
+// `ncells` indicator grids (cells of a batch; problem p uses cell p / lph).
+acm_status ctx_create(acm_ctx** out, int n0, int n1, int n2, void* stream, int B, int ncells) {
+  if (!out || B < 1 || ncells < 1) return ACM_ERR_ARG;
+  *out = nullptr;
+  if (!pow2_in_range(n0) || !pow2_in_range(n1) || !pow2_in_range(n2)) return ACM_ERR_UNSUPPORTED_SIZE;
+  acm_ctx* c = new (std::nothrow) acm_ctx();
+  if (!c) return ACM_ERR_NOMEM;
+  c->n0 = n0;
+  c->n1 = n1;
+  c->n2 = n2;
+  c->B = B;
+  c->ncells = ncells;
+  Geo& g = c->g;
+  g.n0 = n0;
+  g.n1 = n1;
+  g.n2 = n2;
+  g.Pu = n2 / 2 + 1;
+  g.P = n2 / 2 + 4;  // rows start on 32-byte sectors for both precisions
+  g.V = (long long)n0 * n1 * n2;
+  g.S = (long long)n0 * n1 * g.P;
+  g.hs = 0;
+  g.us = 3 * g.V;
+  g.lph = 1;
+  c->st = (cudaStream_t)stream;
+  const int nbx = Ops<float>::x_blocks(g);
+  const int nbz = std::max(std::max(Ops<float>::z_blocks(g, P_STOKES), Ops<float>::z_blocks(g, P_SOLUTE)),
+                           std::max(Ops<double>::z_blocks(g, P_STOKES), Ops<double>::z_blocks(g, P_SOLUTE)));
+  c->nbx = nbx;
+  c->nbz = nbz;
+  bool ok = cudaMalloc(&c->sprm, (size_t)B * sizeof(StokesDev)) == cudaSuccess &&
+            cudaMalloc(&c->cprm, (size_t)B * sizeof(SoluteDev)) == cudaSuccess &&
+            cudaMalloc(&c->part_x, (size_t)B * nbx * 8 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->part_z, (size_t)B * nbz * 4 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->part_r, (size_t)B * NRED * 8 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->Hd, (size_t)ncells * g.V) == cudaSuccess &&
+            cudaMalloc(&c->cnt, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&c->graph.counter, sizeof(unsigned int)) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMalloc(&c->hist, (size_t)BMAX * HIST_CAP * STOKES_HIST * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    acm_destroy(c);
+    return ACM_ERR_NOMEM;
+  }
+  if (cudaMemset(c->sprm, 0, (size_t)B * sizeof(StokesDev)) != cudaSuccess ||
+      cudaMemset(c->cprm, 0, (size_t)B * sizeof(SoluteDev)) != cudaSuccess) {
+    cudaGetLastError();
+    acm_destroy(c);
+    return ACM_ERR_CUDA;
+  }
+  *out = c;
+  return ACM_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -840,6 +1177,7 @@ acm_status acm_stokes_default_params(acm_stokes_params* p) {
   p->deriv = ACM_DERIV_EXACT;
   p->precision = ACM_FP32;
   p->check_every = 16;
+  p->device_loop = 1;
   return ACM_OK;
 }
 
@@ -858,51 +1196,7 @@ acm_status acm_advdiff_default_params(acm_advdiff_params* p) {
 }
 
 acm_status acm_create(acm_ctx** out, int n0, int n1, int n2, void* stream) {
-  if (!out) return ACM_ERR_ARG;
-  *out = nullptr;
-  if (!pow2_in_range(n0) || !pow2_in_range(n1) || !pow2_in_range(n2)) return ACM_ERR_UNSUPPORTED_SIZE;
-  acm_ctx* c = new (std::nothrow) acm_ctx();
-  if (!c) return ACM_ERR_NOMEM;
-  c->n0 = n0;
-  c->n1 = n1;
-  c->n2 = n2;
-  Geo& g = c->g;
-  g.n0 = n0;
-  g.n1 = n1;
-  g.n2 = n2;
-  g.Pu = n2 / 2 + 1;
-  g.P = n2 / 2 + 4;  // rows start on 32-byte sectors for both precisions
-  g.V = (long long)n0 * n1 * n2;
-  g.S = (long long)n0 * n1 * g.P;
-  g.hs = 0;
-  g.us = 3 * g.V;
-  c->st = (cudaStream_t)stream;
-  const int nbx = Ops<float>::x_blocks(g);
-  const int nbz = std::max(std::max(Ops<float>::z_blocks(g, P_STOKES), Ops<float>::z_blocks(g, P_SOLUTE)),
-                           std::max(Ops<double>::z_blocks(g, P_STOKES), Ops<double>::z_blocks(g, P_SOLUTE)));
-  c->nbx = nbx;
-  c->nbz = nbz;
-  bool ok = cudaMalloc(&c->sprm, BMAX * sizeof(StokesDev)) == cudaSuccess &&
-            cudaMalloc(&c->cprm, BMAX * sizeof(SoluteDev)) == cudaSuccess &&
-            cudaMalloc(&c->part_x, (size_t)BMAX * nbx * 8 * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->part_z, (size_t)BMAX * nbz * 4 * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->part_r, (size_t)BMAX * NRED * 8 * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->Hd, (size_t)g.V) == cudaSuccess &&
-            cudaMalloc(&c->cnt, sizeof(unsigned long long)) == cudaSuccess &&
-            cudaMalloc(&c->hist, (size_t)BMAX * HIST_CAP * STOKES_HIST * sizeof(double)) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    acm_destroy(c);
-    return ACM_ERR_NOMEM;
-  }
-  if (cudaMemset(c->sprm, 0, BMAX * sizeof(StokesDev)) != cudaSuccess ||
-      cudaMemset(c->cprm, 0, BMAX * sizeof(SoluteDev)) != cudaSuccess) {
-    cudaGetLastError();
-    acm_destroy(c);
-    return ACM_ERR_CUDA;
-  }
-  *out = c;
-  return ACM_OK;
+  return ctx_create(out, n0, n1, n2, stream, BMAX, 1);
 }
 
 acm_status acm_destroy(acm_ctx* c) {
@@ -911,7 +1205,9 @@ acm_status acm_destroy(acm_ctx* c) {
   else cudaDeviceSynchronize();
   free_prec(c->pf);
   free_prec(c->pd);
-  void* ps[] = {c->sprm, c->cprm, c->part_x, c->part_z, c->part_r, c->Hd, c->cnt, c->hist};
+  if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  void* ps[] = {c->sprm, c->cprm, c->part_x, c->part_z, c->part_r, c->Hd, c->cnt, c->hist, c->graph.counter};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->pin) cudaFreeHost(c->pin);
@@ -1083,6 +1379,102 @@ acm_status acm_profile_read(acm_ctx* c, double* ms, long long* launches) {
   c->ev_used = 0;
   return ACM_OK;
 }
+
+acm_status acm_batch_create(acm_batch** out, int ncells, const int* dims, void* stream) {
+  if (!out || ncells < 1 || !dims) return ACM_ERR_ARG;
+  *out = nullptr;
+  acm_batch* b = new (std::nothrow) acm_batch();
+  if (!b) return ACM_ERR_NOMEM;
+  b->st = (cudaStream_t)stream;
+  b->ncells = ncells;
+  for (int i = 0; i < ncells; ++i) {
+    const int* d = dims + 3 * i;
+    if (!pow2_in_range(d[0]) || !pow2_in_range(d[1]) || !pow2_in_range(d[2])) {
+      delete b;
+      return ACM_ERR_UNSUPPORTED_SIZE;
+    }
+    BatchGroup* gr = nullptr;
+    for (auto& x : b->groups)
+      if (x.n[0] == d[0] && x.n[1] == d[1] && x.n[2] == d[2]) gr = &x;
+    if (!gr) {
+      b->groups.push_back(BatchGroup());
+      gr = &b->groups.back();
+      gr->n[0] = d[0];
+      gr->n[1] = d[1];
+      gr->n[2] = d[2];
+    }
+    gr->cells.push_back(i);
+  }
+  acm_status s = ACM_OK;
+  for (auto& gr : b->groups) {
+    s = ctx_create(&gr.c, gr.n[0], gr.n[1], gr.n[2], stream, 3 * (int)gr.cells.size(), (int)gr.cells.size());
+    if (s != ACM_OK) break;
+  }
+  if (s == ACM_OK && (cudaMalloc(&b->counts, (size_t)ncells * sizeof(unsigned long long)) != cudaSuccess ||
+                      cudaMalloc(&b->graph.counter, sizeof(unsigned int)) != cudaSuccess)) {
+    cudaGetLastError();
+    s = ACM_ERR_NOMEM;
+  }
+  if (s != ACM_OK) {
+    acm_batch_destroy(b);
+    return s;
+  }
+  *out = b;
+  return ACM_OK;
+}
+
+acm_status acm_batch_destroy(acm_batch* b) {
+  if (!b) return ACM_ERR_ARG;
+  if (b->st) cudaStreamSynchronize(b->st);
+  else cudaDeviceSynchronize();
+  for (auto& gr : b->groups)
+    if (gr.c) acm_destroy(gr.c);
+  if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
+  if (b->graph.counter) cudaFree(b->graph.counter);
+  if (b->counts) cudaFree(b->counts);
+  cudaGetLastError();
+  delete b;
+  return ACM_OK;
+}
+
+acm_status acm_batch_stokes(acm_batch* b, const uint8_t* const* H, const acm_stokes_params* prm, void* const* u_out,
+                            double* K, acm_report* rep) {
+  if (!b || !H || !K) return ACM_ERR_ARG;
+  acm_stokes_params P;
+  fill_stokes_params(prm, &P);
+  CKS(check_stokes_args(P));
+  if (P.precision == ACM_FP32_THEN_FP64) return ACM_ERR_ARG;
+  return P.precision == ACM_FP32 ? batch_stokes_run<float>(b, H, P, u_out, K, rep)
+                                 : batch_stokes_run<double>(b, H, P, u_out, K, rep);
+}
+
+acm_status acm_batch_profile_read(acm_batch* b, double* ms, long long* launches) {
+  if (!b) return ACM_ERR_ARG;
+  double acc[ACM_K_COUNT] = {};
+  long long cnt[ACM_K_COUNT] = {};
+  for (auto& gr : b->groups) {
+    double m[ACM_K_COUNT];
+    long long n[ACM_K_COUNT];
+    CKS(acm_profile_read(gr.c, m, n));
+    for (int k = 0; k < ACM_K_COUNT; ++k) {
+      acc[k] += m[k];
+      cnt[k] += n[k];
+    }
+  }
+  for (int k = 0; k < ACM_K_COUNT; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  return ACM_OK;
+}
+
+acm_status acm_batch_profile_enable(acm_batch* b, int on) {
+  if (!b) return ACM_ERR_ARG;
+  for (auto& gr : b->groups) acm_profile_enable(gr.c, on);
+  return ACM_OK;
+}
+
+const char* acm_last_error(void) { return g_last_error; }
 
 const char* acm_status_str(acm_status s) {
   switch (s) {

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(3 * 64) k_x_stokes_local(const cx<T>* __restri
   const cx<T>* sp = spec + (long long)p * 3 * g.S;
   T* up = u + (long long)p * 3 * g.V;
   T* lp = lam + (long long)p * 3 * g.V;
-  const uint8_t* Hp = H + (long long)p * g.hs;
+  const uint8_t* Hp = H + (long long)(p / g.lph) * g.hs;
   cx<T>* nyq = reinterpret_cast<cx<T>*>(smem_raw + Lay::QB);
   x_load_spec_raw_async<T, N2, 3>(sm, nyq, sp, g.S, g.P, line0);
 #pragma unroll
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(3 * 64) k_x_stokes_rhs(cx<T>* __restrict__ spe
   cx<T>* sp = spec + (long long)p * 3 * g.S;
   const T* up = u + (long long)p * 3 * g.V;
   const T* lp = lam + (long long)p * 3 * g.V;
-  const uint8_t* Hp = H + (long long)p * g.hs;
+  const uint8_t* Hp = H + (long long)(p / g.lph) * g.hs;
   load_tw_x<T, N2>(tw, twg);
   for (int idx = threadIdx.x; idx < C::LPB * N2; idx += blockDim.x) {
     const int l = idx / N2, n = idx & (N2 - 1);
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, c
   const long long v0 = (long long)line0 * N2;
   cx<T>* sp = spec + (long long)p * 4 * g.S;
   const T* up = u + (long long)p * g.us;
-  const uint8_t* Hp = H + (long long)p * g.hs;
+  const uint8_t* Hp = H + (long long)(p / g.lph) * g.hs;
   cx<T>* nyq = reinterpret_cast<cx<T>*>(smem_raw + Lay::QB);
   x_load_spec_raw_async<T, N2, 3>(sm, nyq, sp, g.S, g.P, line0);
   for (int i = threadIdx.x; i < TOT / 16; i += blockDim.x) cp_async<16>(sh + 16 * i, Hp + v0 + 16 * i);

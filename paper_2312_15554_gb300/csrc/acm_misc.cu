@@ -146,6 +146,28 @@ __global__ void k_count_solid(const uint8_t* __restrict__ H, long long V, unsign
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+__global__ void __launch_bounds__(256) k_loop_control(LoopCtl c) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int gi = 0; gi < c.ngroups; ++gi)
+    for (int i = threadIdx.x; i < c.n[gi]; i += blockDim.x)
+      mine |= (*reinterpret_cast<const int*>(c.base[gi] + (size_t)i * c.stride[gi] + c.done_off) == 0);
+  if (mine) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int it = *c.counter + 1;
+    *c.counter = it;
+    cudaGraphSetConditional(c.handle, (any && it < c.cap) ? 1u : 0u);
+  }
+}
+
+cudaError_t loop_control(const LoopCtl& c, cudaStream_t s) {
+  k_loop_control<<<1, 256, 0, s>>>(c);
+  return cudaGetLastError();
+}
+
 cudaError_t stokes_finalize(int nprob, StokesDev* prm, const double* part_x, int nbx, const double* part_z,
                             int nbz, double V, double* hist, int hist_cap, cudaStream_t s) {
   k_stokes_finalize<<<nprob, 256, 0, s>>>(prm, part_x, nbx, part_z, nbz, V, hist, hist_cap);
@@ -161,6 +183,11 @@ cudaError_t solute_finalize(int nprob, SoluteDev* prm, const double* part_z, int
 cudaError_t count_solid(const uint8_t* H, long long V, unsigned long long* out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  k_count_solid<<<304, 256, 0, s>>>(H, V, out);
+  return cudaGetLastError();
+}
+
+cudaError_t count_solid_add(const uint8_t* H, long long V, unsigned long long* out, cudaStream_t s) {
   k_count_solid<<<304, 256, 0, s>>>(H, V, out);
   return cudaGetLastError();
 }

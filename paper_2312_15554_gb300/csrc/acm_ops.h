@@ -54,5 +54,22 @@ cudaError_t stokes_finalize(int nprob, StokesDev* prm, const double* part_x, int
 cudaError_t solute_finalize(int nprob, SoluteDev* prm, const double* part_z, int nbz, double V, double* hist,
                             int hist_cap, cudaStream_t s);
 cudaError_t count_solid(const uint8_t* H, long long V, unsigned long long* out, cudaStream_t s);
+cudaError_t count_solid_add(const uint8_t* H, long long V, unsigned long long* out, cudaStream_t s);
+
+// Condition of the device-resident loop (a CUDA graph while node): continue
+// while any problem of any group has not set its stop flag, and at most `cap`
+// iterations. Group g has n[g] control blocks of `stride` bytes starting at
+// base[g]; the stop flag is the int at byte offset `done_off` of each block.
+struct LoopCtl {
+  const char* base[4];
+  int n[4];
+  int stride[4];
+  int ngroups;
+  int done_off;
+  unsigned int* counter;  // iterations run so far (device)
+  unsigned int cap;
+  cudaGraphConditionalHandle handle;
+};
+cudaError_t loop_control(const LoopCtl& c, cudaStream_t s);
 
 }  // namespace acm

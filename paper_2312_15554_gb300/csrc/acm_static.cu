@@ -131,6 +131,7 @@ extern "C" acm_status acm_fft_r2c_static(int n0, int n1, int n2, int fp64, const
   g.S = (long long)n0 * n1 * g.P;
   g.hs = 0;
   g.us = 0;
+  g.lph = 1;
   const size_t need = (size_t)g.S * (fp64 ? 2 * sizeof(double) : 2 * sizeof(float));
   if (need > STATIC_SCRATCH_BYTES) return ACM_ERR_UNSUPPORTED_SIZE;
   if (!on_device(in) || !on_device(out)) return ACM_ERR_ARG;

@@ -50,6 +50,7 @@ struct Geo {
   long long S;  // complex elements of one spectral component: n0 * n1 * P
   long long hs; // stride of H between problems of a batch (0: one shared H)
   long long us; // stride of the advecting velocity between problems (0: shared)
+  int lph;      // problems per indicator: problem p uses H + (p / lph) * hs
 };
 
 // Symbols of one precision: d and L per axis (axis 2 only up to n2/2).
