@@ -319,6 +319,79 @@ def run_gpu(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def _batched_cell(i):
+    """Cell i of the batched workload: 64^3 for even i, 128^3 for odd i."""
+    from paper_2312_15554_gb300 import inputs as I
+    n = 64 if i % 2 == 0 else 128
+    por, radii = I.cell_recipe(5000 + i)
+    return I.sphere_pack((n, n, n), por, radii, 5000 + i)[0]
+
+
+def run_batched(args, rank, world, dist):
+    """Many cells in one device-resident solve (Stokes, three loads per cell)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    idx = list(range(rank * args.cells, (rank + 1) * args.cells))
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        Hs = list(ex.map(_batched_cell, idx, chunksize=4))
+    import torch
+
+    from paper_2312_15554_gb300 import acm
+    from paper_2312_15554_gb300 import build as B
+    B.build()
+    acm.load()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    shapes = [h.shape for h in Hs]
+    Hd = [torch.as_tensor(h, device=dev) for h in Hs]
+    batch = acm.acm_batch(shapes, stream.cuda_stream)
+    prm = acm.stokes_params(eps=0.0, max_iter=args.iters, precision=acm.FP32)
+    vi = sum(int(np.prod(sh)) for sh in shapes) * 3 * args.iters
+    for _ in range(args.warmup):
+        acm.acm_batch_stokes(batch, Hd, prm)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s, K, reps = acm.acm_batch_stokes(batch, Hd, prm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    # per-kernel shares of one more step, host-launched with CUDA events
+    acm.acm_batch_profile_read(batch)
+    acm.acm_batch_profile_enable(batch, True)
+    acm.acm_batch_stokes(batch, Hd, prm)
+    prof = acm.acm_batch_profile_read(batch)
+    acm.acm_batch_profile_enable(batch, False)
+    batch.close()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": vi * args.steps * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: {len(shapes)} cells (half 64^3, half 128^3), 3 loads each, "
+                               "porosity U[0.2,0.6], radii U[3,10] vox", "iters_per_step": args.iters,
+                   "device_loop": "CUDA graph while node"},
+        "clocks": clocks,
+        "kernels_profiled_step": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]},
+        "K_mean_diag_cell0": [float(K[0, i, i]) for i in range(3)],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,6 +403,9 @@ def main():
     ap.add_argument("--ttk", action="store_true",
                     help="also measure time-to-permeability (K within 1e-4 of a long-run reference)")
     ap.add_argument("--ttk-long", type=int, default=20000, help="iterations of the reference run")
+    ap.add_argument("--config", default="cell256", choices=["cell256", "batched"],
+                    help="cell256: the 256^3 cell (default); batched: 384 cells (192 at 64^3, 192 at 128^3)")
+    ap.add_argument("--cells", type=int, default=384, help="cells of the batched configuration")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -343,7 +419,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         tdist.init_process_group("nccl")
         dist = tdist
-    run_gpu(args, rank, world, dist)
+    if args.config == "batched":
+        run_batched(args, rank, world, dist)
+    else:
+        run_gpu(args, rank, world, dist)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -31,7 +31,7 @@ struct Prec {
   void* st1 = nullptr;   // [BMAX][S] complex: div^ of the previous iteration
   void* u = nullptr;     // [BMAX][3][V] real
   void* lam = nullptr;   // [BMAX][3][V] real: H lambda
-  void* aux = nullptr;   // [BMAX][4][V] real: grad chi [B][3][V], then chi [B][V]
+  void* aux = nullptr;   // [B][4][V] real, allocated on first use: staging, grad chi [B][3][V], chi [B][V]
   void* tw = nullptr;    // [TW_MAX] complex twiddles W_1024^k
   void* sym = nullptr;   // two symbol sets (EXACT, CENTRAL)
 };
@@ -56,6 +56,7 @@ struct acm_ctx {
   cudaStream_t st;
   int B = BMAX;       // problem capacity of the workspace
   int ncells = 1;     // indicator slots in Hd (cells of a batch)
+  int spec_comps = 4; // spectral components per problem (3 suffice for Stokes-only batches)
   GraphCache graph;
   cudaStream_t cap = nullptr;  // non-blocking stream used only to capture graphs
   Prec pf, pd;
@@ -204,15 +205,15 @@ acm_status ensure_prec(acm_ctx* c) {
   const Geo& g = c->g;
   const size_t cs = 2 * sizeof(T);
   auto alloc = [&](void** p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
-  if (!alloc(&w.spec, (size_t)c->B * 4 * g.S * cs) || !alloc(&w.st0, (size_t)c->B * g.S * cs) ||
+  if (!alloc(&w.spec, (size_t)c->B * c->spec_comps * g.S * cs) || !alloc(&w.st0, (size_t)c->B * g.S * cs) ||
       !alloc(&w.st1, (size_t)c->B * g.S * cs) || !alloc(&w.u, (size_t)c->B * 3 * g.V * sizeof(T)) ||
-      !alloc(&w.lam, (size_t)c->B * 3 * g.V * sizeof(T)) || !alloc(&w.aux, (size_t)c->B * 4 * g.V * sizeof(T)) ||
-      !alloc(&w.tw, (size_t)TW_MAX * cs) || !alloc(&w.sym, 2 * sym_count<T>(g) * sizeof(T))) {
+      !alloc(&w.lam, (size_t)c->B * 3 * g.V * sizeof(T)) || !alloc(&w.tw, (size_t)TW_MAX * cs) ||
+      !alloc(&w.sym, 2 * sym_count<T>(g) * sizeof(T))) {
     cudaGetLastError();
     return ACM_ERR_NOMEM;
   }
   // zero the spectral padding columns once (they are never written by the passes)
-  CK(cudaMemset(w.spec, 0, (size_t)c->B * 4 * g.S * cs));
+  CK(cudaMemset(w.spec, 0, (size_t)c->B * c->spec_comps * g.S * cs));
   CK(cudaMemset(w.st0, 0, (size_t)c->B * g.S * cs));
   CK(cudaMemset(w.st1, 0, (size_t)c->B * g.S * cs));
   std::vector<T> tw(2 * TW_MAX);
@@ -237,6 +238,20 @@ acm_status ensure_prec(acm_ctx* c) {
   }
   CK(cudaMemcpy(w.sym, sym.data(), sym.size() * sizeof(T), cudaMemcpyHostToDevice));
   w.ready = true;
+  return ACM_OK;
+}
+
+// the auxiliary real buffer (staging of host inputs, solute and pressure outputs)
+template <typename T>
+acm_status ensure_aux(acm_ctx* c) {
+  CKS(ensure_prec<T>(c));
+  Prec& w = prec<T>(c);
+  if (w.aux) return ACM_OK;
+  if (cudaMalloc(&w.aux, (size_t)c->B * 4 * c->g.V * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    w.aux = nullptr;
+    return ACM_ERR_NOMEM;
+  }
   return ACM_OK;
 }
 
@@ -344,6 +359,7 @@ acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
       LK(ACM_K_OTHER, Ops<T>::div_spec(g, sp, (char*)w.st1 + (size_t)p * g.S * cs, sym, c->st));
     }
     if (init_lam) {
+      CKS(ensure_aux<T>(c));
       CK(cudaMemcpyAsync(w.aux, init_lam, 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
       LK(ACM_K_OTHER, Ops<T>::mask_solid(g, w.aux, lp, Hdev + (size_t)(p / lph) * hs, c->st));
     }
@@ -610,6 +626,7 @@ acm_status stokes_outputs(acm_ctx* c, int nprob, void* u_out, long long u_stride
                          3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
   }
   if (p_out) {
+    CKS(ensure_aux<T>(c));
     // p = q - mean(q): inverse transform of q^ (its k = 0 coefficient is 0)
     const Sym<T> sym = sym_of<T>(c, 0);
     LK(ACM_K_OTHER, Ops<T>::pass(g, 0, P_INV_SCALE, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -731,6 +748,7 @@ acm_status perm_grad(acm_ctx* c, const uint8_t* Hdev, int deriv, double Kg[9]) {
   const Geo& g = c->g;
   const Sym<T> sym = sym_of<T>(c, deriv);
   const size_t cs = 2 * sizeof(T);
+  CKS(ensure_aux<T>(c));
   T* f = (T*)w.aux;
   double K[6] = {0, 0, 0, 0, 0, 0};
   for (int l = 0; l < 3; ++l) {
@@ -827,6 +845,7 @@ acm_status solute_outputs(acm_ctx* c, int nprob, const uint8_t* Hdev, const void
   g.hs = 0;
   g.us = us;
   const Sym<T> sym = sym_of<T>(c, 0);
+  CKS(ensure_aux<T>(c));
   T* grad = (T*)w.aux;
   T* chi = (T*)w.aux + (size_t)c->B * 3 * g.V;
   // grad chi^{n+1}: the last pass left i d chi^ (inverse along z and y) in components 0..2
@@ -1285,8 +1304,8 @@ static acm_status fft_impl(acm_ctx* c, int fp64, int nbatch, const void* in, voi
   const Geo& g = c->g;
   const size_t rs = fp64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * rs;
-  if (fp64) CKS(ensure_prec<double>(c));
-  else CKS(ensure_prec<float>(c));
+  if (fp64) CKS(ensure_aux<double>(c));
+  else CKS(ensure_aux<float>(c));
   Prec& w = fp64 ? c->pd : c->pf;
   for (int b = 0; b < nbatch; ++b) {
     if (forward) {
@@ -1409,6 +1428,7 @@ acm_status acm_batch_create(acm_batch** out, int ncells, const int* dims, void* 
   for (auto& gr : b->groups) {
     s = ctx_create(&gr.c, gr.n[0], gr.n[1], gr.n[2], stream, 3 * (int)gr.cells.size(), (int)gr.cells.size());
     if (s != ACM_OK) break;
+    gr.c->spec_comps = 3;  // Stokes only
   }
   if (s == ACM_OK && (cudaMalloc(&b->counts, (size_t)ncells * sizeof(unsigned long long)) != cudaSuccess ||
                       cudaMalloc(&b->graph.counter, sizeof(unsigned int)) != cudaSuccess)) {
