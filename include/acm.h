@@ -217,6 +217,37 @@ acm_status acm_batch_stokes(acm_batch* batch, const uint8_t* const* H, const acm
 acm_status acm_batch_profile_enable(acm_batch* batch, int on);
 acm_status acm_batch_profile_read(acm_batch* batch, double* ms, long long* launches);
 
+/* Learned warm start: a 3D Fourier neural operator mapping an indicator H to
+ * an initial velocity and solid multiplier for acm_stokes (warm-start inputs
+ * init_u, init_lambda), trained on solutions of the method itself.
+ *   features (H, x0, x1, x2) with x_c = (i_c + 1/2)/n_c; lift v = P a + p;
+ *   L layers v <- gelu(G(R_l F(v)) + M_l v + m_l), F the forward DFT on the
+ *   kept modes (k2 < modes; k0, k1 in [0, modes) or [n - modes, n)), R_l a
+ *   width x width complex matrix per kept mode, G(Y) = (1/V) sum w_k Re[Y e^{2 pi i k.x}]
+ *   (w_k = 1 on k2 = 0, else 2); projection out = Q v + q to 6 channels
+ *   (u, lambda). Loss (1/(B V)) sum |out_u - t_u|^2 + H |out_lambda - t_lambda|^2.
+ * Weights and stored activations are BF16; arithmetic and accumulation FP32.
+ * Parameters form one FP32 vector: P [W][4], p [W], per layer R [M][W][W][2]
+ * (M = 4 modes^3), M [W][W], m [W]; then Q [6][W], q [6].
+ *   acm_fno_create    width in {4, 8, 16, 32}; 1 <= max_batch <= 64; parameters zero.
+ *   acm_fno_forward   H [batch][V] (device or host), out [batch][6][V] FP32 (device
+ *                     or host, nullable).
+ *   acm_fno_backward  forward with targets t [batch][6][V] FP32, loss (host,
+ *                     nullable), gradient kept for acm_fno_adamw and copied to
+ *                     grad [nparams] (nullable).
+ *   acm_fno_adamw     one AdamW step on the FP32 master parameters. */
+typedef struct acm_fno acm_fno;
+acm_status acm_fno_create(acm_fno** fno, int n0, int n1, int n2, int width, int modes, int layers, int max_batch,
+                          void* cuda_stream);
+acm_status acm_fno_destroy(acm_fno* fno);
+acm_status acm_fno_num_params(acm_fno* fno, long long* n);
+acm_status acm_fno_set_params(acm_fno* fno, const float* theta);
+acm_status acm_fno_get_params(acm_fno* fno, float* theta);
+acm_status acm_fno_forward(acm_fno* fno, int batch, const uint8_t* H, float* out);
+acm_status acm_fno_backward(acm_fno* fno, int batch, const uint8_t* H, const float* target, double* loss,
+                            float* grad);
+acm_status acm_fno_adamw(acm_fno* fno, double lr, double beta1, double beta2, double eps, double weight_decay);
+
 /* Convergence history of the last solve on this context for problem `index`
  * (0 for acm_stokes and acm_advdiff; the load index 0..2 for the tensor calls).
  * Copies up to `cap` records, record-major, into `out` (host) and returns the

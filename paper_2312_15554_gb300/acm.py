@@ -26,7 +26,8 @@ EXPORTED = (
     "acm_stokes", "acm_stokes_tensor", "acm_advdiff", "acm_advdiff_tensor",
     "acm_fft_r2c", "acm_fft_c2r", "acm_fft_r2c_static", "acm_history",
     "acm_batch_create", "acm_batch_destroy", "acm_batch_stokes", "acm_batch_profile_enable",
-    "acm_batch_profile_read", "acm_profile_enable", "acm_profile_read", "acm_last_error", "acm_status_str",
+    "acm_batch_profile_read", "acm_fno_create", "acm_fno_destroy", "acm_fno_num_params", "acm_fno_set_params",
+    "acm_fno_get_params", "acm_fno_forward", "acm_fno_backward", "acm_fno_adamw", "acm_profile_enable", "acm_profile_read", "acm_last_error", "acm_status_str",
 )
 
 KERNEL_KINDS = ("x_stokes_local", "x_stokes_rhs", "y_fwd_stokes", "z_stokes", "y_inv_stokes", "x_solute",
@@ -97,6 +98,15 @@ def load(path: str = None):
                                      C.POINTER(acm_report)]
     lib.acm_batch_profile_enable.argtypes = [vp, ip]
     lib.acm_batch_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
+    fp = C.POINTER(C.c_float)
+    lib.acm_fno_create.argtypes = [C.POINTER(vp), ip, ip, ip, ip, ip, ip, ip, vp]
+    lib.acm_fno_destroy.argtypes = [vp]
+    lib.acm_fno_num_params.argtypes = [vp, C.POINTER(C.c_longlong)]
+    lib.acm_fno_set_params.argtypes = [vp, vp]
+    lib.acm_fno_get_params.argtypes = [vp, vp]
+    lib.acm_fno_forward.argtypes = [vp, ip, vp, vp]
+    lib.acm_fno_backward.argtypes = [vp, ip, vp, vp, dp, vp]
+    lib.acm_fno_adamw.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
     lib.acm_history.argtypes = [vp, ip, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.acm_profile_enable.argtypes = [vp, ip]
     lib.acm_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
@@ -327,3 +337,52 @@ def acm_batch_profile_read(batch):
     cnt = (C.c_longlong * k)()
     _check(load().acm_batch_profile_read(batch.h, ms, cnt), "acm_batch_profile_read")
     return {name: (ms[i], cnt[i]) for i, name in enumerate(KERNEL_KINDS)}
+
+
+class acm_fno:
+    """Owns an acm_fno* (the learned warm start) for grids of one shape."""
+
+    def __init__(self, shape, width=32, modes=12, layers=4, max_batch=4, stream: int = 0):
+        lib = load()
+        self.shape = tuple(int(a) for a in shape)
+        self.width, self.modes, self.layers, self.max_batch = width, modes, layers, max_batch
+        h = C.c_void_p()
+        _check(lib.acm_fno_create(C.byref(h), *self.shape, width, modes, layers, max_batch, C.c_void_p(stream)),
+               "acm_fno_create")
+        self.h = h
+        n = C.c_longlong()
+        _check(lib.acm_fno_num_params(self.h, C.byref(n)), "acm_fno_num_params")
+        self.num_params = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().acm_fno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        _check(load().acm_fno_set_params(self.h, _ptr(theta)), "acm_fno_set_params")
+
+    def get_params(self):
+        out = np.zeros(self.num_params, np.float32)
+        _check(load().acm_fno_get_params(self.h, _ptr(out)), "acm_fno_get_params")
+        return out
+
+    def forward(self, H, out, batch=None):
+        b = int(batch if batch is not None else H.shape[0])
+        _check(load().acm_fno_forward(self.h, b, _ptr(H), _ptr(out)), "acm_fno_forward")
+
+    def backward(self, H, target, grad=None, batch=None):
+        b = int(batch if batch is not None else H.shape[0])
+        loss = C.c_double()
+        _check(load().acm_fno_backward(self.h, b, _ptr(H), _ptr(target), C.byref(loss), _ptr(grad)),
+               "acm_fno_backward")
+        return loss.value
+
+    def adamw(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4):
+        _check(load().acm_fno_adamw(self.h, lr, beta1, beta2, eps, weight_decay), "acm_fno_adamw")

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["acm_f32.cu", "acm_f64.cu", "acm_misc.cu", "acm_api.cu", "acm_static.cu"]
+SOURCES = ["acm_f32.cu", "acm_f64.cu", "acm_misc.cu", "acm_api.cu", "acm_static.cu", "acm_fno.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 LIB = os.path.join(OUT, "libacm.so")
 
