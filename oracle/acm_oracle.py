@@ -161,6 +161,32 @@ def zero_state(shape) -> StokesState:
     return StokesState(u=z3.copy(), ut=z3.copy(), q=np.zeros(tuple(shape)), a=z3.copy(), lam=z3.copy())
 
 
+def consistent_pressure(a, d):
+    """The pressure q (mean zero) of an ADMM fixed point with multiplier field a.
+
+    At a fixed point of Section 3.1, u = u~ and div u = 0, so the divergence of
+    the Step 1 equation (Eq. 7 in Fourier space, Eq. 13) leaves
+    |d|^2 q^ = i d . a^ at every k != 0 (the uniform body force has no k != 0
+    part); q^ is 0 where |d|^2 = 0. A warm start given u and lambda starts from
+    this q with a = H lambda.
+    """
+    ah = fft3(a)
+    dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2]
+    num = 1j * (d[0] * ah[0] + d[1] * ah[1] + d[2] * ah[2])
+    qh = np.where(dd > 0, num / np.where(dd > 0, dd, 1.0), 0.0)
+    return ifft3(qh)
+
+
+def warm_state(H, u, lam, deriv=EXACT) -> StokesState:
+    """Warm-start state from a velocity and a multiplier: u~ = u, lambda and a
+    masked by H, q the consistent pressure of a."""
+    Hf = np.asarray(H).astype(np.float64)
+    lam = np.asarray(lam, dtype=np.float64) * Hf[None]
+    d, _ = symbols(np.asarray(H).shape, deriv)
+    u = np.asarray(u, dtype=np.float64)
+    return StokesState(u=u.copy(), ut=u.copy(), q=consistent_pressure(lam, d), a=lam.copy(), lam=lam.copy())
+
+
 def stokes_step1(state: StokesState, g, nu, beta, b, d, L):
     """Step 1 (Eq. 7), solved in Fourier space (Eq. 13).
 

@@ -142,6 +142,49 @@ def test_converged_result_is_penalty_independent():
     np.testing.assert_allclose(Ra.state.u, Rb.state.u, atol=1e-8 * np.abs(Ra.state.u).max())
 
 
+def test_consistent_pressure_of_a_gradient_force_is_minus_its_potential():
+    # a = grad(phi) is balanced by q = -phi (Eq. 7 with u = 0); phi in the band
+    # of the exact symbols, its gradient written out by hand
+    shape = (8, 12, 16)
+    x = [(np.arange(n) + 0.5) / n for n in shape]
+    X0, X1, X2 = np.meshgrid(*x, indexing="ij")
+    tp = 2 * np.pi
+    phi = np.sin(tp * X0) * np.cos(tp * 2 * X1) + 0.5 * np.cos(tp * 3 * X2)
+    a = np.stack([tp * np.cos(tp * X0) * np.cos(tp * 2 * X1),
+                  -2 * tp * np.sin(tp * X0) * np.sin(tp * 2 * X1),
+                  -1.5 * tp * np.sin(tp * 3 * X2)])
+    d, _ = O.symbols(shape, O.EXACT)
+    q = O.consistent_pressure(a, d)
+    np.testing.assert_allclose(q, -(phi - phi.mean()), atol=1e-12)
+
+
+@pytest.mark.parametrize("deriv", [O.EXACT, O.CENTRAL])
+def test_converged_pressure_is_the_consistent_pressure_of_the_multiplier(deriv):
+    shape = (8, 8, 8)
+    H = I.random_indicator(shape, 0.3, 4)
+    R = O.stokes(H, [0.3, 1.0, -0.5], O.StokesParams(eps=1e-12, alpha0=300, beta0=300, b0=300, adaptive=False,
+                                                     max_iter=40000, deriv=deriv))
+    assert R.converged
+    d, _ = O.symbols(shape, deriv)
+    q = O.consistent_pressure(R.state.a, d)
+    np.testing.assert_allclose(q, R.p, atol=1e-7 * np.abs(R.p).max())
+
+
+def test_restart_from_a_converged_velocity_and_multiplier_stops_at_once():
+    shape = (8, 8, 8)
+    H = I.random_indicator(shape, 0.3, 5)
+    P = O.StokesParams(eps=1e-9, alpha0=300, beta0=300, b0=300, adaptive=False, max_iter=40000)
+    R = O.stokes(H, [1.0, 0.0, 0.0], P)
+    assert R.converged and R.iters > 50
+    init = O.warm_state(H, R.state.u, R.state.lam)
+    R2 = O.stokes(H, [1.0, 0.0, 0.0], P, init=init)
+    assert R2.converged and R2.iters <= 8
+    # without the consistent pressure the restart is far from done
+    init.q[...] = 0.0
+    R3 = O.stokes(H, [1.0, 0.0, 0.0], P, init=init)
+    assert R3.iters > 10 * R2.iters
+
+
 # --------------------------------------------------------------------------
 # plane Poiseuille flow (closed forms)
 # --------------------------------------------------------------------------
