@@ -139,7 +139,10 @@ acm_status acm_destroy(acm_ctx* ctx);
 /* Problem 1 of Algorithm 1 (Section 3.1): Stokes flow for the body force g
  * (g = -g_p, the negative average pressure gradient of Eq. 1).
  *   init_u, init_lambda  optional warm start (NULL = zero): X^0 = {u, u~ = u,
- *                        q = 0, a = H lambda, lambda = H lambda}; real type.
+ *                        q, a = H lambda, lambda = H lambda}; real type. q is 0
+ *                        without init_lambda; with it, q is the pressure of a
+ *                        fixed point with that a: the divergence of Eq. 7 at
+ *                        u = u~, div u = 0 gives |d|^2 q^ = i d.a^ (k != 0).
  *   u       out [3][V] velocity u^{n} of the last iteration (real type).
  *   p       out [V] pressure q - mean(q) (nullable; real type).
  *   lambda  out [3][V] solid multiplier H lambda (nullable; real type).
@@ -201,8 +204,12 @@ acm_status acm_fft_c2r(acm_ctx* ctx, int fp64, int nbatch, const void* in, void*
  *                     allocated here (about 95 MB per 128^3 cell in FP32).
  *   acm_batch_stokes  H: host array of ncells indicator pointers (device or
  *                     host); prm: precision ACM_FP32 or ACM_FP64 (the mixed
- *                     mode is not batched); u_out: nullable host array of
- *                     ncells nullable pointers to [3 loads][3][V] (real type);
+ *                     mode is not batched); init_u, init_lambda: nullable host
+ *                     arrays of ncells nullable pointers to [3 loads][3][V]
+ *                     (real type), the warm start X^0 of each load as in
+ *                     acm_stokes (u~ = u, lambda masked by H, a = H lambda);
+ *                     u_out, lambda_out: nullable host arrays of ncells
+ *                     nullable pointers to [3 loads][3][V] (real type);
  *                     K: host [ncells][9], row-major K[i][j] of each cell (NaN
  *                     for a cell without solid or without pore voxels, whose
  *                     reports carry ACM_ERR_NO_SOLID / ACM_ERR_NO_FLUID);
@@ -212,7 +219,16 @@ typedef struct acm_batch acm_batch;
 acm_status acm_batch_create(acm_batch** batch, int ncells, const int* dims, void* cuda_stream);
 acm_status acm_batch_destroy(acm_batch* batch);
 acm_status acm_batch_stokes(acm_batch* batch, const uint8_t* const* H, const acm_stokes_params* prm,
-                            void* const* u_out, double* K, acm_report* rep);
+                            const void* const* init_u, const void* const* init_lambda, void* const* u_out,
+                            void* const* lambda_out, double* K, acm_report* rep);
+/* Per-iteration records of every problem of a batch (the Stokes record of
+ * acm_history: residuals, tolerances, penalties, mean velocity), off by default.
+ *   acm_batch_history_enable  cap > 0 allocates cap records per problem
+ *                     (160 bytes each; 3 problems per cell), cap = 0 frees them.
+ *   acm_batch_history  the records of (cell, load) from the last acm_batch_stokes
+ *                     into out [min(cap, count)][20]; count = records kept. */
+acm_status acm_batch_history_enable(acm_batch* batch, int cap);
+acm_status acm_batch_history(acm_batch* batch, int cell, int load, double* out, int cap, int* count);
 /* The profiler of acm_profile_enable / acm_profile_read over all cells of a batch. */
 acm_status acm_batch_profile_enable(acm_batch* batch, int on);
 acm_status acm_batch_profile_read(acm_batch* batch, double* ms, long long* launches);
@@ -235,6 +251,13 @@ acm_status acm_batch_profile_read(acm_batch* batch, double* ms, long long* launc
  *   acm_fno_backward  forward with targets t [batch][6][V] FP32, loss (host,
  *                     nullable), gradient kept for acm_fno_adamw and copied to
  *                     grad [nparams] (nullable).
+ *   acm_fno_warm_start  cubic grids only: the warm start of all three unit
+ *                     loads, init_u and init_lambda [batch][3 loads][3][V]
+ *                     FP32 on the device (the layout acm_batch_stokes takes).
+ *                     The network predicts the load e_0; the load e_j uses the
+ *                     cell with axes 0 and j swapped and swaps them back
+ *                     (with the vector components), which is exact for the
+ *                     Stokes problem itself.
  *   acm_fno_adamw     one AdamW step on the FP32 master parameters. */
 typedef struct acm_fno acm_fno;
 acm_status acm_fno_create(acm_fno** fno, int n0, int n1, int n2, int width, int modes, int layers, int max_batch,
@@ -244,6 +267,7 @@ acm_status acm_fno_num_params(acm_fno* fno, long long* n);
 acm_status acm_fno_set_params(acm_fno* fno, const float* theta);
 acm_status acm_fno_get_params(acm_fno* fno, float* theta);
 acm_status acm_fno_forward(acm_fno* fno, int batch, const uint8_t* H, float* out);
+acm_status acm_fno_warm_start(acm_fno* fno, int batch, const uint8_t* H, float* init_u, float* init_lambda);
 acm_status acm_fno_backward(acm_fno* fno, int batch, const uint8_t* H, const float* target, double* loss,
                             float* grad);
 acm_status acm_fno_adamw(acm_fno* fno, double lr, double beta1, double beta2, double eps, double weight_decay);

@@ -26,8 +26,8 @@ EXPORTED = (
     "acm_stokes", "acm_stokes_tensor", "acm_advdiff", "acm_advdiff_tensor",
     "acm_fft_r2c", "acm_fft_c2r", "acm_fft_r2c_static", "acm_history",
     "acm_batch_create", "acm_batch_destroy", "acm_batch_stokes", "acm_batch_profile_enable",
-    "acm_batch_profile_read", "acm_fno_create", "acm_fno_destroy", "acm_fno_num_params", "acm_fno_set_params",
-    "acm_fno_get_params", "acm_fno_forward", "acm_fno_backward", "acm_fno_adamw", "acm_profile_enable", "acm_profile_read", "acm_last_error", "acm_status_str",
+    "acm_batch_profile_read", "acm_batch_history_enable", "acm_batch_history", "acm_fno_create", "acm_fno_destroy", "acm_fno_num_params", "acm_fno_set_params",
+    "acm_fno_get_params", "acm_fno_forward", "acm_fno_warm_start", "acm_fno_backward", "acm_fno_adamw", "acm_profile_enable", "acm_profile_read", "acm_last_error", "acm_status_str",
 )
 
 KERNEL_KINDS = ("x_stokes_local", "x_stokes_rhs", "y_fwd_stokes", "z_stokes", "y_inv_stokes", "x_solute",
@@ -94,8 +94,10 @@ def load(path: str = None):
     lib.acm_fft_r2c_static.argtypes = [ip, ip, ip, ip, vp, vp, vp]
     lib.acm_batch_create.argtypes = [C.POINTER(vp), ip, C.POINTER(C.c_int), vp]
     lib.acm_batch_destroy.argtypes = [vp]
-    lib.acm_batch_stokes.argtypes = [vp, C.POINTER(vp), C.POINTER(acm_stokes_params), C.POINTER(vp), dp,
-                                     C.POINTER(acm_report)]
+    lib.acm_batch_stokes.argtypes = [vp, C.POINTER(vp), C.POINTER(acm_stokes_params), C.POINTER(vp),
+                                     C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), dp, C.POINTER(acm_report)]
+    lib.acm_batch_history_enable.argtypes = [vp, ip]
+    lib.acm_batch_history.argtypes = [vp, ip, ip, dp, ip, C.POINTER(C.c_int)]
     lib.acm_batch_profile_enable.argtypes = [vp, ip]
     lib.acm_batch_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
     fp = C.POINTER(C.c_float)
@@ -105,6 +107,7 @@ def load(path: str = None):
     lib.acm_fno_set_params.argtypes = [vp, vp]
     lib.acm_fno_get_params.argtypes = [vp, vp]
     lib.acm_fno_forward.argtypes = [vp, ip, vp, vp]
+    lib.acm_fno_warm_start.argtypes = [vp, ip, vp, vp, vp]
     lib.acm_fno_backward.argtypes = [vp, ip, vp, vp, dp, vp]
     lib.acm_fno_adamw.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
     lib.acm_history.argtypes = [vp, ip, dp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -315,16 +318,36 @@ class acm_batch:
             pass
 
 
-def acm_batch_stokes(batch, Hs, params=None, u_out=None):
-    """Returns (status, K [ncells, 3, 3], reports [ncells][3])."""
+def acm_batch_stokes(batch, Hs, params=None, u_out=None, init_u=None, init_lambda=None, lambda_out=None):
+    """Returns (status, K [ncells, 3, 3], reports [ncells][3]). The optional
+    per-cell buffers are [3 loads][3][V] of the solve's real type."""
     n = len(batch.shapes)
-    hp = (C.c_void_p * n)(*[_ptr(h) for h in Hs])
-    up = None if u_out is None else (C.c_void_p * n)(*[_ptr(u) for u in u_out])
+
+    def arr(xs):
+        return None if xs is None else (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    hp = arr(Hs)
     K = (C.c_double * (9 * n))()
     reps = (acm_report * (3 * n))()
-    s = load().acm_batch_stokes(batch.h, hp, C.byref(params or stokes_params()), up, K, reps)
+    s = load().acm_batch_stokes(batch.h, hp, C.byref(params or stokes_params()), arr(init_u), arr(init_lambda),
+                                arr(u_out), arr(lambda_out), K, reps)
     _check(s, "acm_batch_stokes", allow_maxiter=True)
     return s, np.array(K[:]).reshape(n, 3, 3), [list(reps[3 * i:3 * i + 3]) for i in range(n)]
+
+
+def acm_batch_history_enable(batch, cap: int):
+    _check(load().acm_batch_history_enable(batch.h, int(cap)), "acm_batch_history_enable")
+
+
+def acm_batch_history(batch, cell: int, load_index: int):
+    """Records (count, 20) of one problem of the last batched solve (see acm_history)."""
+    lib = load()
+    cnt = C.c_int()
+    _check(lib.acm_batch_history(batch.h, cell, load_index, None, 0, C.byref(cnt)), "acm_batch_history")
+    out = np.zeros((cnt.value, 20))
+    if cnt.value:
+        _check(lib.acm_batch_history(batch.h, cell, load_index, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                     cnt.value, C.byref(cnt)), "acm_batch_history")
+    return out
 
 
 def acm_batch_profile_enable(batch, on: bool = True):
@@ -376,6 +399,12 @@ class acm_fno:
     def forward(self, H, out, batch=None):
         b = int(batch if batch is not None else H.shape[0])
         _check(load().acm_fno_forward(self.h, b, _ptr(H), _ptr(out)), "acm_fno_forward")
+
+    def warm_start(self, H, init_u, init_lambda, batch=None):
+        """Warm starts of the three unit loads, [batch][3][3][V] FP32 on the device."""
+        b = int(batch if batch is not None else H.shape[0])
+        _check(load().acm_fno_warm_start(self.h, b, _ptr(H), _ptr(init_u), _ptr(init_lambda)),
+               "acm_fno_warm_start")
 
     def backward(self, H, target, grad=None, batch=None):
         b = int(batch if batch is not None else H.shape[0])

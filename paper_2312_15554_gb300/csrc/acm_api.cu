@@ -69,6 +69,8 @@ struct acm_ctx {
   uint8_t* Hd = nullptr;
   unsigned long long* cnt = nullptr;
   double* hist = nullptr;
+  double* hist_b = nullptr;  // batches: [B][hist_b_cap][STOKES_HIST] when enabled
+  int hist_b_cap = 0;
   int hist_kind = 0;  // 1: Stokes (16 doubles / record), 2: solute (4 doubles / record)
   int hist_n[BMAX] = {0, 0, 0};
   void* pin = nullptr;  // pinned host scratch
@@ -333,8 +335,8 @@ double default_penalty(const Geo& g, double nu) {
 
 template <typename T>
 acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int lph, const double (*gs)[3],
-                        const acm_stokes_params& P, double eps, const void* init_u, const void* init_lam,
-                        const int* preset_status = nullptr) {
+                        const acm_stokes_params& P, double eps, const void* const* init_u,
+                        const void* const* init_lam, const int* preset_status = nullptr) {
   CKS(ensure_prec<T>(c));
   Prec& w = prec<T>(c);
   Geo g = c->g;
@@ -349,8 +351,8 @@ acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
   for (int p = 0; p < nprob; ++p) {
     T* up = (T*)w.u + (size_t)p * 3 * g.V;
     T* lp = (T*)w.lam + (size_t)p * 3 * g.V;
-    if (init_u) {
-      CK(cudaMemcpyAsync(up, init_u, 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
+    if (init_u && init_u[p]) {
+      CK(cudaMemcpyAsync(up, init_u[p], 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
       // div u^0 in Fourier space for the first dual residual of pair 2
       void* sp = (char*)w.spec;
       LK(ACM_K_OTHER, Ops<T>::x_r2c(g, 1, 3, sp, 3 * g.S, up, 3 * g.V, w.tw, c->st));
@@ -358,10 +360,16 @@ acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
       LK(ACM_K_OTHER, Ops<T>::pass(g, 0, P_FWD, 3, 1, sp, 3 * g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
       LK(ACM_K_OTHER, Ops<T>::div_spec(g, sp, (char*)w.st1 + (size_t)p * g.S * cs, sym, c->st));
     }
-    if (init_lam) {
+    if (init_lam && init_lam[p]) {
       CKS(ensure_aux<T>(c));
-      CK(cudaMemcpyAsync(w.aux, init_lam, 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
+      CK(cudaMemcpyAsync(w.aux, init_lam[p], 3 * g.V * sizeof(T), cudaMemcpyDefault, c->st));
       LK(ACM_K_OTHER, Ops<T>::mask_solid(g, w.aux, lp, Hdev + (size_t)(p / lph) * hs, c->st));
+      // q^0: the pressure consistent with a^0 = H lambda^0 at a fixed point
+      void* sp = (char*)w.spec;
+      LK(ACM_K_OTHER, Ops<T>::x_r2c(g, 1, 3, sp, 3 * g.S, lp, 3 * g.V, w.tw, c->st));
+      LK(ACM_K_OTHER, Ops<T>::pass(g, 1, P_FWD, 3, 1, sp, 3 * g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+      LK(ACM_K_OTHER, Ops<T>::pass(g, 0, P_FWD, 3, 1, sp, 3 * g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr, c->st));
+      LK(ACM_K_OTHER, Ops<T>::q_from_a(g, sp, (char*)w.st0 + (size_t)p * g.S * cs, sym, c->st));
     }
   }
   std::vector<StokesDev> hp(nprob);
@@ -422,9 +430,10 @@ acm_status stokes_body(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs,
   g.hs = hs;
   g.lph = lph;
   const int nbx = Ops<T>::x_blocks(g), nbz = Ops<T>::z_blocks(g, P_STOKES);
-  double* hist = nprob <= BMAX ? c->hist : nullptr;
+  double* hist = c->hist_b ? c->hist_b : (nprob <= BMAX ? c->hist : nullptr);
+  const int hcap = c->hist_b ? c->hist_b_cap : HIST_CAP;
   LK(ACM_K_X_STOKES_LOCAL, Ops<T>::x_stokes_local(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, c->part_x, w.tw, c->st));
-  LK(ACM_K_FINALIZE, stokes_finalize(nprob, c->sprm, c->part_x, nbx, c->part_z, nbz, (double)g.V, hist, HIST_CAP, c->st));
+  LK(ACM_K_FINALIZE, stokes_finalize(nprob, c->sprm, c->part_x, nbx, c->part_z, nbz, (double)g.V, hist, hcap, c->st));
   if (!last) CKS(stokes_step1<T>(c, nprob, Hdev, hs, lph, sym));
   return ACM_OK;
 }
@@ -702,13 +711,14 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
   Hdev = c->Hd;  // one stable buffer, so a cached device loop stays valid
   const bool dl = P.device_loop != 0;
   acm_status st = ACM_OK;
+  const std::vector<const void*> iu(nprob, init_u), il(nprob, init_lam);
   if (P.precision == ACM_FP32) {
-    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, P.eps, init_u, init_lam));
+    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, P.eps, iu.data(), il.data()));
     CKS(stokes_iterate<float>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     CKS(stokes_outputs<float>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
     st = stokes_reports(c, nprob, rep, -1, t0);
   } else if (P.precision == ACM_FP64) {
-    CKS(stokes_setup<double>(c, nprob, Hdev, 0, 1, gs, P, P.eps, init_u, init_lam));
+    CKS(stokes_setup<double>(c, nprob, Hdev, 0, 1, gs, P, P.eps, iu.data(), il.data()));
     CKS(stokes_iterate<double>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
     st = stokes_reports(c, nprob, rep, -2, t0);
@@ -1015,6 +1025,7 @@ struct BatchGroup {
   int n[3];
   std::vector<int> cells;
   acm_ctx* c = nullptr;
+  std::vector<int> iters;  // iterations of each problem in the last solve
 };
 
 }  // namespace
@@ -1030,8 +1041,9 @@ struct acm_batch {
 namespace {
 
 template <typename T>
-acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_stokes_params& P, void* const* u_out,
-                            double* K, acm_report* rep) {
+acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_stokes_params& P,
+                            const void* const* init_u, const void* const* init_lam, void* const* u_out,
+                            void* const* lam_out, double* K, acm_report* rep) {
   const double t0 = now_ms();
   // indicators into each group's cell slots, solid counts per cell
   CK(cudaMemsetAsync(b->counts, 0, (size_t)b->ncells * sizeof(unsigned long long), b->st));
@@ -1059,8 +1071,16 @@ acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_sto
       preset[p] = ns == 0 ? ACM_ERR_NO_SOLID : (ns == (unsigned long long)V ? ACM_ERR_NO_FLUID : ACM_OK);
       gs[(size_t)p * 3 + p % 3] = 1.0;
     }
+    // warm starts of the three loads of a cell lie 3 V apart in its buffer
+    std::vector<const void*> iu(np, nullptr), il(np, nullptr);
+    for (int p = 0; p < np; ++p) {
+      const int cell = gr.cells[p / 3];
+      const size_t off = (size_t)(p % 3) * 3 * V * sizeof(T);
+      if (init_u && init_u[cell]) iu[p] = (const char*)init_u[cell] + off;
+      if (init_lam && init_lam[cell]) il[p] = (const char*)init_lam[cell] + off;
+    }
     CKS(stokes_setup<T>(gr.c, np, gr.c->Hd, V, 3, reinterpret_cast<const double(*)[3]>(gs.data()), P, P.eps,
-                        nullptr, nullptr, preset.data()));
+                        iu.data(), il.data(), preset.data()));
     grp.push_back({gr.c, np, gr.c->Hd, V, 3});
   }
   bool prof = false;
@@ -1086,6 +1106,8 @@ acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_sto
     std::vector<StokesDev> hp(np);
     CK(cudaMemcpyAsync(hp.data(), c->sprm, np * sizeof(StokesDev), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
+    gr.iters.assign(np, 0);
+    for (int p = 0; p < np; ++p) gr.iters[p] = hp[p].iter;
     for (int i = 0; i < nc; ++i) {
       const int cell = gr.cells[i];
       for (int j = 0; j < 3; ++j) {
@@ -1110,6 +1132,9 @@ acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_sto
       }
       if (u_out && u_out[cell])
         CK(cudaMemcpyAsync(u_out[cell], (T*)w.u + (size_t)3 * i * 3 * g.V, (size_t)9 * g.V * sizeof(T),
+                           cudaMemcpyDefault, c->st));
+      if (lam_out && lam_out[cell])
+        CK(cudaMemcpyAsync(lam_out[cell], (T*)w.lam + (size_t)3 * i * 3 * g.V, (size_t)9 * g.V * sizeof(T),
                            cudaMemcpyDefault, c->st));
     }
   }
@@ -1226,7 +1251,7 @@ acm_status acm_destroy(acm_ctx* c) {
   free_prec(c->pd);
   if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
   if (c->cap) cudaStreamDestroy(c->cap);
-  void* ps[] = {c->sprm, c->cprm, c->part_x, c->part_z, c->part_r, c->Hd, c->cnt, c->hist, c->graph.counter};
+  void* ps[] = {c->sprm, c->cprm, c->part_x, c->part_z, c->part_r, c->Hd, c->cnt, c->hist, c->hist_b, c->graph.counter};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->pin) cudaFreeHost(c->pin);
@@ -1457,15 +1482,16 @@ acm_status acm_batch_destroy(acm_batch* b) {
   return ACM_OK;
 }
 
-acm_status acm_batch_stokes(acm_batch* b, const uint8_t* const* H, const acm_stokes_params* prm, void* const* u_out,
-                            double* K, acm_report* rep) {
+acm_status acm_batch_stokes(acm_batch* b, const uint8_t* const* H, const acm_stokes_params* prm,
+                            const void* const* init_u, const void* const* init_lambda, void* const* u_out,
+                            void* const* lambda_out, double* K, acm_report* rep) {
   if (!b || !H || !K) return ACM_ERR_ARG;
   acm_stokes_params P;
   fill_stokes_params(prm, &P);
   CKS(check_stokes_args(P));
   if (P.precision == ACM_FP32_THEN_FP64) return ACM_ERR_ARG;
-  return P.precision == ACM_FP32 ? batch_stokes_run<float>(b, H, P, u_out, K, rep)
-                                 : batch_stokes_run<double>(b, H, P, u_out, K, rep);
+  return P.precision == ACM_FP32 ? batch_stokes_run<float>(b, H, P, init_u, init_lambda, u_out, lambda_out, K, rep)
+                                 : batch_stokes_run<double>(b, H, P, init_u, init_lambda, u_out, lambda_out, K, rep);
 }
 
 acm_status acm_batch_profile_read(acm_batch* b, double* ms, long long* launches) {
@@ -1486,6 +1512,51 @@ acm_status acm_batch_profile_read(acm_batch* b, double* ms, long long* launches)
     if (launches) launches[k] = cnt[k];
   }
   return ACM_OK;
+}
+
+acm_status acm_batch_history_enable(acm_batch* b, int cap) {
+  if (!b || cap < 0) return ACM_ERR_ARG;
+  if (b->st) CK(cudaStreamSynchronize(b->st));
+  for (auto& gr : b->groups) {
+    acm_ctx* c = gr.c;
+    if (c->hist_b) cudaFree(c->hist_b);
+    c->hist_b = nullptr;
+    c->hist_b_cap = 0;
+    if (cap > 0) {
+      if (cudaMalloc(&c->hist_b, (size_t)c->B * cap * STOKES_HIST * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return ACM_ERR_NOMEM;
+      }
+      c->hist_b_cap = cap;
+    }
+    gr.iters.clear();
+  }
+  // a captured loop holds the old history pointer
+  if (b->graph.exec) {
+    cudaGraphExecDestroy(b->graph.exec);
+    b->graph.exec = nullptr;
+  }
+  return ACM_OK;
+}
+
+acm_status acm_batch_history(acm_batch* b, int cell, int load, double* out, int cap, int* count) {
+  if (!b || cell < 0 || cell >= b->ncells || load < 0 || load > 2 || cap < 0 || (cap > 0 && !out))
+    return ACM_ERR_ARG;
+  for (auto& gr : b->groups) {
+    for (size_t i = 0; i < gr.cells.size(); ++i) {
+      if (gr.cells[i] != cell) continue;
+      acm_ctx* c = gr.c;
+      const int p = 3 * (int)i + load;
+      const int recorded = c->hist_b && !gr.iters.empty() ? std::min(gr.iters[p], c->hist_b_cap) : 0;
+      if (count) *count = recorded;
+      const int n = std::min(cap, recorded);
+      if (n > 0)
+        CK(cudaMemcpy(out, c->hist_b + (size_t)p * c->hist_b_cap * STOKES_HIST, (size_t)n * STOKES_HIST * sizeof(double),
+                      cudaMemcpyDeviceToHost));
+      return ACM_OK;
+    }
+  }
+  return ACM_ERR_ARG;
 }
 
 acm_status acm_batch_profile_enable(acm_batch* b, int on) {

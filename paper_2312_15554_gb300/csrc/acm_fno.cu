@@ -433,6 +433,7 @@ struct acm_fno {
   float* dout = nullptr;           // [Bmax][6][V]
   float* tgt = nullptr;            // [Bmax][6][V] staging of host targets
   uint8_t* Hs = nullptr;           // [Bmax][V] staging of indicators
+  uint8_t* Hp = nullptr;           // [Bmax][V] axis-swapped indicators (warm start, allocated on first use)
   cx<float>* spec = nullptr;       // [Bmax * W][S]
   float* part = nullptr;           // [NRB][W*W + W]
   double* lpart = nullptr;         // [NRB]
@@ -570,6 +571,41 @@ acm_status fno_backward_impl(acm_fno* f, int B, const uint8_t* Hd) {
   return ACM_OK;
 }
 
+// Linear index of the voxel whose axes 0 and j (1 or 2) are swapped, on an
+// n x n x n grid. The swap is its own inverse.
+__device__ __forceinline__ long long swap_axes(long long i, int n, int j) {
+  const int c = (int)(i % n), b = (int)((i / n) % n), a = (int)(i / ((long long)n * n));
+  return j == 1 ? ((long long)b * n + a) * n + c : ((long long)c * n + b) * n + a;
+}
+
+__global__ void k_swap_h(const uint8_t* __restrict__ H, uint8_t* __restrict__ Hp, int n, int j, long long V,
+                         long long total) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / V, i = t - b * V;
+    Hp[t] = H[b * V + swap_axes(i, n, j)];
+  }
+}
+
+// Predictions out' [B][6][V] for the load e_0 on the swapped cell become the
+// warm start of load e_j on the cell: u_c(x) = u'_{s(c)}(s x) with s the swap
+// of 0 and j (the identity for j = 0); the multiplier transforms alike.
+// Outputs [B][3 loads][3][V]; this writes the slot of load j.
+__global__ void k_unswap_out(const float* __restrict__ o, float* __restrict__ u, float* __restrict__ lam, int n, int j,
+                             long long V, long long total) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / V, i = t - b * V;
+    const long long si = j == 0 ? i : swap_axes(i, n, j);
+    const float* ob = o + b * 6 * V;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int sc = c == j ? 0 : (c == 0 ? j : c);
+      const long long dst = ((b * 3 + j) * 3 + c) * V + i;
+      u[dst] = ob[sc * V + si];
+      lam[dst] = ob[(3 + sc) * V + si];
+    }
+  }
+}
+
 }  // namespace
 
 
@@ -597,7 +633,7 @@ acm_status dispatch_w(int W, F&& fn) {
 
 void fno_free(acm_fno* f) {
   void* ps[] = {f->theta, f->tb, f->grad, f->m1, f->m2, f->v, f->z, f->X, f->Y, f->r0, f->r1, f->r2,
-                f->dout, f->tgt, f->Hs, f->spec, f->part, f->lpart, f->tw};
+                f->dout, f->tgt, f->Hs, f->Hp, f->spec, f->part, f->lpart, f->tw};
   for (void* p : ps)
     if (p) cudaFree(p);
   cudaGetLastError();
@@ -753,6 +789,32 @@ acm_status acm_fno_forward(acm_fno* f, int batch, const uint8_t* H, float* out) 
   float* o = out && fno_on_device(out) ? out : f->dout;
   CKF(dispatch_w(f->d.W, [&](auto w) { return fno_forward_impl<decltype(w)::value>(f, batch, Hd, nullptr, o, nullptr); }));
   if (out && o != out) FK(cudaMemcpyAsync(out, o, (size_t)batch * 6 * f->d.V * 4, cudaMemcpyDeviceToHost, f->st));
+  FK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+acm_status acm_fno_warm_start(acm_fno* f, int batch, const uint8_t* H, float* init_u, float* init_lambda) {
+  if (!f || !H || !init_u || !init_lambda || batch < 1 || batch > f->Bmax) return ACM_ERR_ARG;
+  const Geo& g = f->g;
+  if (g.n0 != g.n1 || g.n0 != g.n2) return ACM_ERR_UNSUPPORTED_SIZE;
+  if (!fno_on_device(init_u) || !fno_on_device(init_lambda)) return ACM_ERR_ARG;
+  const uint8_t* Hd = nullptr;
+  CKF(stage_inputs(f, batch, H, &Hd));
+  if (!f->Hp) FK(cudaMalloc(&f->Hp, (size_t)f->Bmax * f->d.V));
+  const long long total = (long long)batch * f->d.V;
+  for (int j = 0; j < 3; ++j) {
+    const uint8_t* Hj = Hd;
+    if (j > 0) {
+      k_swap_h<<<blocks_for(total), 256, 0, f->st>>>(Hd, f->Hp, g.n0, j, f->d.V, total);
+      FK(cudaGetLastError());
+      Hj = f->Hp;
+    }
+    CKF(dispatch_w(f->d.W, [&](auto w) {
+      return fno_forward_impl<decltype(w)::value>(f, batch, Hj, nullptr, f->dout, nullptr);
+    }));
+    k_unswap_out<<<blocks_for(total), 256, 0, f->st>>>(f->dout, init_u, init_lambda, g.n0, j, f->d.V, total);
+    FK(cudaGetLastError());
+  }
   FK(cudaStreamSynchronize(f->st));
   return ACM_OK;
 }

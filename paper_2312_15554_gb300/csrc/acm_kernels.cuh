@@ -802,4 +802,26 @@ __global__ void k_div_spec(const cx<T>* __restrict__ uh, cx<T>* __restrict__ dv,
   }
 }
 
+// Consistent pressure of a warm start: at an ADMM fixed point the divergence of
+// the Step 1 equation (Eq. 7 / Eq. 13) gives |d|^2 q^ = i d.a^ for k != 0, and
+// q^ = 0 where |d|^2 = 0. ah: 3 components at stride S (unnormalised
+// transforms, the scale q^ is kept in).
+template <typename T>
+__global__ void k_q_from_a(const cx<T>* __restrict__ ah, cx<T>* __restrict__ q, Geo g, Sym<T> sym) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)g.n0 * g.n1 * g.P;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % g.P);
+    const long long r = i / g.P;
+    const int ky = (int)(r % g.n1), kz = (int)(r / g.n1);
+    const T d0 = sym.d0[kz], d1 = sym.d1[ky], d2 = sym.d2[kx < g.Pu ? kx : 0];
+    const T dd = d0 * d0 + d1 * d1 + d2 * d2;
+    if (kx >= g.Pu || !(dd > (T)0)) {
+      q[i] = mk<T>(0, 0);
+      continue;
+    }
+    const cx<T> s = cscale(ah[i], d0) + cscale(ah[g.S + i], d1) + cscale(ah[2 * g.S + i], d2);
+    q[i] = cscale(mul_i(s), (T)1 / dd);
+  }
+}
+
 }  // namespace acm

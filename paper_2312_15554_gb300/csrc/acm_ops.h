@@ -43,6 +43,7 @@ struct Ops {
                                  const uint8_t* H, const SoluteDev* prm, double* part, int nblk, cudaStream_t s);
   static cudaError_t mask_solid(const Geo& g, const void* in, void* out, const uint8_t* H, cudaStream_t s);
   static cudaError_t div_spec(const Geo& g, const void* uh, void* dv, const Sym<T>& sym, cudaStream_t s);
+  static cudaError_t q_from_a(const Geo& g, const void* ah, void* q, const Sym<T>& sym, cudaStream_t s);
 };
 
 // precision conversion of n elements (float <-> double)

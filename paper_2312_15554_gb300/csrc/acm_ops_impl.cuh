@@ -250,4 +250,10 @@ cudaError_t Ops<T>::div_spec(const Geo& g, const void* uh, void* dv, const Sym<T
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t Ops<T>::q_from_a(const Geo& g, const void* ah, void* q, const Sym<T>& sym, cudaStream_t s) {
+  k_q_from_a<T><<<608, 256, 0, s>>>((const cx<T>*)ah, (cx<T>*)q, g, sym);
+  return cudaGetLastError();
+}
+
 }  // namespace acm

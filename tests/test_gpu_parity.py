@@ -117,7 +117,7 @@ def test_stokes_warm_start_matches_oracle(lib):
     Hf = H.astype(float)
     u0 = 0.01 * I.random_field((3, 16, 16, 16), 3)
     l0 = I.random_field((3, 16, 16, 16), 4) * Hf[None]
-    init = O.StokesState(u=u0, ut=u0.copy(), q=np.zeros(H.shape), a=l0.copy(), lam=l0.copy())
+    init = O.warm_state(H, u0, l0)
     g = [1.0, 0.0, 0.0]
     R = O.stokes(H, g, O.StokesParams(eps=0.0, adaptive=False, max_iter=7, alpha0=200, beta0=200, b0=200),
                  init=init)
