@@ -216,6 +216,11 @@ def run_gpu(args, rank, world, dist):
     u3 = torch.zeros((3, 3) + H.shape, dtype=torch.float32, device=dev)
     sp = acm.stokes_params(eps=0.0, max_iter=iters, precision=acm.FP32)
     cp = acm.advdiff_params(eps=0.0, max_iter=iters, precision=acm.FP32)
+    # tile widths of the strided passes, tuned once per shape (outside the timed region)
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter()
+    tiles = acm.acm_autotune(ctx, False)
+    tune_s = time.perf_counter() - t_tune
 
     def step(Hin):
         s, K, _, _ = acm.acm_stokes_tensor(ctx, Hin, sp, u3)
@@ -302,7 +307,8 @@ def run_gpu(args, rank, world, dist):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "porosity": round(porosity, 4), "iters_per_step": iters,
                    "problems_per_step": 3 + 3 * len(PECLETS), "l2": "inputs larger than L2 (3.3 GB working set)",
-                   "parallelism": f"independent cells x{world}"},
+                   "parallelism": f"independent cells x{world}", "tiles": tiles,
+                   "autotune_s": round(tune_s, 3)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_source": peak_src, "bytes_per_launch": bytes_per_launch},
@@ -349,6 +355,11 @@ def run_batched(args, rank, world, dist):
     Hd = [torch.as_tensor(h, device=dev) for h in Hs]
     batch = acm.acm_batch(shapes, stream.cuda_stream)
     prm = acm.stokes_params(eps=0.0, max_iter=args.iters, precision=acm.FP32)
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter()
+    acm.acm_batch_autotune(batch)
+    tune_s = time.perf_counter() - t_tune
+    tiles = {f"{shapes[i][0]}^3": acm.acm_batch_tiles(batch, i) for i in range(min(2, len(shapes)))}
     vi = sum(int(np.prod(sh)) for sh in shapes) * 3 * args.iters
     for _ in range(args.warmup):
         acm.acm_batch_stokes(batch, Hd, prm)
@@ -384,7 +395,7 @@ def run_batched(args, rank, world, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batched: {len(shapes)} cells (half 64^3, half 128^3), 3 loads each, "
                                "porosity U[0.2,0.6], radii U[3,10] vox", "iters_per_step": args.iters,
-                   "device_loop": "CUDA graph while node"},
+                   "device_loop": "CUDA graph while node", "tiles": tiles, "autotune_s": round(tune_s, 3)},
         "clocks": clocks,
         "kernels_profiled_step": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]},
         "K_mean_diag_cell0": [float(K[0, i, i]) for i in range(3)],

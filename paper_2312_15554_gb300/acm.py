@@ -26,7 +26,8 @@ EXPORTED = (
     "acm_stokes", "acm_stokes_tensor", "acm_advdiff", "acm_advdiff_tensor",
     "acm_fft_r2c", "acm_fft_c2r", "acm_fft_r2c_static", "acm_history",
     "acm_batch_create", "acm_batch_destroy", "acm_batch_stokes", "acm_batch_profile_enable",
-    "acm_batch_profile_read", "acm_batch_history_enable", "acm_batch_history", "acm_fno_create", "acm_fno_destroy", "acm_fno_num_params", "acm_fno_set_params",
+    "acm_batch_profile_read", "acm_autotune", "acm_set_tiles", "acm_get_tiles", "acm_batch_autotune", "acm_batch_tiles",
+    "acm_batch_history_enable", "acm_batch_history", "acm_fno_create", "acm_fno_destroy", "acm_fno_num_params", "acm_fno_set_params",
     "acm_fno_get_params", "acm_fno_forward", "acm_fno_warm_start", "acm_fno_backward", "acm_fno_adamw", "acm_profile_enable", "acm_profile_read", "acm_last_error", "acm_status_str",
 )
 
@@ -96,6 +97,12 @@ def load(path: str = None):
     lib.acm_batch_destroy.argtypes = [vp]
     lib.acm_batch_stokes.argtypes = [vp, C.POINTER(vp), C.POINTER(acm_stokes_params), C.POINTER(vp),
                                      C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), dp, C.POINTER(acm_report)]
+    i5 = C.POINTER(C.c_int)
+    lib.acm_autotune.argtypes = [vp, ip, ip, i5]
+    lib.acm_set_tiles.argtypes = [vp, ip, i5]
+    lib.acm_get_tiles.argtypes = [vp, ip, i5]
+    lib.acm_batch_autotune.argtypes = [vp, ip, ip]
+    lib.acm_batch_tiles.argtypes = [vp, ip, ip, i5]
     lib.acm_batch_history_enable.argtypes = [vp, ip]
     lib.acm_batch_history.argtypes = [vp, ip, ip, dp, ip, C.POINTER(C.c_int)]
     lib.acm_batch_profile_enable.argtypes = [vp, ip]
@@ -332,6 +339,40 @@ def acm_batch_stokes(batch, Hs, params=None, u_out=None, init_u=None, init_lambd
                                 arr(u_out), arr(lambda_out), K, reps)
     _check(s, "acm_batch_stokes", allow_maxiter=True)
     return s, np.array(K[:]).reshape(n, 3, 3), [list(reps[3 * i:3 * i + 3]) for i in range(n)]
+
+
+TILE_PASSES = ("y_fwd_stokes", "z_stokes", "y_inv", "y_fwd_solute", "z_solute")
+
+
+def acm_autotune(ctx, fp64: bool = False, deriv: int = DERIV_EXACT):
+    """Times the tile widths of the strided passes; returns {pass: width}."""
+    t = (C.c_int * 5)()
+    _check(load().acm_autotune(ctx.h, int(fp64), int(deriv), t), "acm_autotune")
+    return dict(zip(TILE_PASSES, list(t)))
+
+
+def acm_set_tiles(ctx, tiles, fp64: bool = False):
+    """tiles: {pass: width} or five widths in TILE_PASSES order."""
+    if isinstance(tiles, dict):
+        tiles = [tiles[k] for k in TILE_PASSES]
+    t = (C.c_int * 5)(*[int(x) for x in tiles])
+    _check(load().acm_set_tiles(ctx.h, int(fp64), t), "acm_set_tiles")
+
+
+def acm_get_tiles(ctx, fp64: bool = False):
+    t = (C.c_int * 5)()
+    _check(load().acm_get_tiles(ctx.h, int(fp64), t), "acm_get_tiles")
+    return dict(zip(TILE_PASSES, list(t)))
+
+
+def acm_batch_autotune(batch, fp64: bool = False, deriv: int = DERIV_EXACT):
+    _check(load().acm_batch_autotune(batch.h, int(fp64), int(deriv)), "acm_batch_autotune")
+
+
+def acm_batch_tiles(batch, cell: int, fp64: bool = False):
+    t = (C.c_int * 5)()
+    _check(load().acm_batch_tiles(batch.h, cell, int(fp64), t), "acm_batch_tiles")
+    return dict(zip(TILE_PASSES, list(t)))
 
 
 def acm_batch_history_enable(batch, cap: int):

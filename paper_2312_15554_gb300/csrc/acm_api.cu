@@ -1142,6 +1142,106 @@ acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_sto
   return ACM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Tile autotuner: times each candidate tile width of the strided passes of the
+// solver loops on this context's workspace (nprob problems, CUDA events on the
+// context's stream) and keeps the fastest. The tile width only regroups which
+// columns a block transforms, so every choice gives the same fields; only the
+// order of the FP64 partial sums of the z pass changes.
+// ---------------------------------------------------------------------------
+struct TuneJob {
+  int axis, op, nc;
+  bool solute;
+};
+constexpr TuneJob TUNE_JOBS[] = {{1, P_FWD, 3, false}, {0, P_STOKES, 3, false}, {1, P_INV, 3, false},
+                                 {1, P_FWD, 4, true},  {0, P_SOLUTE, 4, true}};
+constexpr int TUNE_REPS = 5;
+
+template <typename T>
+acm_status autotune_ctx(acm_ctx* c, int nprob, int deriv) {
+  CKS(ensure_prec<T>(c));
+  Prec& w = prec<T>(c);
+  const int pr = sizeof(T) == 8;
+  // parameters that keep every pass from taking its early exit
+  std::vector<StokesDev> sd(nprob);
+  std::vector<SoluteDev> cd(nprob);
+  for (int p = 0; p < nprob; ++p) {
+    std::memset(&sd[p], 0, sizeof(StokesDev));
+    std::memset(&cd[p], 0, sizeof(SoluteDev));
+    sd[p].nu = 1.0;
+    for (int k = 0; k < 3; ++k) {
+      sd[p].psi[k] = 1.0;
+      cd[p].B0[k] = 1.0;
+    }
+    cd[p].A0 = 0.55;
+  }
+  CK(cudaMemcpyAsync(c->sprm, sd.data(), nprob * sizeof(StokesDev), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->cprm, cd.data(), nprob * sizeof(SoluteDev), cudaMemcpyHostToDevice, c->st));
+  const Sym<T> sym = sym_of<T>(c, deriv);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  acm_status st = ACM_OK;
+  for (const TuneJob& j : TUNE_JOBS) {
+    if (j.solute && c->spec_comps < 4) continue;
+    const int n = j.axis == 1 ? c->g.n1 : c->g.n0;
+    float best = 0;
+    int best_sh = 0;
+    for (int sh = -1; sh <= 1 && st == ACM_OK; ++sh) {
+      if (!Ops<T>::tx_variant(n, j.op, j.nc, sh)) continue;
+      Geo g = c->g;
+      g.txs[pr][j.axis][j.op] = (signed char)sh;
+      const long long ps = (long long)j.nc * g.S;
+      StokesDev* sp = j.solute ? nullptr : c->sprm;
+      SoluteDev* cp = j.solute ? c->cprm : nullptr;
+      void* s0 = j.op == P_STOKES || j.op == P_SOLUTE ? w.st0 : nullptr;
+      void* s1 = j.op == P_STOKES ? w.st1 : nullptr;
+      double* part = j.op == P_STOKES || j.op == P_SOLUTE ? c->part_z : nullptr;
+      float ms = 0;
+      for (int r = 0; r < 2 + TUNE_REPS && st == ACM_OK; ++r) {
+        if (r == 2 && cudaEventRecord(e0, c->st) != cudaSuccess) st = ACM_ERR_CUDA;
+        if (Ops<T>::pass(g, j.axis, j.op, j.nc, nprob, w.spec, ps, sym, w.tw, s0, s1, sp, cp, part, c->st) !=
+            cudaSuccess)
+          st = ACM_ERR_CUDA;
+      }
+      if (st == ACM_OK && (cudaEventRecord(e1, c->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = ACM_ERR_CUDA;
+      if (st == ACM_OK && (sh == -1 || best == 0 || ms < best)) {
+        if (best == 0 || ms < best) {
+          best = ms;
+          best_sh = sh;
+        }
+      }
+    }
+    if (st != ACM_OK) break;
+    c->g.txs[pr][j.axis][j.op] = (signed char)best_sh;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ACM_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  // a captured loop holds the old launches
+  if (c->graph.exec) {
+    cudaGraphExecDestroy(c->graph.exec);
+    c->graph.exec = nullptr;
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return ACM_OK;
+}
+
+// tile widths of the tuned passes (0 where a pass does not apply)
+void tiles_of(const acm_ctx* c, int fp64, int tiles[5]) {
+  for (int i = 0; i < 5; ++i) {
+    const TuneJob& j = TUNE_JOBS[i];
+    tiles[i] = j.solute && c->spec_comps < 4
+                   ? 0
+                   : (fp64 ? Ops<double>::pass_tx(c->g, j.axis, j.op, j.nc) : Ops<float>::pass_tx(c->g, j.axis, j.op, j.nc));
+  }
+}
+
 // A context for grids of one shape with room for B problems (loads) and
 // `ncells` indicator grids (cells of a batch; problem p uses cell p / lph).
 acm_status ctx_create(acm_ctx** out, int n0, int n1, int n2, void* stream, int B, int ncells) {
@@ -1168,8 +1268,13 @@ acm_status ctx_create(acm_ctx** out, int n0, int n1, int n2, void* stream, int B
   g.lph = 1;
   c->st = (cudaStream_t)stream;
   const int nbx = Ops<float>::x_blocks(g);
-  const int nbz = std::max(std::max(Ops<float>::z_blocks(g, P_STOKES), Ops<float>::z_blocks(g, P_SOLUTE)),
-                           std::max(Ops<double>::z_blocks(g, P_STOKES), Ops<double>::z_blocks(g, P_SOLUTE)));
+  // partial sums sized for the narrowest tile variant the autotuner may pick
+  Geo gn = g;
+  for (int pr = 0; pr < 2; ++pr)
+    for (int ax = 0; ax < 2; ++ax)
+      for (int op = 0; op < 6; ++op) gn.txs[pr][ax][op] = -1;
+  const int nbz = std::max(std::max(Ops<float>::z_blocks(gn, P_STOKES), Ops<float>::z_blocks(gn, P_SOLUTE)),
+                           std::max(Ops<double>::z_blocks(gn, P_STOKES), Ops<double>::z_blocks(gn, P_SOLUTE)));
   c->nbx = nbx;
   c->nbz = nbz;
   bool ok = cudaMalloc(&c->sprm, (size_t)B * sizeof(StokesDev)) == cudaSuccess &&
@@ -1512,6 +1617,67 @@ acm_status acm_batch_profile_read(acm_batch* b, double* ms, long long* launches)
     if (launches) launches[k] = cnt[k];
   }
   return ACM_OK;
+}
+
+acm_status acm_autotune(acm_ctx* c, int fp64, int deriv, int tiles[5]) {
+  if (!c || (fp64 != 0 && fp64 != 1) || (deriv != 0 && deriv != 1)) return ACM_ERR_ARG;
+  CKS(fp64 ? autotune_ctx<double>(c, c->B, deriv) : autotune_ctx<float>(c, c->B, deriv));
+  if (tiles) tiles_of(c, fp64, tiles);
+  return ACM_OK;
+}
+
+acm_status acm_set_tiles(acm_ctx* c, int fp64, const int tiles[5]) {
+  if (!c || !tiles || (fp64 != 0 && fp64 != 1)) return ACM_ERR_ARG;
+  Geo g = c->g;
+  for (int i = 0; i < 5; ++i) {
+    const TuneJob& j = TUNE_JOBS[i];
+    if (j.solute && c->spec_comps < 4) continue;
+    const int n = j.axis == 1 ? g.n1 : g.n0;
+    bool found = false;
+    for (int sh = -1; sh <= 1 && !found; ++sh) {
+      if (!(fp64 ? Ops<double>::tx_variant(n, j.op, j.nc, sh) : Ops<float>::tx_variant(n, j.op, j.nc, sh))) continue;
+      g.txs[fp64][j.axis][j.op] = (signed char)sh;
+      const int tx = fp64 ? Ops<double>::pass_tx(g, j.axis, j.op, j.nc) : Ops<float>::pass_tx(g, j.axis, j.op, j.nc);
+      found = tx == tiles[i];
+    }
+    if (!found) return ACM_ERR_ARG;
+  }
+  c->g = g;
+  if (c->graph.exec) {
+    cudaGraphExecDestroy(c->graph.exec);
+    c->graph.exec = nullptr;
+  }
+  return ACM_OK;
+}
+
+acm_status acm_get_tiles(acm_ctx* c, int fp64, int tiles[5]) {
+  if (!c || !tiles || (fp64 != 0 && fp64 != 1)) return ACM_ERR_ARG;
+  tiles_of(c, fp64, tiles);
+  return ACM_OK;
+}
+
+acm_status acm_batch_autotune(acm_batch* b, int fp64, int deriv) {
+  if (!b || (fp64 != 0 && fp64 != 1) || (deriv != 0 && deriv != 1)) return ACM_ERR_ARG;
+  for (auto& gr : b->groups) {
+    const int np = 3 * (int)gr.cells.size();
+    CKS(fp64 ? autotune_ctx<double>(gr.c, np, deriv) : autotune_ctx<float>(gr.c, np, deriv));
+  }
+  if (b->graph.exec) {
+    cudaGraphExecDestroy(b->graph.exec);
+    b->graph.exec = nullptr;
+  }
+  return ACM_OK;
+}
+
+acm_status acm_batch_tiles(acm_batch* b, int cell, int fp64, int tiles[5]) {
+  if (!b || !tiles || cell < 0 || cell >= b->ncells || (fp64 != 0 && fp64 != 1)) return ACM_ERR_ARG;
+  for (auto& gr : b->groups)
+    for (int c : gr.cells)
+      if (c == cell) {
+        tiles_of(gr.c, fp64, tiles);
+        return ACM_OK;
+      }
+  return ACM_ERR_ARG;
 }
 
 acm_status acm_batch_history_enable(acm_batch* b, int cap) {

@@ -15,6 +15,10 @@ struct Ops {
   // blocks per problem of the x-passes and of a z-pass (number of partial sums)
   static int x_blocks(const Geo& g);
   static int z_blocks(const Geo& g, int op);
+  // tile width (columns) a strided pass launches with under g's tile choice, and
+  // whether the choice `shift` (-1, 0, +1) has its own compiled variant
+  static int pass_tx(const Geo& g, int axis, int op, int nc);
+  static bool tx_variant(int n, int op, int nc, int shift);
 
   static cudaError_t x_stokes_local(const Geo& g, int nprob, const void* spec, void* u, void* lam,
                                     const uint8_t* H, StokesDev* prm, double* part, const void* tw,

@@ -105,11 +105,36 @@ static cudaError_t l_x_c2r(const Geo& g, int nprob, int nc, const void* spec, lo
   return cudaErrorInvalidValue;
 }
 
+// Autotuner candidates: the passes of the solver loops at N >= 64 also exist
+// with half and double the default tile width, when the variant stays within
+// 2..32 columns, 512 threads and 200 KB of shared memory.
+template <int N, int OP, int NC>
+constexpr bool tunable() {
+  return N >= 64 && ((OP == OP_FWD && (NC == 3 || NC == 4)) || (OP == OP_INV && NC == 3) || OP == OP_STOKES ||
+                     OP == OP_SOLUTE);
+}
+
+template <typename T, int N, int OP, int NC, int TX>
+constexpr bool tx_ok() {
+  return TX >= 2 && TX <= 32 && NC * TX * (N / ept(N)) <= 512 &&
+         (NC * TX * line_stride(N, N / ept(N), TX, wave_slots<T>()) + tw_total(N)) * (int)sizeof(cx<T>) <= 200 * 1024;
+}
+
+// tile width of (T, N, OP, NC) under the choice `shift`
 template <typename T, int N, int OP, int NC>
-static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
-                            const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
-                            cudaStream_t s, int dm) {
-  constexpr int TX = pick_tx((int)sizeof(cx<T>), N, NC);
+constexpr int resolved_tx(int shift) {
+  constexpr int TX0 = pick_tx((int)sizeof(cx<T>), N, NC);
+  if (tunable<N, OP, NC>()) {
+    if (shift < 0 && tx_ok<T, N, OP, NC, TX0 / 2>()) return TX0 / 2;
+    if (shift > 0 && tx_ok<T, N, OP, NC, TX0 * 2>()) return TX0 * 2;
+  }
+  return TX0;
+}
+
+template <typename T, int N, int OP, int NC, int TX>
+static cudaError_t l_pass_kt(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
+                             const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
+                             cudaStream_t s, int dm) {
   using C = SCfg<T, N, OP, NC, TX>;
   static const cudaError_t attr = set_smem(k_strided<T, N, OP, NC, TX>, C::SMEM);
   if (attr != cudaSuccess) return attr;
@@ -142,6 +167,42 @@ static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long 
   return cudaGetLastError();
 }
 
+template <typename T, int N, int OP, int NC>
+static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
+                            const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
+                            cudaStream_t s, int dm) {
+  constexpr int TX0 = pick_tx((int)sizeof(cx<T>), N, NC);
+  if constexpr (tunable<N, OP, NC>()) {
+    const int sh = g.txs[sizeof(T) == 8][axis][OP];
+    if constexpr (tx_ok<T, N, OP, NC, TX0 / 2>())
+      if (sh < 0)
+        return l_pass_kt<T, N, OP, NC, TX0 / 2>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm,
+                                                part, s, dm);
+    if constexpr (tx_ok<T, N, OP, NC, TX0 * 2>())
+      if (sh > 0)
+        return l_pass_kt<T, N, OP, NC, TX0 * 2>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm,
+                                                part, s, dm);
+  }
+  return l_pass_kt<T, N, OP, NC, TX0>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, s, dm);
+}
+
+template <typename T, int N>
+static int l_pass_tx(int op, int nc, int shift) {
+#define ACM_TX(OPV, NCV) \
+  if (op == OPV && nc == NCV) return resolved_tx<T, N, OPV, NCV>(shift);
+  ACM_TX(OP_FWD, 1)
+  ACM_TX(OP_FWD, 3)
+  ACM_TX(OP_FWD, 4)
+  ACM_TX(OP_INV, 1)
+  ACM_TX(OP_INV, 3)
+  ACM_TX(OP_INV_SCALE, 1)
+  ACM_TX(OP_STOKES, 3)
+  ACM_TX(OP_SOLUTE, 4)
+  ACM_TX(OP_DERIV, 1)
+#undef ACM_TX
+  return 0;
+}
+
 template <typename T, int N>
 static cudaError_t l_pass(const Geo& g, int axis, int op, int nc, int nprob, void* spec, long long ps,
                           const Sym<T>& sym, const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm,
@@ -170,9 +231,34 @@ int Ops<T>::x_blocks(const Geo& g) {
 }
 
 template <typename T>
+int Ops<T>::pass_tx(const Geo& g, int axis, int op, int nc) {
+  const int n = axis == 1 ? g.n1 : g.n0;
+  const int sh = g.txs[sizeof(T) == 8][axis][op];
+  switch (n) {
+    case 8: return l_pass_tx<T, 8>(op, nc, sh);
+    case 16: return l_pass_tx<T, 16>(op, nc, sh);
+    case 32: return l_pass_tx<T, 32>(op, nc, sh);
+    case 64: return l_pass_tx<T, 64>(op, nc, sh);
+    case 128: return l_pass_tx<T, 128>(op, nc, sh);
+    case 256: return l_pass_tx<T, 256>(op, nc, sh);
+    case 512: return l_pass_tx<T, 512>(op, nc, sh);
+    default: return 0;
+  }
+}
+
+template <typename T>
+bool Ops<T>::tx_variant(int n, int op, int nc, int shift) {
+  Geo g;
+  g.n0 = g.n1 = n;
+  const int t0 = pass_tx(g, 0, op, nc);
+  g.txs[sizeof(T) == 8][0][op] = (signed char)shift;
+  return shift == 0 || pass_tx(g, 0, op, nc) != t0;
+}
+
+template <typename T>
 int Ops<T>::z_blocks(const Geo& g, int op) {
   const int nc = op == P_SOLUTE ? 4 : 3;
-  const int tx = pick_tx((int)sizeof(cx<T>), g.n0, nc);
+  const int tx = pass_tx(g, 0, op, nc);
   return ((g.Pu + tx - 1) / tx) * g.n1;
 }
 
