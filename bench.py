@@ -25,6 +25,8 @@ import time
 
 import numpy as np
 
+from paper_2312_15554_gb300 import shard as SH
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -238,8 +240,7 @@ def run_gpu(args, rank, world, dist):
     acm.acm_profile_read(ctx)                      # reset counters
     acm.acm_profile_enable(ctx, True)
     sampler = ClockSampler(local) if rank == 0 else None
-    if dist is not None:
-        dist.barrier()
+    SH.barrier(dist)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -248,32 +249,22 @@ def run_gpu(args, rank, world, dist):
         K, Ds = step(Hd)
     e1.record(stream)
     torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
+    SH.barrier(dist)
     clocks = sampler.stop() if sampler else None
     prof = acm.acm_profile_read(ctx)
     acm.acm_profile_enable(ctx, False)
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = SH.max_over_ranks(e0.elapsed_time(e1), dist, dev)
     value = vi_per_step * args.steps * world / (ms / 1e3)
 
     # end to end through the public API with host buffers: H from pinned host
     # memory every call, K and D read back to the host
     torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
+    SH.barrier(dist)
     t0 = time.perf_counter()
     for _ in range(max(1, args.steps // 2)):
         K, Ds = step(H_pin.numpy())
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / max(1, args.steps // 2)
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = SH.max_over_ranks((time.perf_counter() - t0) / max(1, args.steps // 2), dist, dev)
     e2e_value = vi_per_step * world / e2e_s
 
     # roofline of the dominant kernel (largest device time in the timed region)
@@ -337,7 +328,7 @@ def run_batched(args, rank, world, dist):
     """Many cells in one device-resident solve (Stokes, three loads per cell)."""
     import concurrent.futures as cf
     import multiprocessing as mp
-    idx = list(range(rank * args.cells, (rank + 1) * args.cells))
+    idx = list(SH.shard(args.cells * world, rank, world))   # the same number of cells per rank (weak scaling)
     with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
                                 mp_context=mp.get_context("spawn")) as ex:
         Hs = list(ex.map(_batched_cell, idx, chunksize=4))
@@ -383,10 +374,8 @@ def run_batched(args, rank, world, dist):
     prof = acm.acm_batch_profile_read(batch)
     acm.acm_batch_profile_enable(batch, False)
     batch.close()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = SH.max_over_ranks(ms, dist, dev)
+    K_all = SH.gather_rows(K, args.cells * world, dist, dev, world)
     if rank != 0:
         return
     line = {
@@ -398,7 +387,8 @@ def run_batched(args, rank, world, dist):
                    "device_loop": "CUDA graph while node", "tiles": tiles, "autotune_s": round(tune_s, 3)},
         "clocks": clocks,
         "kernels_profiled_step": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]},
-        "K_mean_diag_cell0": [float(K[0, i, i]) for i in range(3)],
+        "K_mean_diag_cell0": [float(K_all[0, i, i]) for i in range(3)],
+        "cells_all_ranks": int(K_all.shape[0]),
     }
     print(json.dumps(line), flush=True)
 
