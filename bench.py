@@ -54,10 +54,11 @@ def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float) -> float:
         "y_fwd_stokes": 6 * cspec,
         "z_stokes": 10 * cspec,
         "y_inv_stokes": 6 * cspec,
-        "x_solute": 3 * cspec + 12.0 * porosity + 1.0 + 4 * cspec,
-        "y_fwd_solute": 8 * cspec,
-        "z_solute": 9 * cspec,
-        "y_inv_solute": 6 * cspec,
+        # solute passes carry (tau_0, tau_1, s') -> (tau_0, s'') -> (d0 chi, chi) -> (d0 chi, d1 chi, chi)
+        "x_solute": 3 * cspec + 12.0 * porosity + 1.0 + 3 * cspec,
+        "y_fwd_solute": 5 * cspec,
+        "z_solute": 6 * cspec,
+        "y_inv_solute": 5 * cspec,
     }.get(kind, 0.0)
 
 

@@ -223,21 +223,21 @@ acm_status acm_batch_stokes(acm_batch* batch, const uint8_t* const* H, const acm
                             void* const* lambda_out, double* K, acm_report* rep);
 /* Tile autotuner. The strided FFT passes of the solver loops (y forward and
  * inverse of the Stokes iteration, the z pass with the Green step of Eq. 13,
- * the y forward and z pass of the solute iteration, Eq. 20) exist in up to
+ * the y forward, z pass (Eq. 20) and y inverse of the solute iteration) exist in up to
  * three tile widths (columns per block). acm_autotune times each candidate on
  * the context's workspace and stream and keeps the fastest for that precision
  * (fp64 0/1) and derivative symbol; acm_batch_autotune does so per cell shape
  * with the batch's problem count. Fields do not depend on the choice; only the
  * summation order of the FP64 residual partials does. tiles (out, nullable):
- * the widths in the order y-forward(3), z-Stokes, y-inverse(3), y-forward(4),
- * z-solute (0 where a pass does not apply). acm_set_tiles sets them explicitly
+ * the widths in the order y-forward Stokes, z Stokes, y-inverse Stokes,
+ * y-forward solute, z solute, y-inverse solute (0 where a pass does not apply). acm_set_tiles sets them explicitly
  * (ACM_ERR_ARG for a width that has no compiled variant); acm_get_tiles reads
  * the current widths. Call between solves. */
-acm_status acm_autotune(acm_ctx* ctx, int fp64, int deriv, int tiles[5]);
-acm_status acm_set_tiles(acm_ctx* ctx, int fp64, const int tiles[5]);
-acm_status acm_get_tiles(acm_ctx* ctx, int fp64, int tiles[5]);
+acm_status acm_autotune(acm_ctx* ctx, int fp64, int deriv, int tiles[6]);
+acm_status acm_set_tiles(acm_ctx* ctx, int fp64, const int tiles[6]);
+acm_status acm_get_tiles(acm_ctx* ctx, int fp64, int tiles[6]);
 acm_status acm_batch_autotune(acm_batch* batch, int fp64, int deriv);
-acm_status acm_batch_tiles(acm_batch* batch, int cell, int fp64, int tiles[5]);
+acm_status acm_batch_tiles(acm_batch* batch, int cell, int fp64, int tiles[6]);
 
 /* Per-iteration records of every problem of a batch (the Stokes record of
  * acm_history: residuals, tolerances, penalties, mean velocity), off by default.

@@ -341,26 +341,26 @@ def acm_batch_stokes(batch, Hs, params=None, u_out=None, init_u=None, init_lambd
     return s, np.array(K[:]).reshape(n, 3, 3), [list(reps[3 * i:3 * i + 3]) for i in range(n)]
 
 
-TILE_PASSES = ("y_fwd_stokes", "z_stokes", "y_inv", "y_fwd_solute", "z_solute")
+TILE_PASSES = ("y_fwd_stokes", "z_stokes", "y_inv_stokes", "y_fwd_solute", "z_solute", "y_inv_solute")
 
 
 def acm_autotune(ctx, fp64: bool = False, deriv: int = DERIV_EXACT):
     """Times the tile widths of the strided passes; returns {pass: width}."""
-    t = (C.c_int * 5)()
+    t = (C.c_int * 6)()
     _check(load().acm_autotune(ctx.h, int(fp64), int(deriv), t), "acm_autotune")
     return dict(zip(TILE_PASSES, list(t)))
 
 
 def acm_set_tiles(ctx, tiles, fp64: bool = False):
-    """tiles: {pass: width} or five widths in TILE_PASSES order."""
+    """tiles: {pass: width} or six widths in TILE_PASSES order."""
     if isinstance(tiles, dict):
         tiles = [tiles[k] for k in TILE_PASSES]
-    t = (C.c_int * 5)(*[int(x) for x in tiles])
+    t = (C.c_int * 6)(*[int(x) for x in tiles])
     _check(load().acm_set_tiles(ctx.h, int(fp64), t), "acm_set_tiles")
 
 
 def acm_get_tiles(ctx, fp64: bool = False):
-    t = (C.c_int * 5)()
+    t = (C.c_int * 6)()
     _check(load().acm_get_tiles(ctx.h, int(fp64), t), "acm_get_tiles")
     return dict(zip(TILE_PASSES, list(t)))
 
@@ -370,7 +370,7 @@ def acm_batch_autotune(batch, fp64: bool = False, deriv: int = DERIV_EXACT):
 
 
 def acm_batch_tiles(batch, cell: int, fp64: bool = False):
-    t = (C.c_int * 5)()
+    t = (C.c_int * 6)()
     _check(load().acm_batch_tiles(batch.h, cell, int(fp64), t), "acm_batch_tiles")
     return dict(zip(TILE_PASSES, list(t)))
 

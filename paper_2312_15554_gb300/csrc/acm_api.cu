@@ -69,6 +69,7 @@ struct acm_ctx {
   uint8_t* Hd = nullptr;
   unsigned long long* cnt = nullptr;
   double* hist = nullptr;
+  int solute_deriv = 1;      // derivative symbol of the last solute iteration
   double* hist_b = nullptr;  // batches: [B][hist_b_cap][STOKES_HIST] when enabled
   int hist_b_cap = 0;
   int hist_kind = 0;  // 1: Stokes (16 doubles / record), 2: solute (4 doubles / record)
@@ -795,6 +796,7 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
   g.us = us;
   const size_t cs = 2 * sizeof(T);
   const Sym<T> sym = sym_of<T>(c, P.deriv);
+  c->solute_deriv = P.deriv;
   if (setup) {
     CK(cudaMemsetAsync(w.st0, 0, (size_t)nprob * g.S * cs, c->st));
     CK(cudaMemsetAsync(w.spec, 0, (size_t)nprob * 4 * g.S * cs, c->st));
@@ -828,13 +830,15 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
     const int chunk = ce < remaining ? ce : remaining;
     remaining -= chunk;
     for (int k = 0; k < chunk; ++k) {
-      LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->cprm, w.tw, c->st));
-      LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD, 4, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm, nullptr,
+      // spectral components per problem: x -> (tau_0, tau_1, s + d2 tau_2), y forward -> (tau_0, s''),
+      // z -> (d0 chi, chi), y inverse -> (d0 chi, d1 chi, chi); the x pass takes d2 of the last
+      LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->cprm, w.tw, sym, c->st));
+      LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
+                      nullptr, c->st));
+      LK(ACM_K_Z_SOLUTE, Ops<T>::pass(g, 0, P_SOLUTE, 2, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm, c->part_z,
                       c->st));
-      LK(ACM_K_Z_SOLUTE, Ops<T>::pass(g, 0, P_SOLUTE, 4, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm, c->part_z,
-                      c->st));
-      LK(ACM_K_Y_INV_SOLUTE, Ops<T>::pass(g, 1, P_INV, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm, nullptr,
-                      c->st));
+      LK(ACM_K_Y_INV_SOLUTE, Ops<T>::pass(g, 1, P_INV_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
+                      nullptr, c->st));
       LK(ACM_K_FINALIZE, solute_finalize(nprob, c->cprm, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
     }
     CK(cudaMemcpyAsync(c->pin, c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
@@ -858,7 +862,10 @@ acm_status solute_outputs(acm_ctx* c, int nprob, const uint8_t* Hdev, const void
   CKS(ensure_aux<T>(c));
   T* grad = (T*)w.aux;
   T* chi = (T*)w.aux + (size_t)c->B * 3 * g.V;
-  // grad chi^{n+1}: the last pass left i d chi^ (inverse along z and y) in components 0..2
+  // grad chi^{n+1}: the last passes left i d0 chi^, i d1 chi^ and chi^ (inverse along z
+  // and y) in components 0..2; the axis-2 derivative is taken here
+  const Sym<T> symp = sym_of<T>(c, c->solute_deriv);
+  LK(ACM_K_OTHER, Ops<T>::mul_id2(g, nprob, w.spec, 4 * g.S, symp, c->st));
   LK(ACM_K_OTHER, Ops<T>::x_c2r(g, nprob, 3, w.spec, 4 * g.S, grad, 3 * g.V, w.tw, c->st));
   // chi^{n+1}
   LK(ACM_K_OTHER, Ops<T>::pass(g, 0, P_INV_SCALE, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -1153,8 +1160,9 @@ struct TuneJob {
   int axis, op, nc;
   bool solute;
 };
-constexpr TuneJob TUNE_JOBS[] = {{1, P_FWD, 3, false}, {0, P_STOKES, 3, false}, {1, P_INV, 3, false},
-                                 {1, P_FWD, 4, true},  {0, P_SOLUTE, 4, true}};
+constexpr TuneJob TUNE_JOBS[] = {{1, P_FWD, 3, false},    {0, P_STOKES, 3, false}, {1, P_INV, 3, false},
+                                 {1, P_FWD_SOL, 3, true}, {0, P_SOLUTE, 2, true},  {1, P_INV_SOL, 3, true}};
+constexpr int NTUNE = (int)(sizeof(TUNE_JOBS) / sizeof(TUNE_JOBS[0]));
 constexpr int TUNE_REPS = 5;
 
 template <typename T>
@@ -1233,8 +1241,8 @@ acm_status autotune_ctx(acm_ctx* c, int nprob, int deriv) {
 }
 
 // tile widths of the tuned passes (0 where a pass does not apply)
-void tiles_of(const acm_ctx* c, int fp64, int tiles[5]) {
-  for (int i = 0; i < 5; ++i) {
+void tiles_of(const acm_ctx* c, int fp64, int tiles[NTUNE]) {
+  for (int i = 0; i < NTUNE; ++i) {
     const TuneJob& j = TUNE_JOBS[i];
     tiles[i] = j.solute && c->spec_comps < 4
                    ? 0
@@ -1619,17 +1627,17 @@ acm_status acm_batch_profile_read(acm_batch* b, double* ms, long long* launches)
   return ACM_OK;
 }
 
-acm_status acm_autotune(acm_ctx* c, int fp64, int deriv, int tiles[5]) {
+acm_status acm_autotune(acm_ctx* c, int fp64, int deriv, int tiles[NTUNE]) {
   if (!c || (fp64 != 0 && fp64 != 1) || (deriv != 0 && deriv != 1)) return ACM_ERR_ARG;
   CKS(fp64 ? autotune_ctx<double>(c, c->B, deriv) : autotune_ctx<float>(c, c->B, deriv));
   if (tiles) tiles_of(c, fp64, tiles);
   return ACM_OK;
 }
 
-acm_status acm_set_tiles(acm_ctx* c, int fp64, const int tiles[5]) {
+acm_status acm_set_tiles(acm_ctx* c, int fp64, const int tiles[NTUNE]) {
   if (!c || !tiles || (fp64 != 0 && fp64 != 1)) return ACM_ERR_ARG;
   Geo g = c->g;
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < NTUNE; ++i) {
     const TuneJob& j = TUNE_JOBS[i];
     if (j.solute && c->spec_comps < 4) continue;
     const int n = j.axis == 1 ? g.n1 : g.n0;
@@ -1650,7 +1658,7 @@ acm_status acm_set_tiles(acm_ctx* c, int fp64, const int tiles[5]) {
   return ACM_OK;
 }
 
-acm_status acm_get_tiles(acm_ctx* c, int fp64, int tiles[5]) {
+acm_status acm_get_tiles(acm_ctx* c, int fp64, int tiles[NTUNE]) {
   if (!c || !tiles || (fp64 != 0 && fp64 != 1)) return ACM_ERR_ARG;
   tiles_of(c, fp64, tiles);
   return ACM_OK;
@@ -1669,7 +1677,7 @@ acm_status acm_batch_autotune(acm_batch* b, int fp64, int deriv) {
   return ACM_OK;
 }
 
-acm_status acm_batch_tiles(acm_batch* b, int cell, int fp64, int tiles[5]) {
+acm_status acm_batch_tiles(acm_batch* b, int cell, int fp64, int tiles[NTUNE]) {
   if (!b || !tiles || cell < 0 || cell >= b->ncells || (fp64 != 0 && fp64 != 1)) return ACM_ERR_ARG;
   for (auto& gr : b->groups)
     for (int c : gr.cells)

@@ -129,16 +129,25 @@ __device__ __forceinline__ void x_load_spec_raw_async(cx<T>* sm, cx<T>* nyq, con
   }
 }
 
+// With dc >= 0 the lines of component dc are first multiplied by i d(k)
+// (d: the derivative symbol of the kx axis, M + 1 values): they become the
+// half spectrum of that component's derivative along the line.
 template <typename T, int N2, int NC>
-__device__ __forceinline__ void x_pre_smem(cx<T>* sm, const cx<T>* nyq, const cx<T>* twx) {
+__device__ __forceinline__ void x_pre_smem(cx<T>* sm, const cx<T>* nyq, const cx<T>* twx, int dc = -1,
+                                           const T* __restrict__ d = nullptr) {
   using C = XCfg<T, N2>;
   constexpr int M = C::M;
   const cx<T>* tw = twx + tw_total(M);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int cl = warp; cl < NC * C::LPB; cl += nw) {
     cx<T>* s = sm + cl * C::LS;
+    const bool der = cl / C::LPB == dc;
     for (int k = lane; k <= M / 2; k += 32) {
-      const cx<T> X = s[pad(k)], Y = (k == 0) ? nyq[cl] : s[pad(M - k)];
+      cx<T> X = s[pad(k)], Y = (k == 0) ? nyq[cl] : s[pad(M - k)];
+      if (der) {
+        X = cscale(mul_i(X), d[k]);
+        Y = cscale(mul_i(Y), d[M - k]);
+      }
       const cx<T> e1 = X + cconj(Y), o1 = cmul(X - cconj(Y), cconj(tw[k]));
       const cx<T> e2 = Y + cconj(X), o2 = cmul(Y - cconj(X), cconj(tw[M - k]));
       s[pad(k)] = e1 + mul_i(o1);
@@ -173,6 +182,52 @@ __device__ __forceinline__ void x_post_store_spec(const cx<T>* sm, cx<T>* __rest
         dst[k] = ak - mul_i(cmul(tw[k], bk));
         dst[M - k] = am - mul_i(cmul(tw[M - k], bm));
       }
+    }
+  }
+}
+
+// Solute x-pass output: lines (tau_0, tau_1, tau_2, s) -> half spectra
+// (tau_0, tau_1, s + i d2 tau_2) in components 0..2. Adding the axis-2 term of
+// i d.tau^ (Eq. 18 in Fourier space) here, where kx is already known, leaves
+// three components for the y pass instead of four.
+template <typename T, int N2>
+__device__ __forceinline__ void x_post_store_solute(const cx<T>* sm, cx<T>* __restrict__ spec, long long S, int P,
+                                                    int line0, const cx<T>* twx, const T* __restrict__ d2) {
+  using C = XCfg<T, N2>;
+  constexpr int M = C::M;
+  const cx<T>* tw = twx + tw_total(M);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T half = (T)0.5;
+  // half spectrum value at k (and M - k) of the line in shared memory
+  auto post = [&](const cx<T>* s, int k, cx<T>& Xk, cx<T>& Xm) {
+    const cx<T> Zk = s[pad(k)];
+    if (k == 0) {
+      Xk = mk<T>(Zk.x + Zk.y, (T)0);
+      Xm = mk<T>(Zk.x - Zk.y, (T)0);
+    } else {
+      const cx<T> Zm = s[pad(M - k)];
+      const cx<T> ak = cscale(Zk + cconj(Zm), half), bk = cscale(Zk - cconj(Zm), half);
+      const cx<T> am = cscale(Zm + cconj(Zk), half), bm = cscale(Zm - cconj(Zk), half);
+      Xk = ak - mul_i(cmul(tw[k], bk));
+      Xm = am - mul_i(cmul(tw[M - k], bm));
+    }
+  };
+  for (int cl = warp; cl < 3 * C::LPB; cl += nw) {
+    const int c = cl / C::LPB, l = cl - c * C::LPB;
+    cx<T>* dst = spec + c * S + (long long)(line0 + l) * P;
+    const cx<T>* s = sm + cl * C::LS;
+    const cx<T>* s3 = sm + (3 * C::LPB + l) * C::LS;
+    for (int k = lane; k <= M / 2; k += 32) {
+      cx<T> Xk, Xm;
+      post(s, k, Xk, Xm);
+      if (c == 2) {
+        cx<T> Sk, Sm;
+        post(s3, k, Sk, Sm);
+        Xk = Sk + cscale(mul_i(Xk), d2[k]);
+        Xm = Sm + cscale(mul_i(Xm), d2[M - k]);
+      }
+      dst[k] = Xk;
+      dst[M - k] = Xm;
     }
   }
 }
@@ -318,7 +373,7 @@ template <typename T, int N2>
 __global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, const T* __restrict__ u,
                                                     const uint8_t* __restrict__ H,
                                                     const SoluteDev* __restrict__ prm, Geo g,
-                                                    const cx<T>* __restrict__ twg) {
+                                                    const cx<T>* __restrict__ twg, const T* __restrict__ d2) {
   using C = XCfg<T, N2>;
   using Lay = XLayout<T, N2, 4, 3>;
   constexpr int TOT = Lay::TOT;
@@ -350,7 +405,8 @@ __global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, c
     cp_async_pred<(int)sizeof(T)>(su + i, up + c * g.V + v0 + e, sh[e] == 0);
   }
   cp_async_commit();
-  x_pre_smem<T, N2, 3>(sm, nyq, tw);
+  // components 0, 1 hold the x spectra of d0 chi and d1 chi, component 2 that of chi
+  x_pre_smem<T, N2, 3>(sm, nyq, tw, 2, d2);
   __syncthreads();
   x_fft<T, N2, 3, +1>(sm, tw);
   cp_async_wait<0>();
@@ -373,7 +429,7 @@ __global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, c
   __syncthreads();
   x_fft<T, N2, 4, -1>(sm, tw);
   __syncthreads();
-  x_post_store_spec<T, N2, 4>(sm, sp, g.S, g.P, line0, tw);
+  x_post_store_solute<T, N2>(sm, sp, g.S, g.P, line0, tw, d2);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,7 +487,12 @@ __global__ void __launch_bounds__(NC * 64) k_x_c2r(const cx<T>* __restrict__ spe
 // columns, with an optional per-wavevector operator between a forward and an
 // inverse transform (z-pass only).
 // ---------------------------------------------------------------------------
-enum { OP_FWD = 0, OP_INV = 1, OP_INV_SCALE = 2, OP_STOKES = 3, OP_SOLUTE = 4, OP_DERIV = 5 };
+// OP_FWD_SOL (y forward of the solute iteration): lines (tau_0, tau_1, s') in,
+//   (tau_0, s' + i d1 tau_1) out.
+// OP_SOLUTE (z): (tau_0, s'') in, F^ = s'' + i d0 tau_0, Green step, (i d0 chi^, chi^) out.
+// OP_INV_SOL (y inverse): (a, b) in, lines (a, i d1 b, b) inverse-transformed out.
+enum { OP_FWD = 0, OP_INV = 1, OP_INV_SCALE = 2, OP_STOKES = 3, OP_SOLUTE = 4, OP_DERIV = 5, OP_FWD_SOL = 6,
+       OP_INV_SOL = 7 };
 
 template <typename T>
 struct PassArgs {
@@ -450,12 +511,6 @@ struct PassArgs {
   double invV;
   int nkx;          // n2 / 2 (Nyquist column index)
   int dm;           // OP_DERIV: axis of the derivative
-};
-
-template <int OP>
-struct OpComps {
-  static constexpr int IN = (OP == OP_SOLUTE) ? 4 : (OP == OP_STOKES ? 3 : 1);
-  static constexpr int OUT = (OP == OP_SOLUTE) ? 3 : IN;
 };
 
 template <typename T, int N, int OP, int NC, int TX>
@@ -486,8 +541,8 @@ __device__ __forceinline__ void s_fft(cx<T>* sm, const cx<T>* tw) {
 template <typename T, int N, int OP, int NC, int TX>
 __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs<T> a) {
   using C = SCfg<T, N, OP, NC, TX>;
-  constexpr int NIN = (OP == OP_SOLUTE) ? 4 : NC;
-  constexpr int NOUT = (OP == OP_SOLUTE) ? 3 : NC;
+  constexpr int NIN = (OP == OP_INV_SOL) ? 2 : NC;
+  constexpr int NOUT = (OP == OP_FWD_SOL) ? 2 : NC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = sm + NC * TX * C::LS;
@@ -499,14 +554,25 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
   const int w = min(TX, a.Pu - kx0);
   for (int idx = threadIdx.x; idx < NIN * N * TX; idx += blockDim.x) {
     const int col = idx % TX, j = (idx / TX) % N, c = idx / (TX * N);
+    const int line = (OP == OP_INV_SOL && c == 1) ? 2 : c;   // OP_INV_SOL: b goes to line 2
     if (col < w)
-      cp_async<(int)sizeof(cx<T>)>(&sm[(c * TX + col) * C::LS + pad(j)], &base[c * a.compStride + j * a.rowStride + col]);
+      cp_async<(int)sizeof(cx<T>)>(&sm[(line * TX + col) * C::LS + pad(j)],
+                                   &base[c * a.compStride + j * a.rowStride + col]);
   }
   cp_async_commit();
   FillTw<T, N, 1, TW_MAX>::run(tw, a.twg);
   cp_async_wait<0>();
   __syncthreads();
-  if constexpr (OP == OP_INV || OP == OP_INV_SCALE) {
+  if constexpr (OP == OP_INV || OP == OP_INV_SCALE || OP == OP_INV_SOL) {
+    if constexpr (OP == OP_INV_SOL) {
+      // line 1 = i d1(ky) b: the axis-1 derivative of chi before its inverse transform
+      for (int idx = threadIdx.x; idx < N * TX; idx += blockDim.x) {
+        const int col = idx % TX, j = idx / TX;
+        const cx<T> b = sm[(2 * TX + col) * C::LS + pad(j)];
+        sm[(1 * TX + col) * C::LS + pad(j)] = cscale(mul_i(b), a.sym.d1[j]);
+      }
+      __syncthreads();
+    }
     if constexpr (OP == OP_INV_SCALE) {
       const T s = (T)a.invV;
       for (int idx = threadIdx.x; idx < NC * N * TX; idx += blockDim.x) {
@@ -519,6 +585,15 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
     s_fft<T, N, OP, NC, TX, +1, NC * TX>(sm, tw);
   } else {
     s_fft<T, N, OP, NC, TX, -1, NIN * TX>(sm, tw);
+  }
+  if constexpr (OP == OP_FWD_SOL) {
+    // s'' = s' + i d1(ky) tau_1 into line 1
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < N * TX; idx += blockDim.x) {
+      const int col = idx % TX, j = idx / TX;
+      cx<T>& t1 = sm[(1 * TX + col) * C::LS + pad(j)];
+      t1 = sm[(2 * TX + col) * C::LS + pad(j)] + cscale(mul_i(t1), a.sym.d1[j]);
+    }
   }
   if constexpr (OP == OP_DERIV) {
     __syncthreads();
@@ -580,8 +655,8 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
         const bool k0 = (j == 0 && ky == 0 && kx == 0);
         cx<T>* s0 = &sm[(0 * TX + col) * C::LS + pad(j)];
         cx<T>* s1 = &sm[(1 * TX + col) * C::LS + pad(j)];
-        cx<T>* s2 = &sm[(2 * TX + col) * C::LS + pad(j)];
         if constexpr (OP == OP_STOKES) {
+          cx<T>* s2 = &sm[(2 * TX + col) * C::LS + pad(j)];
           const cx<T> qh = sa[k];
           const cx<T> dprev = sb[k];
           // r = w^ - i d q^ (+ g V at k = 0)
@@ -623,9 +698,9 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
           *s1 = cscale(u1, invV);
           *s2 = cscale(u2, invV);
         } else {
-          cx<T>* s3 = &sm[(3 * TX + col) * C::LS + pad(j)];
-          // F^ = s^ + i d.tau^  (Eq. 18 in Fourier space)
-          const cx<T> F = *s3 + mul_i(cscale(*s0, d0) + cscale(*s1, d1) + cscale(*s2, d2));
+          // F^ = s^ + i d.tau^ (Eq. 18 in Fourier space): the axis-2 and axis-1
+          // terms were added in the x and y passes, line 1 holds s''
+          const cx<T> F = *s1 + mul_i(cscale(*s0, d0));
           // Eq. 20: chi^ = F^ / (i B0.d + A0 L), chi^(0) = 0
           const T dre = A0 * L, dim = B00 * d0 + B01 * d1 + B02 * d2;
           cx<T> chi = mk<T>(0, 0);
@@ -637,11 +712,11 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
           a.st0[gi] = chi;
           acc0 += wgt * cabs2(dch);
           acc1 += wgt * dd * cabs2(dch);
-          // grad chi^ = i d chi^, normalised for the inverse transform
-          const cx<T> ic = cscale(mul_i(chi), invV);
-          *s0 = cscale(ic, d0);
-          *s1 = cscale(ic, d1);
-          *s2 = cscale(ic, d2);
+          // i d0 chi^ and chi^, normalised for the inverse transform (the
+          // axis-1 and axis-2 derivatives are taken in the later passes)
+          const cx<T> cs = cscale(chi, invV);
+          *s0 = cscale(mul_i(cs), d0);
+          *s1 = cs;
         }
       }
     }
@@ -799,6 +874,18 @@ __global__ void k_div_spec(const cx<T>* __restrict__ uh, cx<T>* __restrict__ dv,
     }
     const cx<T> s = cscale(uh[i], sym.d0[kz]) + cscale(uh[g.S + i], sym.d1[ky]) + cscale(uh[2 * g.S + i], sym.d2[kx]);
     dv[i] = mul_i(s);
+  }
+}
+
+// spec[c] *= i d2(kx) on the half spectrum of one component per problem
+template <typename T>
+__global__ void k_mul_id2(cx<T>* __restrict__ spec, long long ps, Geo g, const T* __restrict__ d2) {
+  const int p = blockIdx.y;
+  cx<T>* sp = spec + (long long)p * ps;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)g.n0 * g.n1 * g.P;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % g.P);
+    if (kx < g.Pu) sp[i] = cscale(mul_i(sp[i]), d2[kx]);
   }
 }
 

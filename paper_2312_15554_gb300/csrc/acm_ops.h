@@ -8,7 +8,10 @@
 
 namespace acm {
 
-enum PassOp { P_FWD = 0, P_INV = 1, P_INV_SCALE = 2, P_STOKES = 3, P_SOLUTE = 4, P_DERIV = 5 };
+// P_FWD_SOL / P_INV_SOL: the y passes of the solute iteration (derivative
+// terms of axis 1 folded in; see the strided kernel); P_SOLUTE: its z pass.
+enum PassOp { P_FWD = 0, P_INV = 1, P_INV_SCALE = 2, P_STOKES = 3, P_SOLUTE = 4, P_DERIV = 5, P_FWD_SOL = 6,
+              P_INV_SOL = 7 };
 
 template <typename T>
 struct Ops {
@@ -26,7 +29,9 @@ struct Ops {
   static cudaError_t x_stokes_rhs(const Geo& g, int nprob, void* spec, const void* u, const void* lam,
                                   const uint8_t* H, const StokesDev* prm, const void* tw, cudaStream_t s);
   static cudaError_t x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                              const SoluteDev* prm, const void* tw, cudaStream_t s);
+                              const SoluteDev* prm, const void* tw, const Sym<T>& sym, cudaStream_t s);
+  // component 2 of each problem's spectrum (stride ps) times i d2(kx), in place
+  static cudaError_t mul_id2(const Geo& g, int nprob, void* spec, long long ps, const Sym<T>& sym, cudaStream_t s);
   // nc in {1, 3}
   static cudaError_t x_r2c(const Geo& g, int nprob, int nc, void* spec, long long specProbStride,
                            const void* in, long long inProbStride, const void* tw, cudaStream_t s);

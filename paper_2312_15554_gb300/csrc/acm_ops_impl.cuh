@@ -60,12 +60,12 @@ static cudaError_t l_x_rhs(const Geo& g, int nprob, void* spec, const void* u, c
 
 template <typename T, int N2>
 static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                              const SoluteDev* prm, const void* tw, cudaStream_t s) {
+                              const SoluteDev* prm, const void* tw, const T* d2, cudaStream_t s) {
   constexpr int smem = XLayout<T, N2, 4, 3>::BYTES;
   static const cudaError_t attr = set_smem(k_x_solute<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
   dim3 grid(g.n0 * g.n1 / XCfg<T, N2>::LPB, nprob);
-  k_x_solute<T, N2><<<grid, 4 * 64, smem, s>>>((cx<T>*)spec, (const T*)u, H, prm, g, (const cx<T>*)tw);
+  k_x_solute<T, N2><<<grid, 4 * 64, smem, s>>>((cx<T>*)spec, (const T*)u, H, prm, g, (const cx<T>*)tw, d2);
   return cudaGetLastError();
 }
 
@@ -110,8 +110,8 @@ static cudaError_t l_x_c2r(const Geo& g, int nprob, int nc, const void* spec, lo
 // 2..32 columns, 512 threads and 200 KB of shared memory.
 template <int N, int OP, int NC>
 constexpr bool tunable() {
-  return N >= 64 && ((OP == OP_FWD && (NC == 3 || NC == 4)) || (OP == OP_INV && NC == 3) || OP == OP_STOKES ||
-                     OP == OP_SOLUTE);
+  return N >= 64 && ((OP == OP_FWD && NC == 3) || (OP == OP_INV && NC == 3) || OP == OP_STOKES || OP == OP_SOLUTE ||
+                     OP == OP_FWD_SOL || OP == OP_INV_SOL);
 }
 
 template <typename T, int N, int OP, int NC, int TX>
@@ -197,7 +197,9 @@ static int l_pass_tx(int op, int nc, int shift) {
   ACM_TX(OP_INV, 3)
   ACM_TX(OP_INV_SCALE, 1)
   ACM_TX(OP_STOKES, 3)
-  ACM_TX(OP_SOLUTE, 4)
+  ACM_TX(OP_SOLUTE, 2)
+  ACM_TX(OP_FWD_SOL, 3)
+  ACM_TX(OP_INV_SOL, 3)
   ACM_TX(OP_DERIV, 1)
 #undef ACM_TX
   return 0;
@@ -217,7 +219,9 @@ static cudaError_t l_pass(const Geo& g, int axis, int op, int nc, int nprob, voi
   ACM_PASS(OP_INV, 3)
   ACM_PASS(OP_INV_SCALE, 1)
   ACM_PASS(OP_STOKES, 3)
-  ACM_PASS(OP_SOLUTE, 4)
+  ACM_PASS(OP_SOLUTE, 2)
+  ACM_PASS(OP_FWD_SOL, 3)
+  ACM_PASS(OP_INV_SOL, 3)
   ACM_PASS(OP_DERIV, 1)
 #undef ACM_PASS
   return cudaErrorInvalidValue;
@@ -257,7 +261,7 @@ bool Ops<T>::tx_variant(int n, int op, int nc, int shift) {
 
 template <typename T>
 int Ops<T>::z_blocks(const Geo& g, int op) {
-  const int nc = op == P_SOLUTE ? 4 : 3;
+  const int nc = op == P_SOLUTE ? 2 : 3;
   const int tx = pass_tx(g, 0, op, nc);
   return ((g.Pu + tx - 1) / tx) * g.n1;
 }
@@ -276,8 +280,14 @@ cudaError_t Ops<T>::x_stokes_rhs(const Geo& g, int nprob, void* spec, const void
 
 template <typename T>
 cudaError_t Ops<T>::x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                             const SoluteDev* prm, const void* tw, cudaStream_t s) {
-  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, prm, tw, s)
+                             const SoluteDev* prm, const void* tw, const Sym<T>& sym, cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, prm, tw, sym.d2, s)
+}
+
+template <typename T>
+cudaError_t Ops<T>::mul_id2(const Geo& g, int nprob, void* spec, long long ps, const Sym<T>& sym, cudaStream_t s) {
+  k_mul_id2<T><<<dim3(304, nprob), 256, 0, s>>>((cx<T>*)spec + 2 * g.S, ps, g, sym.d2);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -298,6 +308,7 @@ cudaError_t Ops<T>::pass(const Geo& g, int axis, int op, int nc, int nprob, void
                          double* part, cudaStream_t s, int dm) {
   const int n = axis == 1 ? g.n1 : g.n0;
   if ((op == P_STOKES || op == P_SOLUTE || op == P_DERIV) && axis != 0) return cudaErrorInvalidValue;
+  if ((op == P_FWD_SOL || op == P_INV_SOL) && axis != 1) return cudaErrorInvalidValue;
   ACM_DISPATCH_N(n, l_pass, g, axis, op, nc, nprob, spec, ps, sym, tw, st0, st1, sprm, cprm, part, s, dm)
 }
 

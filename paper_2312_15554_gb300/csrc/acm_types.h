@@ -53,7 +53,7 @@ struct Geo {
   int lph;      // problems per indicator: problem p uses H + (p / lph) * hs
   // tile-width choice of the strided passes per [precision (FP64 = 1)][axis][pass op]:
   // -1 half, 0 default, +1 double the default width (set by the autotuner)
-  signed char txs[2][2][6] = {};
+  signed char txs[2][2][8] = {};
 };
 
 // Symbols of one precision: d and L per axis (axis 2 only up to n2/2).
