@@ -394,6 +394,122 @@ def run_batched(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_grf512(args, rank, world, dist):
+    """512^3 thresholded Gaussian random field (correlation length 16 voxels, porosity
+    0.3): Stokes for the load e_x, then advection-diffusion at Pe 10 (3 loads).
+
+    value: voxel-iterations/s of the FP32 path (20 Stokes + 3 x 20 solute iterations
+    per step, FP64 residuals). Accuracy: the same problems solved to eps with FP32
+    iterations and a final FP64 refinement (ACM_FP32_THEN_FP64), against FP64
+    iterations throughout; the differences of K_xx, of u and of D are reported.
+    """
+    import torch
+
+    from paper_2312_15554_gb300 import acm
+    from paper_2312_15554_gb300 import build as B
+    from paper_2312_15554_gb300 import inputs as I
+    n = 512
+    H = I.grf_medium((n, n, n), 16.0, 0.3, 2024 + rank)
+    B.build()
+    acm.load()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    V = H.size
+    porosity = 1.0 - float(H.mean())
+    ctx = acm.acm_ctx(H.shape, stream.cuda_stream)
+    Hd = torch.as_tensor(H, device=dev)
+    tiles = acm.acm_autotune(ctx, False)
+    acm.acm_autotune(ctx, True)
+    iters = args.iters
+    u = torch.zeros((3,) + H.shape, dtype=torch.float32, device=dev)
+    sp = acm.stokes_params(eps=0.0, max_iter=iters, precision=acm.FP32)
+    cp = acm.advdiff_params(eps=0.0, max_iter=iters, precision=acm.FP32)
+
+    def step():
+        acm.acm_stokes(ctx, Hd, [1.0, 0.0, 0.0], sp, u=u)
+        acm.acm_advdiff_tensor(ctx, Hd, u, 10.0, cp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    acm.acm_profile_read(ctx)
+    acm.acm_profile_enable(ctx, True)
+    sampler = ClockSampler(local) if rank == 0 else None
+    SH.barrier(dist)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    prof = acm.acm_profile_read(ctx)
+    acm.acm_profile_enable(ctx, False)
+    ms = SH.max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    vi_step = V * iters * 4
+    value = vi_step * args.steps * world / (ms / 1e3)
+    kinds = {k: v for k, v in prof.items() if k not in ("other", "finalize") and v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    per_problem = {"x_stokes_local": 3, "x_stokes_rhs": 3, "y_fwd_stokes": 3, "z_stokes": 3, "y_inv_stokes": 3}
+    nprob_of = lambda k: 1 if k in per_problem else 3
+    kern = {k: {"ms": round(v[0], 3), "launches": v[1],
+                "GBps": (round(algorithmic_bytes_per_voxel(k, n, porosity) * V * nprob_of(k) * v[1] / (v[0] / 1e3) / 1e9,
+                               1) if v[1] and algorithmic_bytes_per_voxel(k, n, porosity) else None)}
+            for k, v in prof.items() if v[1]}
+    peak, peak_src = measured_peaks()
+    achieved = kern[dom]["GBps"]
+    # accuracy: FP32 iterations + FP64 refinement against FP64 throughout
+    eps, eps32, nu = args.c5_eps, args.c5_eps32, args.c5_nu
+    uA = torch.zeros((3,) + H.shape, dtype=torch.float64, device=dev)
+    uB = torch.zeros_like(uA)
+    pA = acm.stokes_params(nu=nu, eps=eps, eps32=eps32, max_iter=args.c5_max_iter, precision=acm.FP32_THEN_FP64)
+    pB = acm.stokes_params(nu=nu, eps=eps, max_iter=args.c5_max_iter, precision=acm.FP64)
+    sA, KA, rA = acm.acm_stokes(ctx, Hd, [1.0, 0.0, 0.0], pA, u=uA)
+    sB, KB, rB = acm.acm_stokes(ctx, Hd, [1.0, 0.0, 0.0], pB, u=uB)
+    du = float((uA - uB).norm() / uB.norm())
+    qA = acm.advdiff_params(eps=eps, max_iter=args.c5_max_iter, precision=acm.FP32_THEN_FP64)  # FP32 stage to 1e-5
+    qB = acm.advdiff_params(eps=eps, max_iter=args.c5_max_iter, precision=acm.FP64)
+    # the Peclet number is defined with the unit-cell velocity (nu = 1): u scales as 1/nu
+    tA, DA, DxA, dA = acm.acm_advdiff_tensor(ctx, Hd, uA * nu, 10.0, qA)
+    tB, DB, DxB, dB = acm.acm_advdiff_tensor(ctx, Hd, uB * nu, 10.0, qB)
+    ctx.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "512^3 Gaussian random field (correlation 16 vox) thresholded to porosity 0.3; "
+                               "Stokes load e_x + solute Pe 10 x 3 loads", "n": n, "porosity": round(porosity, 4),
+                   "iters_per_step": iters, "problems_per_step": 4, "tiles": tiles,
+                   "l2": "inputs larger than L2"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                     "peak_source": peak_src},
+        "clocks": clocks,
+        "kernels": kern,
+        "precision_check": {
+            "eps": eps, "eps32": eps32, "nu": nu,
+            "note": "nu = 1: unit cell; nu = 1/n^2: lengths in voxels (velocities O(1), so the absolute part "
+                    "of the tolerance does not end the iteration early)",
+            "stokes_fp32_then_fp64": {"status": sA, "iters": rA.iters, "iters_fp64": rA.iters_fp64,
+                                      "converged": rA.converged, "ms": rA.time_ms, "K_xx": float(KA[0] * nu)},
+            "stokes_fp64": {"status": sB, "iters": rB.iters, "converged": rB.converged, "ms": rB.time_ms,
+                            "K_xx": float(KB[0] * nu)},
+            "K_col_rel_diff": float(np.linalg.norm(KA - KB) / np.linalg.norm(KB)),
+            "u_rel_l2_diff": du,
+            "solute_fp32_then_fp64": {"iters": [r.iters for r in dA], "iters_fp64": [r.iters_fp64 for r in dA],
+                                      "converged": [r.converged for r in dA], "D": DA.tolist()},
+            "solute_fp64": {"iters": [r.iters for r in dB], "converged": [r.converged for r in dB], "D": DB.tolist()},
+            "D_rel_diff": float(np.linalg.norm(DA - DB) / np.linalg.norm(DB)),
+        },
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -405,8 +521,13 @@ def main():
     ap.add_argument("--ttk", action="store_true",
                     help="also measure time-to-permeability (K within 1e-4 of a long-run reference)")
     ap.add_argument("--ttk-long", type=int, default=20000, help="iterations of the reference run")
-    ap.add_argument("--config", default="cell256", choices=["cell256", "batched"],
-                    help="cell256: the 256^3 cell (default); batched: 384 cells (192 at 64^3, 192 at 128^3)")
+    ap.add_argument("--config", default="cell256", choices=["cell256", "batched", "grf512"],
+                    help="cell256: the 256^3 cell (default); batched: 384 cells (192 at 64^3, 192 at 128^3); "
+                         "grf512: the 512^3 Gaussian random field with the FP32/FP64 comparison")
+    ap.add_argument("--c5-eps", type=float, default=1e-6, help="grf512: tolerance of the accuracy runs")
+    ap.add_argument("--c5-eps32", type=float, default=1e-5, help="grf512: FP32 stage tolerance")
+    ap.add_argument("--c5-max-iter", type=int, default=20000)
+    ap.add_argument("--c5-nu", type=float, default=1.0, help="grf512: viscosity of the accuracy runs")
     ap.add_argument("--cells", type=int, default=384, help="cells of the batched configuration")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -423,6 +544,8 @@ def main():
         dist = tdist
     if args.config == "batched":
         run_batched(args, rank, world, dist)
+    elif args.config == "grf512":
+        run_grf512(args, rank, world, dist)
     else:
         run_gpu(args, rank, world, dist)
     if dist is not None:

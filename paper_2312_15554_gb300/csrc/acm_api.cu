@@ -657,7 +657,9 @@ acm_status stokes_outputs(acm_ctx* c, int nprob, void* u_out, long long u_stride
   return ACM_OK;
 }
 
-acm_status stokes_reports(acm_ctx* c, int nprob, acm_report* rep, int fp64_from, double t0) {
+// fp64_from: -1 all FP32, -2 all FP64, >= 0 mixed with it32[p] FP32 iterations of problem p
+acm_status stokes_reports(acm_ctx* c, int nprob, acm_report* rep, int fp64_from, double t0,
+                          const std::vector<int>* it32 = nullptr) {
   std::vector<StokesDev> hp(nprob);
   CK(cudaMemcpyAsync(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -669,7 +671,7 @@ acm_status stokes_reports(acm_ctx* c, int nprob, acm_report* rep, int fp64_from,
       acm_report& r = rep[p];
       std::memset(&r, 0, sizeof(r));
       r.iters = d.iter;
-      r.iters_fp64 = fp64_from >= 0 ? d.iter - fp64_from : (fp64_from == -2 ? d.iter : 0);
+      r.iters_fp64 = fp64_from >= 0 ? d.iter - (it32 ? (*it32)[p] : fp64_from) : (fp64_from == -2 ? d.iter : 0);
       r.converged = d.converged;
       r.status = d.status;
       for (int k = 0; k < 6; ++k) {
@@ -731,14 +733,21 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
     CKS(stokes_iterate<float>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     std::vector<StokesDev> hp(nprob);
     CK(cudaMemcpy(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost));
-    int it32 = hp[0].iter;
+    // FP32 iterations of each problem; the host loop may run until the problem
+    // with the fewest reaches the cap (the device stops each one at its own)
+    std::vector<int> it32(nprob);
+    int it32_min = P.max_iter;
     bool ok = true;
-    for (auto& x : hp) ok = ok && x.status == ACM_OK;
+    for (int p = 0; p < nprob; ++p) {
+      it32[p] = hp[p].iter;
+      it32_min = std::min(it32_min, it32[p]);
+      ok = ok && hp[p].status == ACM_OK;
+    }
     if (ok && P.eps < e32) {
       CKS(stokes_promote(c, nprob, P.eps));
-      CKS(stokes_iterate<double>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter - it32, dl));
+      CKS(stokes_iterate<double>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter - it32_min, dl));
       CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
-      st = stokes_reports(c, nprob, rep, it32, t0);
+      st = stokes_reports(c, nprob, rep, 0, t0, &it32);
     } else {
       // nothing left for FP64: report the FP32 result converted to the caller's double buffers
       CKS(stokes_promote(c, nprob, P.eps));
@@ -910,7 +919,9 @@ acm_status solute_promote(acm_ctx* c, int nprob, double eps) {
   return ACM_OK;
 }
 
-acm_status solute_reports(acm_ctx* c, int nprob, acm_report* rep, int it32, bool fp64_all, double t0) {
+// it32: FP32 iterations of each problem of a mixed solve (nullptr: no FP64 stage)
+acm_status solute_reports(acm_ctx* c, int nprob, acm_report* rep, const std::vector<int>* it32, bool fp64_all,
+                          double t0) {
   std::vector<SoluteDev> hp(nprob);
   CK(cudaMemcpyAsync(hp.data(), c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -922,7 +933,7 @@ acm_status solute_reports(acm_ctx* c, int nprob, acm_report* rep, int it32, bool
       acm_report& r = rep[p];
       std::memset(&r, 0, sizeof(r));
       r.iters = d.iter;
-      r.iters_fp64 = fp64_all ? d.iter : (it32 >= 0 ? d.iter - it32 : 0);
+      r.iters_fp64 = fp64_all ? d.iter : (it32 ? d.iter - (*it32)[p] : 0);
       r.converged = d.converged;
       r.status = d.status;
       r.res[0] = d.res[0];
@@ -998,11 +1009,11 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
   if (P.precision == ACM_FP32) {
     CKS(solute_run<float>(c, nprob, Hdev, ud, 0, gchi, Pe, P, P.eps, true, B0, ubar));
     CKS(solute_outputs<float>(c, nprob, Hdev, ud, 0, chi_out, grad_out, Dg, Dx));
-    st = solute_reports(c, nprob, rep, -1, false, t0);
+    st = solute_reports(c, nprob, rep, nullptr, false, t0);
   } else if (P.precision == ACM_FP64) {
     CKS(solute_run<double>(c, nprob, Hdev, ud, 0, gchi, Pe, P, P.eps, true, B0, ubar));
     CKS(solute_outputs<double>(c, nprob, Hdev, ud, 0, chi_out, grad_out, Dg, Dx));
-    st = solute_reports(c, nprob, rep, -1, true, t0);
+    st = solute_reports(c, nprob, rep, nullptr, true, t0);
   } else {
     // FP32 phase needs the velocity in FP32
     CKS(ensure_prec<float>(c));
@@ -1011,14 +1022,20 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
     CKS(solute_run<float>(c, nprob, Hdev, c->pf.u, 0, gchi, Pe, P, e32, true, B0, ubar));
     std::vector<SoluteDev> hp(nprob);
     CK(cudaMemcpy(hp.data(), c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost));
-    const int it32 = hp[0].iter;
+    std::vector<int> it32(nprob);
+    int it32_min = P.max_iter;
     bool ok = true;
-    for (auto& x : hp) ok = ok && x.status == ACM_OK;
+    for (int p = 0; p < nprob; ++p) {
+      it32[p] = hp[p].iter;
+      it32_min = std::min(it32_min, it32[p]);
+      ok = ok && hp[p].status == ACM_OK;
+    }
     CKS(solute_promote(c, nprob, P.eps));
-    if (ok && P.eps < e32) CKS(solute_run<double>(c, nprob, Hdev, ud, 0, gchi, Pe, P, P.eps, false, B0, ubar, it32));
+    const bool refine = ok && P.eps < e32;
+    if (refine) CKS(solute_run<double>(c, nprob, Hdev, ud, 0, gchi, Pe, P, P.eps, false, B0, ubar, it32_min));
     else CK(cudaMemcpy(c->cprm, hp.data(), nprob * sizeof(SoluteDev), cudaMemcpyHostToDevice));
     CKS(solute_outputs<double>(c, nprob, Hdev, ud, 0, chi_out, grad_out, Dg, Dx));
-    st = solute_reports(c, nprob, rep, it32, false, t0);
+    st = solute_reports(c, nprob, rep, refine ? &it32 : nullptr, false, t0);
   }
   return st;
 }

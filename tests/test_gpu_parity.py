@@ -322,3 +322,21 @@ def test_history_records_the_oracle_residuals_and_mean_velocity(lib):
     np.testing.assert_allclose(hist[:, 12:15], R.penalties, rtol=1e-12)
     np.testing.assert_allclose(hist[:, 15:18], R.mean_u_hist, rtol=1e-9, atol=1e-14)
     np.testing.assert_allclose(hist[-1, 15:18], K, rtol=1e-9, atol=1e-14)
+
+
+def test_mixed_precision_reports_split_iterations_per_load(lib):
+    """FP32 then FP64: every load reports its own FP64 share (loads stop their
+    FP32 stage at different iterations)."""
+    H = I.sphere_pack((32, 32, 32), 0.45, 4.0, 12)[0]
+    ctx = lib.acm_ctx(H.shape)
+    Hd = dev(H, torch.uint8)
+    u3 = torch.zeros((3, 3) + H.shape, dtype=torch.float64, device=DEV)
+    s, K, Kg, reps = lib.acm_stokes_tensor(ctx, Hd, lib.stokes_params(
+        precision=lib.FP32_THEN_FP64, eps=1e-7, eps32=1e-5, max_iter=20000, deriv=O.CENTRAL), u3)
+    for r in reps:
+        assert r.converged and 0 < r.iters_fp64 < r.iters
+    s, D, Dx, dreps = lib.acm_advdiff_tensor(ctx, Hd, u3[0], 10.0, lib.advdiff_params(
+        precision=lib.FP32_THEN_FP64, eps=1e-8, max_iter=20000))
+    for r in dreps:
+        assert r.converged and 0 < r.iters_fp64 < r.iters
+    ctx.close()
