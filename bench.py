@@ -165,26 +165,19 @@ def run_reference(args, rank, world):
 # GPU arm
 # ---------------------------------------------------------------------------
 def time_to_permeability(acm, ctx, Hd, stream, n_long):
-    """Seconds until the permeability tensor is within 1e-4 (Frobenius, relative) of
-    the tensor after n_long iterations, for the plain solve with default parameters.
+    """Seconds until the permeability tensor stays within a relative error
+    (Frobenius) of the tensor after n_long iterations, for the plain solve with
+    default parameters, at 1e-1 ... 1e-4.
 
     The k = 0 Fourier coefficient of each Green solve gives the volume average of
     u for every iteration (history), so the crossing iteration n* is found from one
-    long run; then exactly n* iterations are timed with CUDA events.
+    long run; the seconds are n* times the per-iteration time of that run (CUDA
+    events). A threshold below the change of the reference over its last tenth
+    cannot be resolved by the reference and is reported as not reached.
     """
     import torch
     u3 = torch.zeros((3, 3) + tuple(Hd.shape), dtype=torch.float32, device=Hd.device)
     prm = acm.stokes_params(eps=0.0, max_iter=n_long, precision=acm.FP32, check_every=500)
-    acm.acm_stokes_tensor(ctx, Hd, prm, u3)
-    hs = [acm.acm_history(ctx, j) for j in range(3)]
-    m = min(len(h) for h in hs)
-    Kn = np.stack([np.stack([hs[j][:m, 15 + i] for j in range(3)], axis=-1) for i in range(3)], axis=1)
-    Kref = Kn[-1]
-    err = np.linalg.norm(Kn - Kref, axis=(1, 2)) / np.linalg.norm(Kref)
-    bad = np.nonzero(err > 1e-4)[0]
-    n_star = int(bad[-1]) + 2 if len(bad) else 1
-    tail = float(np.linalg.norm(Kn[-1] - Kn[max(0, m - 1 - m // 10)]) / np.linalg.norm(Kref))
-    prm = acm.stokes_params(eps=0.0, max_iter=n_star, precision=acm.FP32, check_every=500)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -192,9 +185,24 @@ def time_to_permeability(acm, ctx, Hd, stream, n_long):
     acm.acm_stokes_tensor(ctx, Hd, prm, u3)
     e1.record(stream)
     torch.cuda.synchronize()
-    return {"seconds": e0.elapsed_time(e1) / 1e3, "iterations": n_star, "rel_err_target": 1e-4,
-            "reference_iterations": n_long, "reference_last10pct_change": tail,
-            "K_ref": Kref.tolist(), "form": "plain (FP32, adaptive penalties of Eq. 22, library defaults)"}
+    per_iter = e0.elapsed_time(e1) / 1e3 / n_long
+    hs = [acm.acm_history(ctx, j) for j in range(3)]
+    m = min(len(h) for h in hs)
+    Kn = np.stack([np.stack([hs[j][:m, 15 + i] for j in range(3)], axis=-1) for i in range(3)], axis=1)
+    Kref = Kn[-1]
+    err = np.linalg.norm(Kn - Kref, axis=(1, 2)) / np.linalg.norm(Kref)
+    tail = float(np.linalg.norm(Kn[-1] - Kn[max(0, m - 1 - m // 10)]) / np.linalg.norm(Kref))
+    out = {}
+    for rel in (1e-1, 1e-2, 1e-3, 1e-4):
+        bad = np.nonzero(err > rel)[0]
+        n_star = int(bad[-1]) + 2 if len(bad) else 1
+        if rel <= tail or n_star > m:
+            out[f"{rel:g}"] = {"reached": False}
+        else:
+            out[f"{rel:g}"] = {"reached": True, "iterations": n_star, "seconds": n_star * per_iter}
+    return {"thresholds": out, "reference_iterations": n_long, "reference_last10pct_change": tail,
+            "seconds_per_iteration": per_iter, "K_ref": Kref.tolist(),
+            "form": "plain (FP32, adaptive penalties of Eq. 22, library defaults, unit cell, nu = 1)"}
 
 
 def run_gpu(args, rank, world, dist):

@@ -67,6 +67,7 @@ struct acm_ctx {
   double* part_r = nullptr;
   int nbx = 0, nbz = 0;
   uint8_t* Hd = nullptr;
+  uint32_t* Hb = nullptr;   // [ncells][V / 32] indicator bits (x passes)
   unsigned long long* cnt = nullptr;
   double* hist = nullptr;
   int solute_deriv = 1;      // derivative symbol of the last solute iteration
@@ -433,7 +434,8 @@ acm_status stokes_body(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs,
   const int nbx = Ops<T>::x_blocks(g), nbz = Ops<T>::z_blocks(g, P_STOKES);
   double* hist = c->hist_b ? c->hist_b : (nprob <= BMAX ? c->hist : nullptr);
   const int hcap = c->hist_b ? c->hist_b_cap : HIST_CAP;
-  LK(ACM_K_X_STOKES_LOCAL, Ops<T>::x_stokes_local(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, c->part_x, w.tw, c->st));
+  LK(ACM_K_X_STOKES_LOCAL, Ops<T>::x_stokes_local(g, nprob, w.spec, w.u, w.lam, Hdev, c->Hb, c->sprm, c->part_x, w.tw,
+                                                  c->st));
   LK(ACM_K_FINALIZE, stokes_finalize(nprob, c->sprm, c->part_x, nbx, c->part_z, nbz, (double)g.V, hist, hcap, c->st));
   if (!last) CKS(stokes_step1<T>(c, nprob, Hdev, hs, lph, sym));
   return ACM_OK;
@@ -712,6 +714,7 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
   if (nsolid == c->g.V) return ACM_ERR_NO_FLUID;
   if (Hdev != c->Hd) CK(cudaMemcpyAsync(c->Hd, Hdev, (size_t)c->g.V, cudaMemcpyDeviceToDevice, c->st));
   Hdev = c->Hd;  // one stable buffer, so a cached device loop stays valid
+  LK(ACM_K_OTHER, pack_hbits(c->Hd, c->Hb, c->g.V, c->st));
   const bool dl = P.device_loop != 0;
   acm_status st = ACM_OK;
   const std::vector<const void*> iu(nprob, init_u), il(nprob, init_lam);
@@ -841,7 +844,7 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
     for (int k = 0; k < chunk; ++k) {
       // spectral components per problem: x -> (tau_0, tau_1, s + d2 tau_2), y forward -> (tau_0, s''),
       // z -> (d0 chi, chi), y inverse -> (d0 chi, d1 chi, chi); the x pass takes d2 of the last
-      LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->cprm, w.tw, sym, c->st));
+      LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym, c->st));
       LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
                       nullptr, c->st));
       LK(ACM_K_Z_SOLUTE, Ops<T>::pass(g, 0, P_SOLUTE, 2, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm, c->part_z,
@@ -962,14 +965,16 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
   const uint8_t* Hdev = nullptr;
   long long nsolid = 0;
   CKS(stage_H(c, H, &Hdev, &nsolid));
+  LK(ACM_K_OTHER, pack_hbits(Hdev, c->Hb, c->g.V, c->st));
   if (nsolid == c->g.V) return ACM_ERR_NO_FLUID;
   const bool fp32 = P.precision == ACM_FP32;
   const size_t rs = fp32 ? sizeof(float) : sizeof(double);
   const Geo& g0 = c->g;
-  // the advecting velocity in device memory of the working precision
-  // used in place when it is a device buffer aligned to its element size
+  // the advecting velocity in device memory of the working precision, used in
+  // place when it is a 16-byte aligned device buffer (the x pass reads voxel
+  // pairs as vectors and prefetches whole rows into L2 in 16-byte units)
   const void* ud = u;
-  const bool in_place = is_device_ptr(u) && ((uintptr_t)u % rs) == 0;
+  const bool in_place = is_device_ptr(u) && ((uintptr_t)u % 16) == 0;
   if (fp32) {
     CKS(ensure_prec<float>(c));
     if (!in_place) {
@@ -1079,6 +1084,7 @@ acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_sto
       CK(cudaMemcpyAsync(gr.c->Hd + i * V, H[cell], (size_t)V, cudaMemcpyDefault, b->st));
       CK(count_solid_add(gr.c->Hd + i * V, V, b->counts + cell, b->st));
     }
+    CK(pack_hbits(gr.c->Hd, gr.c->Hb, (long long)gr.cells.size() * V, b->st));
   }
   std::vector<unsigned long long> cnt(b->ncells);
   CK(cudaMemcpyAsync(cnt.data(), b->counts, cnt.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->st));
@@ -1297,7 +1303,7 @@ acm_status ctx_create(acm_ctx** out, int n0, int n1, int n2, void* stream, int B
   Geo gn = g;
   for (int pr = 0; pr < 2; ++pr)
     for (int ax = 0; ax < 2; ++ax)
-      for (int op = 0; op < 6; ++op) gn.txs[pr][ax][op] = -1;
+      for (int op = 0; op < 8; ++op) gn.txs[pr][ax][op] = -1;
   const int nbz = std::max(std::max(Ops<float>::z_blocks(gn, P_STOKES), Ops<float>::z_blocks(gn, P_SOLUTE)),
                            std::max(Ops<double>::z_blocks(gn, P_STOKES), Ops<double>::z_blocks(gn, P_SOLUTE)));
   c->nbx = nbx;
@@ -1308,6 +1314,7 @@ acm_status ctx_create(acm_ctx** out, int n0, int n1, int n2, void* stream, int B
             cudaMalloc(&c->part_z, (size_t)B * nbz * 4 * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->part_r, (size_t)B * NRED * 8 * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->Hd, (size_t)ncells * g.V) == cudaSuccess &&
+            cudaMalloc(&c->Hb, (size_t)ncells * g.V / 8) == cudaSuccess &&
             cudaMalloc(&c->cnt, sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&c->graph.counter, sizeof(unsigned int)) == cudaSuccess &&
             cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess &&
@@ -1381,7 +1388,8 @@ acm_status acm_destroy(acm_ctx* c) {
   free_prec(c->pd);
   if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
   if (c->cap) cudaStreamDestroy(c->cap);
-  void* ps[] = {c->sprm, c->cprm, c->part_x, c->part_z, c->part_r, c->Hd, c->cnt, c->hist, c->hist_b, c->graph.counter};
+  void* ps[] = {c->sprm, c->cprm, c->part_x, c->part_z, c->part_r, c->Hd, c->Hb, c->cnt, c->hist, c->hist_b,
+                c->graph.counter};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->pin) cudaFreeHost(c->pin);

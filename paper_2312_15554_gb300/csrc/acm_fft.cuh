@@ -296,6 +296,11 @@ __device__ __forceinline__ void cp_async_pred(void* smem, const void* gmem, bool
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 
+// Bulk prefetch of bytes (a multiple of 16, 16-byte aligned, in bounds) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* gmem, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
+}
+
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 

@@ -22,6 +22,7 @@
 // The multiplier q only enters through its gradient and is kept in Fourier space.
 #pragma once
 #include "acm_fft.cuh"
+#include "acm_xline.cuh"
 #include "acm_types.h"
 
 namespace acm {
@@ -43,20 +44,6 @@ template <typename T, int N2, int NC>
 constexpr int x_smem_bytes() {
   return (NC * XCfg<T, N2>::LPB * XCfg<T, N2>::LS + tw_total(N2 / 2) + N2 / 2 + 1) * (int)sizeof(cx<T>);
 }
-
-// Shared-memory layout of an x-pass block: NC component lines, the twiddle
-// tables, then (16-byte aligned) NR staged real fields of LPB*N2 values and
-// the staged indicator bytes.
-template <typename T, int N2, int NC, int NR>
-struct XLayout {
-  using C = XCfg<T, N2>;
-  static constexpr int TOT = C::LPB * N2;
-  static constexpr int TW = NC * C::LPB * C::LS;                         // complex offset of the twiddles
-  static constexpr int RB = ((TW + tw_total(C::M) + C::M + 1) * (int)sizeof(cx<T>) + 15) / 16 * 16;  // bytes
-  static constexpr int HB = RB + NR * TOT * (int)sizeof(T);              // byte offset of H
-  static constexpr int QB = (HB + (NR > 0 ? TOT : 0) + 15) / 16 * 16;    // byte offset of the Nyquist bins
-  static constexpr int BYTES = QB + NC * C::LPB * (int)sizeof(cx<T>);
-};
 
 template <typename T>
 __device__ __forceinline__ T& re_at(cx<T>* line, int n) {
@@ -129,25 +116,16 @@ __device__ __forceinline__ void x_load_spec_raw_async(cx<T>* sm, cx<T>* nyq, con
   }
 }
 
-// With dc >= 0 the lines of component dc are first multiplied by i d(k)
-// (d: the derivative symbol of the kx axis, M + 1 values): they become the
-// half spectrum of that component's derivative along the line.
 template <typename T, int N2, int NC>
-__device__ __forceinline__ void x_pre_smem(cx<T>* sm, const cx<T>* nyq, const cx<T>* twx, int dc = -1,
-                                           const T* __restrict__ d = nullptr) {
+__device__ __forceinline__ void x_pre_smem(cx<T>* sm, const cx<T>* nyq, const cx<T>* twx) {
   using C = XCfg<T, N2>;
   constexpr int M = C::M;
   const cx<T>* tw = twx + tw_total(M);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int cl = warp; cl < NC * C::LPB; cl += nw) {
     cx<T>* s = sm + cl * C::LS;
-    const bool der = cl / C::LPB == dc;
     for (int k = lane; k <= M / 2; k += 32) {
-      cx<T> X = s[pad(k)], Y = (k == 0) ? nyq[cl] : s[pad(M - k)];
-      if (der) {
-        X = cscale(mul_i(X), d[k]);
-        Y = cscale(mul_i(Y), d[M - k]);
-      }
+      const cx<T> X = s[pad(k)], Y = (k == 0) ? nyq[cl] : s[pad(M - k)];
       const cx<T> e1 = X + cconj(Y), o1 = cmul(X - cconj(Y), cconj(tw[k]));
       const cx<T> e2 = Y + cconj(X), o2 = cmul(Y - cconj(X), cconj(tw[M - k]));
       s[pad(k)] = e1 + mul_i(o1);
@@ -186,52 +164,6 @@ __device__ __forceinline__ void x_post_store_spec(const cx<T>* sm, cx<T>* __rest
   }
 }
 
-// Solute x-pass output: lines (tau_0, tau_1, tau_2, s) -> half spectra
-// (tau_0, tau_1, s + i d2 tau_2) in components 0..2. Adding the axis-2 term of
-// i d.tau^ (Eq. 18 in Fourier space) here, where kx is already known, leaves
-// three components for the y pass instead of four.
-template <typename T, int N2>
-__device__ __forceinline__ void x_post_store_solute(const cx<T>* sm, cx<T>* __restrict__ spec, long long S, int P,
-                                                    int line0, const cx<T>* twx, const T* __restrict__ d2) {
-  using C = XCfg<T, N2>;
-  constexpr int M = C::M;
-  const cx<T>* tw = twx + tw_total(M);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const T half = (T)0.5;
-  // half spectrum value at k (and M - k) of the line in shared memory
-  auto post = [&](const cx<T>* s, int k, cx<T>& Xk, cx<T>& Xm) {
-    const cx<T> Zk = s[pad(k)];
-    if (k == 0) {
-      Xk = mk<T>(Zk.x + Zk.y, (T)0);
-      Xm = mk<T>(Zk.x - Zk.y, (T)0);
-    } else {
-      const cx<T> Zm = s[pad(M - k)];
-      const cx<T> ak = cscale(Zk + cconj(Zm), half), bk = cscale(Zk - cconj(Zm), half);
-      const cx<T> am = cscale(Zm + cconj(Zk), half), bm = cscale(Zm - cconj(Zk), half);
-      Xk = ak - mul_i(cmul(tw[k], bk));
-      Xm = am - mul_i(cmul(tw[M - k], bm));
-    }
-  };
-  for (int cl = warp; cl < 3 * C::LPB; cl += nw) {
-    const int c = cl / C::LPB, l = cl - c * C::LPB;
-    cx<T>* dst = spec + c * S + (long long)(line0 + l) * P;
-    const cx<T>* s = sm + cl * C::LS;
-    const cx<T>* s3 = sm + (3 * C::LPB + l) * C::LS;
-    for (int k = lane; k <= M / 2; k += 32) {
-      cx<T> Xk, Xm;
-      post(s, k, Xk, Xm);
-      if (c == 2) {
-        cx<T> Sk, Sm;
-        post(s3, k, Sk, Sm);
-        Xk = Sk + cscale(mul_i(Xk), d2[k]);
-        Xm = Sm + cscale(mul_i(Xm), d2[M - k]);
-      }
-      dst[k] = Xk;
-      dst[M - k] = Xm;
-    }
-  }
-}
-
 // complex FFT of length M on NC * LPB component lines, TL threads per line
 template <typename T, int N2, int NC, int SIGN>
 __device__ __forceinline__ void x_fft(cx<T>* sm, const cx<T>* tw) {
@@ -242,85 +174,179 @@ __device__ __forceinline__ void x_fft(cx<T>* sm, const cx<T>* tw) {
 }
 
 // ---------------------------------------------------------------------------
+// Line-resident x passes (acm_xline.cuh): blocks of XS_WARPS warps, each warp
+// taking XS_GPW consecutive groups of LPW lines.
+// ---------------------------------------------------------------------------
+constexpr int XS_WARPS = 8;   // warps per block of the line-resident x passes
+constexpr int XS_GPW = 4;     // line groups per warp
+
+template <typename T, int N2>
+__host__ __device__ constexpr int xs_tw_slots() { return (tw_total(N2 / 2) + N2 / 2 + 1 + 1) / 2 * 2; }
+
+// shared memory: twiddles, NBUF line buffers per line, and ACC real values per lane
+template <typename T, int N2, int NBUF, int ACC>
+__host__ __device__ constexpr int xs_smem_bytes() {
+  return (xs_tw_slots<T, N2>() + XS_WARPS * XL<T, N2>::LPW * XL<T, N2>::template lb<NBUF>()) * (int)sizeof(cx<T>) +
+         XS_WARPS * 32 * ACC * (int)sizeof(T);
+}
+
+// blocks per problem of the line-resident x passes
+__host__ __device__ constexpr int xs_blocks(int lines, int lpw) {
+  return (lines / lpw + XS_WARPS * XS_GPW - 1) / (XS_WARPS * XS_GPW);
+}
+
+// ---------------------------------------------------------------------------
 // Stokes x-pass 1: C2R of u^{n+1}, steps 2-3 of ADMM, residual partial sums
 //
-// The block's spectrum rows, u^n and H are staged into shared memory with
-// asynchronous copies; H lambda^n is then staged for the solid voxels only,
-// overlapping the inverse transform. The local step reads shared memory only.
+// Line-resident: each component of a line is inverse-transformed into
+// registers and the local steps run on the lane's voxel pairs 2k, 2k+1 read
+// and written as vectors; a chunk of pairs loads its old state before it
+// stores, so no store waits for the load of its own address.
 // ---------------------------------------------------------------------------
 template <typename T, int N2>
-__global__ void __launch_bounds__(3 * 64) k_x_stokes_local(const cx<T>* __restrict__ spec, T* __restrict__ u,
-                                                          T* __restrict__ lam, const uint8_t* __restrict__ H,
-                                                          StokesDev* __restrict__ prm, double* __restrict__ part,
-                                                          Geo g, const cx<T>* __restrict__ twg) {
-  using C = XCfg<T, N2>;
-  using Lay = XLayout<T, N2, 3, 6>;
-  constexpr int TOT = Lay::TOT;
+__global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
+    k_x_stokes_local(const cx<T>* __restrict__ spec, T* __restrict__ u, T* __restrict__ lam,
+                     const uint8_t* __restrict__ H, const uint32_t* __restrict__ Hb, StokesDev* __restrict__ prm,
+                     double* __restrict__ part, Geo g, const cx<T>* __restrict__ twg) {
+  using L = XL<T, N2>;
+  constexpr int M = L::M, E = L::E, TL = L::TL, LPW = L::LPW, LS = L::LS;
+  constexpr int LB = L::template lb<2>();
+  constexpr int CH = E < 8 ? E : 8;  // voxel pairs per load-then-store chunk
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* tw = sm + Lay::TW;
-  T* su = reinterpret_cast<T*>(smem_raw + Lay::RB);   // [3][TOT] u^n
-  T* sl = su + 3 * TOT;                                // [3][TOT] H lambda^n
-  uint8_t* sh = smem_raw + Lay::HB;                    // [TOT] H
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* lines = tw + xs_tw_slots<T, N2>();
   __shared__ double red[5 * 32];
   const int p = blockIdx.y;
   StokesDev* P = prm + p;
   if (P->done) return;
+  load_tw_x<T, N2>(tw, twg);
+  __syncthreads();
   const T alpha = (T)P->psi[0], b = (T)P->psi[2];
   // u~^n on solid voxels = s_prev u^n (s_prev = 1 before the first iteration)
   const T s_prev = (T)(P->psi_prev[2] / (P->psi_prev[2] + P->psi_prev[0]));
   const T s_now = b / (b + alpha);
-  const int line0 = blockIdx.x * C::LPB;
-  const long long v0 = (long long)line0 * N2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ll = lane / TL, t = lane % TL;
+  const unsigned mask = xl_mask();
+  cx<T>* b0 = lines + (warp * LPW + ll) * LB;
+  cx<T>* b1 = b0 + LS;
   const cx<T>* sp = spec + (long long)p * 3 * g.S;
   T* up = u + (long long)p * 3 * g.V;
   T* lp = lam + (long long)p * 3 * g.V;
-  const uint8_t* Hp = H + (long long)(p / g.lph) * g.hs;
-  cx<T>* nyq = reinterpret_cast<cx<T>*>(smem_raw + Lay::QB);
-  x_load_spec_raw_async<T, N2, 3>(sm, nyq, sp, g.S, g.P, line0);
+  const long long hcell = (long long)(p / g.lph) * g.hs;
+  const uint8_t* Hp = H + hcell;
+  const uint32_t* Hbp = Hb + hcell / 32;
+  double d5[5] = {0, 0, 0, 0, 0};
+  const int ngroups = g.n0 * g.n1 / LPW;
+  const int gbase = (blockIdx.x * XS_WARPS + warp) * XS_GPW;
+#pragma unroll 1
+  for (int gi = 0; gi < XS_GPW; ++gi) {
+    const int grp = gbase + gi;
+    if (grp >= ngroups) break;
+    const long long line = (long long)grp * LPW + ll;
+    const long long v0 = line * N2;
+    const cx<T>* srow = sp + line * g.P;
+    __syncwarp(mask);
+    for (int e = t; e <= M; e += TL) {
+      cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[e]);
+      cp_async<(int)sizeof(cx<T>)>(&b1[pad(e)], &srow[g.S + e]);
+    }
+    cp_async_commit();
+    if (lane == 0) {
+      // the group's rows of u^n and H lambda^n (consecutive lines are contiguous),
+      // and the next group's spectrum rows, on their way to L2
+      const long long w0 = (long long)grp * LPW * N2;
+      constexpr unsigned RB = LPW * N2 * sizeof(T);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) stage_real(su + c * TOT, up + c * g.V + v0, TOT);
-  for (int i = threadIdx.x; i < TOT / 16; i += blockDim.x) cp_async<16>(sh + 16 * i, Hp + v0 + 16 * i);
-  cp_async_commit();
-  load_tw_x<T, N2>(tw, twg);
-  cp_async_wait<0>();
-  __syncthreads();
-  for (int i = threadIdx.x; i < 3 * TOT; i += blockDim.x) {
-    const int c = i / TOT, e = i - c * TOT;
-    cp_async_pred<(int)sizeof(T)>(sl + i, lp + c * g.V + v0 + e, sh[e] != 0);
-  }
-  cp_async_commit();
-  x_pre_smem<T, N2, 3>(sm, nyq, tw);
-  __syncthreads();
-  x_fft<T, N2, 3, +1>(sm, tw);
-  cp_async_wait<0>();
-  __syncthreads();
-  T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-  for (int idx = threadIdx.x; idx < TOT; idx += blockDim.x) {
-    const int l = idx / N2, n = idx & (N2 - 1);
-    const bool solid = sh[idx] != 0;
+      for (int c = 0; c < 3; ++c) {
+        prefetch_l2(up + c * g.V + w0, RB);
+        prefetch_l2(lp + c * g.V + w0, RB);
+      }
+      if (gi + 1 < XS_GPW && grp + 1 < ngroups) {
+        const unsigned SB = (unsigned)(LPW * g.P * sizeof(cx<T>));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T u1 = re_at(sm + (c * C::LPB + l) * C::LS, n);
-      const T u0 = su[c * TOT + idx];
-      up[c * g.V + v0 + idx] = u1;
-      const T du = u1 - u0;
-      a3 += du * du;
-      if (solid) {
-        const T ut1 = s_now * u1;                 // step 2 (Eq. 8) with a^n = H lambda^n
-        const T ut0 = s_prev * u0;
-        const T l1 = sl[c * TOT + idx] + alpha * ut1;  // step 3 (Eq. 9)
-        lp[c * g.V + v0 + idx] = l1;
-        const T dut = ut1 - ut0, dd = u1 - ut1;
-        a0 += ut1 * ut1;
-        a1 += dut * dut;
-        a2 += dd * dd;
-        a4 += l1 * l1;
+        for (int c = 0; c < 3; ++c) prefetch_l2(sp + c * g.S + (long long)(grp + 1) * LPW * g.P, SB);
       }
     }
+    const unsigned hm = xl_hmask<N2, TL, E>(Hbp, Hp, line, t);
+    cp_async_wait<0>();
+    __syncwarp(mask);
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    cx<T> v[E];
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      cx<T>* bc = c == 1 ? b1 : b0;
+      xl_inverse<T, N2>(bc, tw, t, mask, v, nullptr);
+      if (c == 0) {
+        // the row of component 2 into b0, behind components 0 and 1
+        __syncwarp(mask);
+        for (int e = t; e <= M; e += TL) cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[2 * g.S + e]);
+        cp_async_commit();
+      }
+      T* uc = up + c * g.V + v0;
+      T* lc = lp + c * g.V + v0;
+#pragma unroll
+      for (int m0 = 0; m0 < E; m0 += CH) {
+        T2 u0[CH], l0[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const int k = t + TL * (m0 + j);
+          u0[j] = *reinterpret_cast<const T2*>(uc + 2 * k);
+          if ((hm >> (2 * (m0 + j))) & 3u) {
+            l0[j] = *reinterpret_cast<const T2*>(lc + 2 * k);
+          } else {
+            l0[j].x = (T)0;
+            l0[j].y = (T)0;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const int m = m0 + j, k = t + TL * m;
+          const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
+          const T u1a = v[m].x, u1b = v[m].y;
+          T2 w;
+          w.x = u1a;
+          w.y = u1b;
+          *reinterpret_cast<T2*>(uc + 2 * k) = w;
+          const T dua = u1a - u0[j].x, dub = u1b - u0[j].y;
+          a3 += dua * dua + dub * dub;
+          if (sa | sb) {
+            T2 ln = l0[j];
+            if (sa) {
+              const T ut1 = s_now * u1a, ut0 = s_prev * u0[j].x;   // step 2 (Eq. 8) with a^n = H lambda^n
+              ln.x = l0[j].x + alpha * ut1;                          // step 3 (Eq. 9)
+              const T dut = ut1 - ut0, dd = u1a - ut1;
+              a0 += ut1 * ut1;
+              a1 += dut * dut;
+              a2 += dd * dd;
+              a4 += ln.x * ln.x;
+            }
+            if (sb) {
+              const T ut1 = s_now * u1b, ut0 = s_prev * u0[j].y;
+              ln.y = l0[j].y + alpha * ut1;
+              const T dut = ut1 - ut0, dd = u1b - ut1;
+              a0 += ut1 * ut1;
+              a1 += dut * dut;
+              a2 += dd * dd;
+              a4 += ln.y * ln.y;
+            }
+            *reinterpret_cast<T2*>(lc + 2 * k) = ln;   // lambda stays 0 on pore voxels
+          }
+        }
+      }
+      if (c == 1) {
+        cp_async_wait<0>();
+        __syncwarp(mask);
+      }
+    }
+    d5[0] += (double)a0;
+    d5[1] += (double)a1;
+    d5[2] += (double)a2;
+    d5[3] += (double)a3;
+    d5[4] += (double)a4;
   }
-  double v5[5] = {(double)a0, (double)a1, (double)a2, (double)a3, (double)a4};
-  block_sum_store<5>(v5, red, part + ((long long)p * gridDim.x + blockIdx.x) * 8);
+  block_sum_store<5>(d5, red, part + ((long long)p * gridDim.x + blockIdx.x) * 8);
 }
 
 // ---------------------------------------------------------------------------
@@ -364,72 +390,143 @@ __global__ void __launch_bounds__(3 * 64) k_x_stokes_rhs(cx<T>* __restrict__ spe
 }
 
 // ---------------------------------------------------------------------------
-// Solute x-pass: C2R of grad chi^n (3 components), local terms of Eq. 18:
+// Solute x-pass: C2R of the gradient of chi^n (3 components), local terms of Eq. 18:
 //   tau = (A - A0)(grad chi + g),  s = F - (B - B0).(grad chi + g),
 //   A = (1 - H) + eta H,  B = Pe (1 - H) u,  F = Pe (1 - H) ubar.g,
-// then R2C of (tau_0, tau_1, tau_2, s).
+// then R2C of (tau_0, tau_1, tau_2, s), stored as (tau_0, tau_1, s + i d2 tau_2).
+//
+// Line-resident (acm_xline.cuh): every warp owns LPW lines; their three
+// spectrum rows arrive by cp.async, then each component is inverse-transformed
+// into registers, turned into tau_c (and its share of s accumulated) on the
+// same registers and forward-transformed, without a block-wide barrier.
 // ---------------------------------------------------------------------------
 template <typename T, int N2>
-__global__ void __launch_bounds__(4 * 64) k_x_solute(cx<T>* __restrict__ spec, const T* __restrict__ u,
-                                                    const uint8_t* __restrict__ H,
-                                                    const SoluteDev* __restrict__ prm, Geo g,
-                                                    const cx<T>* __restrict__ twg, const T* __restrict__ d2) {
-  using C = XCfg<T, N2>;
-  using Lay = XLayout<T, N2, 4, 3>;
-  constexpr int TOT = Lay::TOT;
+__global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
+    k_x_solute(cx<T>* __restrict__ spec, const T* __restrict__ u, const uint8_t* __restrict__ H,
+               const uint32_t* __restrict__ Hb, const SoluteDev* __restrict__ prm, Geo g,
+               const cx<T>* __restrict__ twg, const T* __restrict__ d2) {
+  using L = XL<T, N2>;
+  constexpr int M = L::M, E = L::E, TL = L::TL, LPW = L::LPW, LS = L::LS;
+  constexpr int LB = L::template lb<2>();
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* tw = sm + Lay::TW;
-  T* su = reinterpret_cast<T*>(smem_raw + Lay::RB);   // [3][TOT] u on pore voxels, 0 on solid ones
-  uint8_t* sh = smem_raw + Lay::HB;                    // [TOT] H
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* lines = tw + xs_tw_slots<T, N2>();
+  // s accumulated per lane: [m][lane] for conflict-free access
+  T* acc = reinterpret_cast<T*>(lines + XS_WARPS * LPW * LB) + (threadIdx.x >> 5) * 32 * 2 * E;
   const int p = blockIdx.y;
   const SoluteDev* P = prm + p;
   if (P->done) return;
+  load_tw_x<T, N2>(tw, twg);
+  __syncthreads();
   const T A0 = (T)P->A0, eta = (T)P->eta, Pe = (T)P->Pe, Fc = (T)P->Fc;
-  const T g0 = (T)P->g[0], g1 = (T)P->g[1], g2 = (T)P->g[2];
-  const T B00 = (T)P->B0[0], B01 = (T)P->B0[1], B02 = (T)P->B0[2];
-  const int line0 = blockIdx.x * C::LPB;
-  const long long v0 = (long long)line0 * N2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ll = lane / TL, t = lane % TL;
+  const unsigned mask = xl_mask();
+  cx<T>* b0 = lines + (warp * LPW + ll) * LB;
+  cx<T>* b1 = b0 + LS;
   cx<T>* sp = spec + (long long)p * 4 * g.S;
   const T* up = u + (long long)p * g.us;
-  const uint8_t* Hp = H + (long long)(p / g.lph) * g.hs;
-  cx<T>* nyq = reinterpret_cast<cx<T>*>(smem_raw + Lay::QB);
-  x_load_spec_raw_async<T, N2, 3>(sm, nyq, sp, g.S, g.P, line0);
-  for (int i = threadIdx.x; i < TOT / 16; i += blockDim.x) cp_async<16>(sh + 16 * i, Hp + v0 + 16 * i);
-  cp_async_commit();
-  load_tw_x<T, N2>(tw, twg);
-  cp_async_wait<0>();
-  __syncthreads();
-  for (int i = threadIdx.x; i < 3 * TOT; i += blockDim.x) {
-    const int c = i / TOT, e = i - c * TOT;
-    cp_async_pred<(int)sizeof(T)>(su + i, up + c * g.V + v0 + e, sh[e] == 0);
+  const long long hcell = (long long)(p / g.lph) * g.hs;
+  const uint8_t* Hp = H + hcell;
+  const uint32_t* Hbp = Hb + hcell / 32;
+  const int ngroups = g.n0 * g.n1 / LPW;
+  const int gbase = (blockIdx.x * XS_WARPS + warp) * XS_GPW;
+#pragma unroll 1
+  for (int gi = 0; gi < XS_GPW; ++gi) {
+    const int grp = gbase + gi;
+    if (grp >= ngroups) break;
+    const long long line = (long long)grp * LPW + ll;
+    const long long v0 = line * N2;
+    const cx<T>* srow = sp + line * g.P;
+    // spectrum rows of d0 chi and d1 chi (that of chi follows into b0 later)
+    __syncwarp(mask);
+    for (int e = t; e <= M; e += TL) {
+      cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[e]);
+      cp_async<(int)sizeof(cx<T>)>(&b1[pad(e)], &srow[g.S + e]);
+    }
+    cp_async_commit();
+    if (lane == 0) {
+      // the group's velocity rows and the next group's spectrum rows, on their way to L2
+      const long long w0 = (long long)grp * LPW * N2;
+      constexpr unsigned RB = LPW * N2 * sizeof(T);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) prefetch_l2(up + c * g.V + w0, RB);
+      if (gi + 1 < XS_GPW && grp + 1 < ngroups) {
+        const unsigned SB = (unsigned)(LPW * g.P * sizeof(cx<T>));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) prefetch_l2(sp + c * g.S + (long long)(grp + 1) * LPW * g.P, SB);
+      }
+    }
+    const unsigned hm = xl_hmask<N2, TL, E>(Hbp, Hp, line, t);
+#pragma unroll
+    for (int m = 0; m < 2 * E; ++m) acc[m * 32 + lane] = (T)0;
+    cp_async_wait<0>();
+    __syncwarp(mask);
+    cx<T> v[E];
+    // components 0..2: tau_c from the gradient of chi; component 3: s
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+      cx<T>* bc = c == 1 ? b1 : b0;
+      if (c < 3) {
+        xl_inverse<T, N2>(bc, tw, t, mask, v, c == 2 ? d2 : nullptr);
+        const T gc = (T)(c == 0 ? P->g[0] : c == 1 ? P->g[1] : P->g[2]);
+        const T Bc = (T)(c == 0 ? P->B0[0] : c == 1 ? P->B0[1] : P->B0[2]);
+        const T* uc = up + c * g.V + v0;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int k = t + TL * m;
+          const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
+          T2 uu;
+          if (sa && sb) {
+            uu.x = (T)0;
+            uu.y = (T)0;
+          } else {
+            uu = *reinterpret_cast<const T2*>(uc + 2 * k);
+          }
+          const T ea = v[m].x + gc, eb = v[m].y + gc;
+          acc[(2 * m) * 32 + lane] += (Bc - (sa ? (T)0 : Pe * uu.x)) * ea;
+          acc[(2 * m + 1) * 32 + lane] += (Bc - (sb ? (T)0 : Pe * uu.y)) * eb;
+          v[m].x = ((sa ? eta : (T)1) - A0) * ea;
+          v[m].y = ((sb ? eta : (T)1) - A0) * eb;
+        }
+      } else {
+        // s = F - (B - B0).(grad chi + g): the accumulated terms plus Pe ubar.g on pore voxels
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
+          v[m] = mk<T>(acc[(2 * m) * 32 + lane] + (sa ? (T)0 : Fc), acc[(2 * m + 1) * 32 + lane] + (sb ? (T)0 : Fc));
+        }
+      }
+      cx<T> xn;
+      xl_forward<T, N2>(bc, tw, t, mask, v, v, xn);
+      if (c < 2) {
+        cx<T>* dst = sp + c * g.S + line * g.P;
+#pragma unroll
+        for (int m = 0; m < E; ++m) dst[t + TL * m] = v[m];
+        if (t == 0) dst[M] = xn;
+        if (c == 0) {
+          // the row of chi into b0, hidden behind component 1
+          __syncwarp(mask);
+          for (int e = t; e <= M; e += TL) cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[2 * g.S + e]);
+          cp_async_commit();
+        } else {
+          cp_async_wait<0>();
+          __syncwarp(mask);
+        }
+      } else if (c == 2) {
+        // i d2 tau_2^ waits in b1 (own positions only)
+#pragma unroll
+        for (int m = 0; m < E; ++m) b1[pad(t + TL * m)] = cscale(mul_i(v[m]), d2[t + TL * m]);
+        if (t == 0) b1[pad(M)] = cscale(mul_i(xn), d2[M]);
+      } else {
+        cx<T>* dst = sp + 2 * g.S + line * g.P;
+#pragma unroll
+        for (int m = 0; m < E; ++m) dst[t + TL * m] = v[m] + b1[pad(t + TL * m)];
+        if (t == 0) dst[M] = xn + b1[pad(M)];
+      }
+    }
   }
-  cp_async_commit();
-  // components 0, 1 hold the x spectra of d0 chi and d1 chi, component 2 that of chi
-  x_pre_smem<T, N2, 3>(sm, nyq, tw, 2, d2);
-  __syncthreads();
-  x_fft<T, N2, 3, +1>(sm, tw);
-  cp_async_wait<0>();
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < TOT; idx += blockDim.x) {
-    const int l = idx / N2, n = idx & (N2 - 1);
-    const bool solid = sh[idx] != 0;
-    T& r0 = re_at(sm + (0 * C::LPB + l) * C::LS, n);
-    T& r1 = re_at(sm + (1 * C::LPB + l) * C::LS, n);
-    T& r2 = re_at(sm + (2 * C::LPB + l) * C::LS, n);
-    const T e0 = r0 + g0, e1 = r1 + g1, e2 = r2 + g2;
-    const T Am = (solid ? eta : (T)1) - A0;
-    T s = B00 * e0 + B01 * e1 + B02 * e2;
-    if (!solid) s += Fc - Pe * (su[idx] * e0 + su[TOT + idx] * e1 + su[2 * TOT + idx] * e2);
-    r0 = Am * e0;
-    r1 = Am * e1;
-    r2 = Am * e2;
-    re_at(sm + (3 * C::LPB + l) * C::LS, n) = s;
-  }
-  __syncthreads();
-  x_fft<T, N2, 4, -1>(sm, tw);
-  __syncthreads();
-  x_post_store_solute<T, N2>(sm, sp, g.S, g.P, line0, tw, d2);
 }
 
 // ---------------------------------------------------------------------------

@@ -180,6 +180,21 @@ cudaError_t solute_finalize(int nprob, SoluteDev* prm, const double* part_z, int
   return cudaGetLastError();
 }
 
+// one bit per voxel of H: word w holds voxels 32 w .. 32 w + 31 (n a multiple of
+// 32, so every warp of the grid-stride loop sees 32 valid voxels)
+__global__ void k_hbits(const uint8_t* __restrict__ H, uint32_t* __restrict__ Hb, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned b = __ballot_sync(0xffffffffu, H[i] != 0);
+    if ((threadIdx.x & 31) == 0) Hb[i >> 5] = b;
+  }
+}
+
+cudaError_t pack_hbits(const uint8_t* H, uint32_t* Hb, long long n, cudaStream_t s) {
+  if (n % 32 != 0) return cudaErrorInvalidValue;
+  k_hbits<<<608, 256, 0, s>>>(H, Hb, n);
+  return cudaGetLastError();
+}
+
 cudaError_t count_solid(const uint8_t* H, long long V, unsigned long long* out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;

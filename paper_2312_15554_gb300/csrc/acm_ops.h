@@ -24,12 +24,13 @@ struct Ops {
   static bool tx_variant(int n, int op, int nc, int shift);
 
   static cudaError_t x_stokes_local(const Geo& g, int nprob, const void* spec, void* u, void* lam,
-                                    const uint8_t* H, StokesDev* prm, double* part, const void* tw,
-                                    cudaStream_t s);
+                                    const uint8_t* H, const uint32_t* Hb, StokesDev* prm, double* part,
+                                    const void* tw, cudaStream_t s);
   static cudaError_t x_stokes_rhs(const Geo& g, int nprob, void* spec, const void* u, const void* lam,
                                   const uint8_t* H, const StokesDev* prm, const void* tw, cudaStream_t s);
   static cudaError_t x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                              const SoluteDev* prm, const void* tw, const Sym<T>& sym, cudaStream_t s);
+                              const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym,
+                              cudaStream_t s);
   // component 2 of each problem's spectrum (stride ps) times i d2(kx), in place
   static cudaError_t mul_id2(const Geo& g, int nprob, void* spec, long long ps, const Sym<T>& sym, cudaStream_t s);
   // nc in {1, 3}
@@ -64,6 +65,8 @@ cudaError_t stokes_finalize(int nprob, StokesDev* prm, const double* part_x, int
 cudaError_t solute_finalize(int nprob, SoluteDev* prm, const double* part_z, int nbz, double V, double* hist,
                             int hist_cap, cudaStream_t s);
 cudaError_t count_solid(const uint8_t* H, long long V, unsigned long long* out, cudaStream_t s);
+// Hb[w] = bits of H[32 w .. 32 w + 31] (n a multiple of 32)
+cudaError_t pack_hbits(const uint8_t* H, uint32_t* Hb, long long n, cudaStream_t s);
 cudaError_t count_solid_add(const uint8_t* H, long long V, unsigned long long* out, cudaStream_t s);
 
 // Condition of the device-resident loop (a CUDA graph while node): continue

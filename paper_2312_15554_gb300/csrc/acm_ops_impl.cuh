@@ -36,13 +36,13 @@ static cudaError_t set_smem(K* k, int bytes) {
 
 template <typename T, int N2>
 static cudaError_t l_x_local(const Geo& g, int nprob, const void* spec, void* u, void* lam, const uint8_t* H,
-                             StokesDev* prm, double* part, const void* tw, cudaStream_t s) {
-  constexpr int smem = XLayout<T, N2, 3, 6>::BYTES;
+                             const uint32_t* Hb, StokesDev* prm, double* part, const void* tw, cudaStream_t s) {
+  constexpr int smem = xs_smem_bytes<T, N2, 2, 0>();
   static const cudaError_t attr = set_smem(k_x_stokes_local<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
-  dim3 grid(g.n0 * g.n1 / XCfg<T, N2>::LPB, nprob);
-  k_x_stokes_local<T, N2><<<grid, 3 * 64, smem, s>>>((const cx<T>*)spec, (T*)u, (T*)lam, H, prm, part, g,
-                                                     (const cx<T>*)tw);
+  dim3 grid(xs_blocks(g.n0 * g.n1, XL<T, N2>::LPW), nprob);
+  k_x_stokes_local<T, N2><<<grid, XS_WARPS * 32, smem, s>>>((const cx<T>*)spec, (T*)u, (T*)lam, H, Hb, prm, part, g,
+                                                            (const cx<T>*)tw);
   return cudaGetLastError();
 }
 
@@ -60,12 +60,13 @@ static cudaError_t l_x_rhs(const Geo& g, int nprob, void* spec, const void* u, c
 
 template <typename T, int N2>
 static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                              const SoluteDev* prm, const void* tw, const T* d2, cudaStream_t s) {
-  constexpr int smem = XLayout<T, N2, 4, 3>::BYTES;
+                              const uint32_t* Hb, const SoluteDev* prm, const void* tw, const T* d2, cudaStream_t s) {
+  constexpr int smem = xs_smem_bytes<T, N2, 2, 2 * XL<T, N2>::E>();
   static const cudaError_t attr = set_smem(k_x_solute<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
-  dim3 grid(g.n0 * g.n1 / XCfg<T, N2>::LPB, nprob);
-  k_x_solute<T, N2><<<grid, 4 * 64, smem, s>>>((cx<T>*)spec, (const T*)u, H, prm, g, (const cx<T>*)tw, d2);
+  dim3 grid(xs_blocks(g.n0 * g.n1, XL<T, N2>::LPW), nprob);
+  k_x_solute<T, N2><<<grid, XS_WARPS * 32, smem, s>>>((cx<T>*)spec, (const T*)u, H, Hb, prm, g, (const cx<T>*)tw,
+                                                        d2);
   return cudaGetLastError();
 }
 
@@ -231,7 +232,7 @@ template <typename T>
 int Ops<T>::x_blocks(const Geo& g) {
   const int M = g.n2 / 2;
   const int TL = M / ept(M);
-  return g.n0 * g.n1 / (64 / TL);
+  return xs_blocks(g.n0 * g.n1, 32 / TL);
 }
 
 template <typename T>
@@ -268,8 +269,8 @@ int Ops<T>::z_blocks(const Geo& g, int op) {
 
 template <typename T>
 cudaError_t Ops<T>::x_stokes_local(const Geo& g, int nprob, const void* spec, void* u, void* lam, const uint8_t* H,
-                                   StokesDev* prm, double* part, const void* tw, cudaStream_t s) {
-  ACM_DISPATCH_N(g.n2, l_x_local, g, nprob, spec, u, lam, H, prm, part, tw, s)
+                                   const uint32_t* Hb, StokesDev* prm, double* part, const void* tw, cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_local, g, nprob, spec, u, lam, H, Hb, prm, part, tw, s)
 }
 
 template <typename T>
@@ -280,8 +281,9 @@ cudaError_t Ops<T>::x_stokes_rhs(const Geo& g, int nprob, void* spec, const void
 
 template <typename T>
 cudaError_t Ops<T>::x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                             const SoluteDev* prm, const void* tw, const Sym<T>& sym, cudaStream_t s) {
-  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, prm, tw, sym.d2, s)
+                             const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym,
+                             cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, Hb, prm, tw, sym.d2, s)
 }
 
 template <typename T>

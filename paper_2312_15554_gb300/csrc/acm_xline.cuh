@@ -1,0 +1,181 @@
+// acm_xline.cuh -- x passes with line-resident components.
+//
+// A real line of N2 values along the contiguous axis is transformed as a
+// complex line of M = N2/2 values z_j = x_{2j} + i x_{2j+1} (see the pre- and
+// post-processing formulas in acm_kernels.cuh). TL = M/E consecutive lanes of
+// a warp own one line; lane t of the line holds the E elements
+// z[t + TL m], m = 0..E-1, in registers.
+//
+// With E = 16 and TL > 1 the transform has two Stockham stages (radix E, then
+// radix TL). The first stage reads exactly the elements t + TL m of its own
+// lane, and the second stage leaves its lane with exactly those positions too,
+// so between an inverse and a forward transform the local step of the method
+// runs on registers, and the voxels 2k, 2k+1 (k = t + TL m) of every component
+// belong to the same lane. Shared memory carries only the exchange between the
+// two stages, the pairing of k with M - k in the real-transform pre- and
+// post-processing, and the spectrum rows on their way in. A line's lanes sit in
+// one warp, so every synchronisation is a __syncwarp of those lanes.
+#pragma once
+
+#include "acm_fft.cuh"
+
+namespace acm {
+
+template <typename T, int N2>
+struct XL {
+  static constexpr int M = N2 / 2;
+  static constexpr int E = ept(M);
+  static constexpr int TL = M / E;        // lanes per line
+  static constexpr int LPW = 32 / TL;     // lines per warp
+  static constexpr int NB = E / TL;       // second-stage groups per lane (TL > 1)
+  // slots per line buffer: X[0..M] (pad(M) included), bank-friendly for TL lanes
+  static constexpr int LS = line_stride(M + 1, TL, 0, wave_slots<T>());
+  // stride between the consecutive lines of a warp holding NBUF buffers each:
+  // an odd multiple of TL modulo the wavefront, so that the lines of one
+  // access fall on different banks
+  template <int NBUF>
+  __host__ __device__ static constexpr int lb() {
+    constexpr int W = wave_slots<T>();
+    int s = NBUF * LS;
+    if (TL < W)
+      while ((s / TL) % 2 == 0 || s % TL != 0) ++s;
+    return s;
+  }
+};
+
+// Indicator bits of the lane's voxels 2k, 2k+1 (k = t + TL m) as bits 2m, 2m+1.
+// Hb: one bit per voxel, 32 voxels per word in index order (lines of N2 >= 32
+// voxels start on a word); the words of a line are read by all its lanes.
+// Shorter lines read the bytes of H.
+template <int N2, int TL, int E>
+__device__ __forceinline__ unsigned xl_hmask(const uint32_t* __restrict__ Hb, const uint8_t* __restrict__ H,
+                                             long long line, int t) {
+  unsigned hm = 0;
+  if constexpr (N2 >= 32) {
+    constexpr int NW = N2 / 32, SPW = 16 / TL;  // values of m per word
+    const uint32_t* w = Hb + line * NW;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const unsigned word = __ldg(w + m / SPW);
+      hm |= ((word >> (2 * t + 2 * TL * (m % SPW))) & 3u) << (2 * m);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const uchar2 h = *reinterpret_cast<const uchar2*>(H + line * N2 + 2 * (t + TL * m));
+      hm |= (h.x ? 1u : 0u) << (2 * m) | (h.y ? 1u : 0u) << (2 * m + 1);
+    }
+  }
+  return hm;
+}
+
+// Mask of the lanes of a warp that own lines (all of them when the warp is full).
+__device__ __forceinline__ unsigned xl_mask() { return 0xffffffffu; }
+
+// Z_k from the half spectrum: (X_k + conj X_{M-k}) + i (X_k - conj X_{M-k}) conj(W^k)
+template <typename T>
+__device__ __forceinline__ cx<T> xl_pre(cx<T> X, cx<T> Y, cx<T> w) {
+  const cx<T> e = X + cconj(Y), o = cmul(X - cconj(Y), cconj(w));
+  return e + mul_i(o);
+}
+
+// X_k from Z: (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2  (k = 1..M-1)
+template <typename T>
+__device__ __forceinline__ cx<T> xl_post(cx<T> Zk, cx<T> Zm, cx<T> w) {
+  const T h = (T)0.5;
+  const cx<T> a = cscale(Zk + cconj(Zm), h), b = cscale(Zk - cconj(Zm), h);
+  return a - mul_i(cmul(w, b));
+}
+
+// Second Stockham stage (radix TL, span E) between shared memory and v:
+// reads positions t + TL i + E r, writes nothing; v[i + NB r] = outputs.
+template <typename T, int N2, int SIGN>
+__device__ __forceinline__ void xl_stage2(const cx<T>* sl, const cx<T>* tw, int t, cx<T> (&v)[XL<T, N2>::E]) {
+  using L = XL<T, N2>;
+  constexpr int M = L::M, E = L::E, TL = L::TL, NB = L::NB;
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int j = t + TL * i;  // j < E: jm = j
+    cx<T> w2[TL];
+#pragma unroll
+    for (int r = 0; r < TL; ++r) w2[r] = sl[pad(j + E * r)];
+    const cx<T>* tws = tw + tw_offset(M, E) + j;
+#pragma unroll
+    for (int r = 1; r < TL; ++r) {
+      cx<T> w = tws[(r - 1) * E];
+      if constexpr (SIGN > 0) w.y = -w.y;
+      w2[r] = cmul(w2[r], w);
+    }
+    dft<TL, SIGN>(w2);
+#pragma unroll
+    for (int r = 0; r < TL; ++r) v[i + NB * r] = w2[r];
+  }
+}
+
+// Inverse real transform of one line. sl holds the half spectrum X[0..M]
+// (at pad(k)) and is visible to all lanes of the line. With d non-null, X_k is
+// first multiplied by i d[k] (the derivative along the line). On return v[m] =
+// z[t + TL m]; sl is free for reuse by the line's lanes.
+template <typename T, int N2>
+__device__ __forceinline__ void xl_inverse(cx<T>* sl, const cx<T>* tw, int t, unsigned mask,
+                                           cx<T> (&v)[XL<T, N2>::E], const T* __restrict__ d) {
+  using L = XL<T, N2>;
+  constexpr int M = L::M, E = L::E, TL = L::TL;
+  const cx<T>* twp = tw + tw_total(M);
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int k = t + TL * r;
+    cx<T> X = sl[pad(k)], Y = sl[pad(M - k)];
+    if (d) {
+      X = cscale(mul_i(X), d[k]);
+      Y = cscale(mul_i(Y), d[M - k]);
+    }
+    v[r] = xl_pre(X, Y, twp[k]);
+  }
+  dft<E, +1>(v);
+  if constexpr (TL > 1) {
+    __syncwarp(mask);  // every lane has read its X pairs
+#pragma unroll
+    for (int r = 0; r < E; ++r) sl[pad(t * E + r)] = v[r];
+    __syncwarp(mask);
+    xl_stage2<T, N2, +1>(sl, tw, t, v);
+    __syncwarp(mask);  // the stage-2 reads are done before sl is reused
+  }
+}
+
+// Forward real transform of one line: v[m] = z[t + TL m] in; on return
+// X[m] = X_{t + TL m} (m = 0..E-1) and, on lane t = 0, xn = X_M. sl is used
+// as exchange buffer (its previous contents are dropped).
+template <typename T, int N2>
+__device__ __forceinline__ void xl_forward(cx<T>* sl, const cx<T>* tw, int t, unsigned mask,
+                                           cx<T> (&v)[XL<T, N2>::E], cx<T> (&X)[XL<T, N2>::E], cx<T>& xn) {
+  using L = XL<T, N2>;
+  constexpr int M = L::M, E = L::E, TL = L::TL;
+  const cx<T>* twp = tw + tw_total(M);
+  dft<E, -1>(v);
+  __syncwarp(mask);  // earlier readers of sl are done
+#pragma unroll
+  for (int r = 0; r < E; ++r) sl[pad(t * E + r)] = v[r];
+  if constexpr (TL > 1) {
+    __syncwarp(mask);
+    xl_stage2<T, N2, -1>(sl, tw, t, v);
+    __syncwarp(mask);
+    // stage-2 outputs back to their positions t + TL m for the pairing
+#pragma unroll
+    for (int m = 0; m < E; ++m) sl[pad(t + TL * m)] = v[m];
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + TL * m;
+    const cx<T> Zk = sl[pad(k)];
+    if (k == 0) {
+      X[m] = mk<T>(Zk.x + Zk.y, (T)0);
+      xn = mk<T>(Zk.x - Zk.y, (T)0);
+    } else {
+      X[m] = xl_post(Zk, sl[pad(M - k)], twp[k]);
+    }
+  }
+}
+
+}  // namespace acm
