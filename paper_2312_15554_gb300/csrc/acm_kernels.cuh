@@ -404,7 +404,7 @@ template <typename T, int N2>
 __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
     k_x_solute(cx<T>* __restrict__ spec, const T* __restrict__ u, const uint8_t* __restrict__ H,
                const uint32_t* __restrict__ Hb, const SoluteDev* __restrict__ prm, Geo g,
-               const cx<T>* __restrict__ twg, const T* __restrict__ d2) {
+               const cx<T>* __restrict__ twg, const T* __restrict__ d2, int nprob, int gpw) {
   using L = XL<T, N2>;
   constexpr int M = L::M, E = L::E, TL = L::TL, LPW = L::LPW, LS = L::LS;
   constexpr int LB = L::template lb<2>();
@@ -414,116 +414,129 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
   cx<T>* lines = tw + xs_tw_slots<T, N2>();
   // s accumulated per lane: [m][lane] for conflict-free access
   T* acc = reinterpret_cast<T*>(lines + XS_WARPS * LPW * LB) + (threadIdx.x >> 5) * 32 * 2 * E;
-  const int p = blockIdx.y;
-  const SoluteDev* P = prm + p;
-  if (P->done) return;
+  // Problems that share one velocity and indicator (us = hs = 0, e.g. the three
+  // composition loads of a tensor solve) run back to back on the same warp, so
+  // each velocity row crosses DRAM once; otherwise blockIdx.y is the problem.
+  const bool shared = g.us == 0 && g.hs == 0;
+  const int pbeg = shared ? 0 : blockIdx.y, pend = shared ? nprob : blockIdx.y + 1;
+  bool any = false;
+  for (int p = pbeg; p < pend; ++p) any = any || !prm[p].done;
+  if (!any) return;
   load_tw_x<T, N2>(tw, twg);
   __syncthreads();
-  const T A0 = (T)P->A0, eta = (T)P->eta, Pe = (T)P->Pe, Fc = (T)P->Fc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ll = lane / TL, t = lane % TL;
   const unsigned mask = xl_mask();
   cx<T>* b0 = lines + (warp * LPW + ll) * LB;
   cx<T>* b1 = b0 + LS;
-  cx<T>* sp = spec + (long long)p * 4 * g.S;
-  const T* up = u + (long long)p * g.us;
-  const long long hcell = (long long)(p / g.lph) * g.hs;
-  const uint8_t* Hp = H + hcell;
-  const uint32_t* Hbp = Hb + hcell / 32;
   const int ngroups = g.n0 * g.n1 / LPW;
-  const int gbase = (blockIdx.x * XS_WARPS + warp) * XS_GPW;
+  const int gbase = (blockIdx.x * XS_WARPS + warp) * gpw;
 #pragma unroll 1
-  for (int gi = 0; gi < XS_GPW; ++gi) {
+  for (int gi = 0; gi < gpw; ++gi) {
     const int grp = gbase + gi;
     if (grp >= ngroups) break;
     const long long line = (long long)grp * LPW + ll;
     const long long v0 = line * N2;
-    const cx<T>* srow = sp + line * g.P;
-    // spectrum rows of d0 chi and d1 chi (that of chi follows into b0 later)
-    __syncwarp(mask);
-    for (int e = t; e <= M; e += TL) {
-      cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[e]);
-      cp_async<(int)sizeof(cx<T>)>(&b1[pad(e)], &srow[g.S + e]);
-    }
-    cp_async_commit();
-    if (lane == 0) {
-      // the group's velocity rows and the next group's spectrum rows, on their way to L2
-      const long long w0 = (long long)grp * LPW * N2;
-      constexpr unsigned RB = LPW * N2 * sizeof(T);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) prefetch_l2(up + c * g.V + w0, RB);
-      if (gi + 1 < XS_GPW && grp + 1 < ngroups) {
-        const unsigned SB = (unsigned)(LPW * g.P * sizeof(cx<T>));
-#pragma unroll
-        for (int c = 0; c < 3; ++c) prefetch_l2(sp + c * g.S + (long long)(grp + 1) * LPW * g.P, SB);
-      }
-    }
-    const unsigned hm = xl_hmask<N2, TL, E>(Hbp, Hp, line, t);
-#pragma unroll
-    for (int m = 0; m < 2 * E; ++m) acc[m * 32 + lane] = (T)0;
-    cp_async_wait<0>();
-    __syncwarp(mask);
-    cx<T> v[E];
-    // components 0..2: tau_c from the gradient of chi; component 3: s
+    // the indicator is the same for every problem of the loop (hs = 0 when shared)
+    const long long hcell = (long long)(pbeg / g.lph) * g.hs;
+    const unsigned hm = xl_hmask<N2, TL, E>(Hb + hcell / 32, H + hcell, line, t);
 #pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-      cx<T>* bc = c == 1 ? b1 : b0;
-      if (c < 3) {
-        xl_inverse<T, N2>(bc, tw, t, mask, v, c == 2 ? d2 : nullptr);
-        const T gc = (T)(c == 0 ? P->g[0] : c == 1 ? P->g[1] : P->g[2]);
-        const T Bc = (T)(c == 0 ? P->B0[0] : c == 1 ? P->B0[1] : P->B0[2]);
-        const T* uc = up + c * g.V + v0;
+    for (int p = pbeg; p < pend; ++p) {
+      const SoluteDev* P = prm + p;
+      if (P->done) continue;
+      cx<T>* sp = spec + (long long)p * 4 * g.S;
+      const T* up = u + (long long)p * g.us;
+      const cx<T>* srow = sp + line * g.P;
+      // spectrum rows of d0 chi and d1 chi (that of chi follows into b0 later)
+      __syncwarp(mask);
+      for (int e = t; e <= M; e += TL) {
+        cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[e]);
+        cp_async<(int)sizeof(cx<T>)>(&b1[pad(e)], &srow[g.S + e]);
+      }
+      cp_async_commit();
+      if (lane == 0) {
+        // the group's velocity rows (once for problems that share them) and the
+        // next group's spectrum rows, on their way to L2
+        const long long w0 = (long long)grp * LPW * N2;
+        constexpr unsigned RB = LPW * N2 * sizeof(T);
+        if (p == pbeg || !shared) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-          const int k = t + TL * m;
-          const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
-          T2 uu;
-          if (sa && sb) {
-            uu.x = (T)0;
-            uu.y = (T)0;
-          } else {
-            uu = *reinterpret_cast<const T2*>(uc + 2 * k);
-          }
-          const T ea = v[m].x + gc, eb = v[m].y + gc;
-          acc[(2 * m) * 32 + lane] += (Bc - (sa ? (T)0 : Pe * uu.x)) * ea;
-          acc[(2 * m + 1) * 32 + lane] += (Bc - (sb ? (T)0 : Pe * uu.y)) * eb;
-          v[m].x = ((sa ? eta : (T)1) - A0) * ea;
-          v[m].y = ((sb ? eta : (T)1) - A0) * eb;
+          for (int c = 0; c < 3; ++c) prefetch_l2(up + c * g.V + w0, RB);
         }
-      } else {
-        // s = F - (B - B0).(grad chi + g): the accumulated terms plus Pe ubar.g on pore voxels
+        if (gi + 1 < gpw && grp + 1 < ngroups) {
+          const unsigned SB = (unsigned)(LPW * g.P * sizeof(cx<T>));
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-          const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
-          v[m] = mk<T>(acc[(2 * m) * 32 + lane] + (sa ? (T)0 : Fc), acc[(2 * m + 1) * 32 + lane] + (sb ? (T)0 : Fc));
+          for (int c = 0; c < 3; ++c) prefetch_l2(sp + c * g.S + (long long)(grp + 1) * LPW * g.P, SB);
         }
       }
-      cx<T> xn;
-      xl_forward<T, N2>(bc, tw, t, mask, v, v, xn);
-      if (c < 2) {
-        cx<T>* dst = sp + c * g.S + line * g.P;
 #pragma unroll
-        for (int m = 0; m < E; ++m) dst[t + TL * m] = v[m];
-        if (t == 0) dst[M] = xn;
-        if (c == 0) {
-          // the row of chi into b0, hidden behind component 1
-          __syncwarp(mask);
-          for (int e = t; e <= M; e += TL) cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[2 * g.S + e]);
-          cp_async_commit();
+      for (int m = 0; m < 2 * E; ++m) acc[m * 32 + lane] = (T)0;
+      cp_async_wait<0>();
+      __syncwarp(mask);
+      cx<T> v[E];
+      // components 0..2: tau_c from the gradient of chi; component 3: s
+#pragma unroll 1
+      for (int c = 0; c < 4; ++c) {
+        cx<T>* bc = c == 1 ? b1 : b0;
+        if (c < 3) {
+          xl_inverse<T, N2>(bc, tw, t, mask, v, c == 2 ? d2 : nullptr);
+          const T gc = (T)(c == 0 ? P->g[0] : c == 1 ? P->g[1] : P->g[2]);
+          const T Bc = (T)(c == 0 ? P->B0[0] : c == 1 ? P->B0[1] : P->B0[2]);
+          const T A0 = (T)P->A0, eta = (T)P->eta, Pe = (T)P->Pe;
+          const T* uc = up + c * g.V + v0;
+#pragma unroll
+          for (int m = 0; m < E; ++m) {
+            const int k = t + TL * m;
+            const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
+            T2 uu;
+            if (sa && sb) {
+              uu.x = (T)0;
+              uu.y = (T)0;
+            } else {
+              uu = *reinterpret_cast<const T2*>(uc + 2 * k);
+            }
+            const T ea = v[m].x + gc, eb = v[m].y + gc;
+            acc[(2 * m) * 32 + lane] += (Bc - (sa ? (T)0 : Pe * uu.x)) * ea;
+            acc[(2 * m + 1) * 32 + lane] += (Bc - (sb ? (T)0 : Pe * uu.y)) * eb;
+            v[m].x = ((sa ? eta : (T)1) - A0) * ea;
+            v[m].y = ((sb ? eta : (T)1) - A0) * eb;
+          }
         } else {
-          cp_async_wait<0>();
-          __syncwarp(mask);
+          // s = F - (B - B0).(grad chi + g): the accumulated terms plus Pe ubar.g on pore voxels
+          const T Fc = (T)P->Fc;
+#pragma unroll
+          for (int m = 0; m < E; ++m) {
+            const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
+            v[m] = mk<T>(acc[(2 * m) * 32 + lane] + (sa ? (T)0 : Fc), acc[(2 * m + 1) * 32 + lane] + (sb ? (T)0 : Fc));
+          }
         }
-      } else if (c == 2) {
-        // i d2 tau_2^ waits in b1 (own positions only)
+        cx<T> xn;
+        xl_forward<T, N2>(bc, tw, t, mask, v, v, xn);
+        if (c < 2) {
+          cx<T>* dst = sp + c * g.S + line * g.P;
 #pragma unroll
-        for (int m = 0; m < E; ++m) b1[pad(t + TL * m)] = cscale(mul_i(v[m]), d2[t + TL * m]);
-        if (t == 0) b1[pad(M)] = cscale(mul_i(xn), d2[M]);
-      } else {
-        cx<T>* dst = sp + 2 * g.S + line * g.P;
+          for (int m = 0; m < E; ++m) dst[t + TL * m] = v[m];
+          if (t == 0) dst[M] = xn;
+          if (c == 0) {
+            // the row of chi into b0, hidden behind component 1
+            __syncwarp(mask);
+            for (int e = t; e <= M; e += TL) cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[2 * g.S + e]);
+            cp_async_commit();
+          } else {
+            cp_async_wait<0>();
+            __syncwarp(mask);
+          }
+        } else if (c == 2) {
+          // i d2 tau_2^ waits in b1 (own positions only)
 #pragma unroll
-        for (int m = 0; m < E; ++m) dst[t + TL * m] = v[m] + b1[pad(t + TL * m)];
-        if (t == 0) dst[M] = xn + b1[pad(M)];
+          for (int m = 0; m < E; ++m) b1[pad(t + TL * m)] = cscale(mul_i(v[m]), d2[t + TL * m]);
+          if (t == 0) b1[pad(M)] = cscale(mul_i(xn), d2[M]);
+        } else {
+          cx<T>* dst = sp + 2 * g.S + line * g.P;
+#pragma unroll
+          for (int m = 0; m < E; ++m) dst[t + TL * m] = v[m] + b1[pad(t + TL * m)];
+          if (t == 0) dst[M] = xn + b1[pad(M)];
+        }
       }
     }
   }
