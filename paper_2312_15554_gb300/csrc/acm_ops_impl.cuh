@@ -112,8 +112,10 @@ static cudaError_t l_x_c2r(const Geo& g, int nprob, int nc, const void* spec, lo
 }
 
 // Autotuner candidates: the passes of the solver loops at N >= 64 also exist
-// with half and double the default tile width, when the variant stays within
-// 2..32 columns, 512 threads and 200 KB of shared memory.
+// with half, double and four times the default tile width, when the variant
+// stays within 2..32 columns, 1536 line threads (run in rounds of at most 512
+// or 1024) and 200 KB of shared memory. Wide tiles read longer row segments,
+// which matters most along the slowest axis.
 template <int N, int OP, int NC>
 constexpr bool tunable() {
   return N >= 64 && ((OP == OP_FWD && NC == 3) || (OP == OP_INV && NC == 3) || OP == OP_STOKES || OP == OP_SOLUTE ||
@@ -122,7 +124,7 @@ constexpr bool tunable() {
 
 template <typename T, int N, int OP, int NC, int TX>
 constexpr bool tx_ok() {
-  return TX >= 2 && TX <= 32 && NC * TX * (N / ept(N)) <= 512 &&
+  return TX >= 2 && TX <= 32 && NC * TX * (N / ept(N)) <= 1536 &&
          (NC * TX * line_stride(N, N / ept(N), TX, wave_slots<T>()) + tw_total(N)) * (int)sizeof(cx<T>) <= 200 * 1024;
 }
 
@@ -132,7 +134,8 @@ constexpr int resolved_tx(int shift) {
   constexpr int TX0 = pick_tx((int)sizeof(cx<T>), N, NC);
   if (tunable<N, OP, NC>()) {
     if (shift < 0 && tx_ok<T, N, OP, NC, TX0 / 2>()) return TX0 / 2;
-    if (shift > 0 && tx_ok<T, N, OP, NC, TX0 * 2>()) return TX0 * 2;
+    if (shift == 1 && tx_ok<T, N, OP, NC, TX0 * 2>()) return TX0 * 2;
+    if (shift == 2 && tx_ok<T, N, OP, NC, TX0 * 4>()) return TX0 * 4;
   }
   return TX0;
 }
@@ -185,8 +188,12 @@ static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long 
         return l_pass_kt<T, N, OP, NC, TX0 / 2>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm,
                                                 part, s, dm);
     if constexpr (tx_ok<T, N, OP, NC, TX0 * 2>())
-      if (sh > 0)
+      if (sh == 1)
         return l_pass_kt<T, N, OP, NC, TX0 * 2>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm,
+                                                part, s, dm);
+    if constexpr (tx_ok<T, N, OP, NC, TX0 * 4>())
+      if (sh == 2)
+        return l_pass_kt<T, N, OP, NC, TX0 * 4>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm,
                                                 part, s, dm);
   }
   return l_pass_kt<T, N, OP, NC, TX0>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, s, dm);

@@ -52,7 +52,7 @@ struct Geo {
   long long us; // stride of the advecting velocity between problems (0: shared)
   int lph;      // problems per indicator: problem p uses H + (p / lph) * hs
   // tile-width choice of the strided passes per [precision (FP64 = 1)][axis][pass op]:
-  // -1 half, 0 default, +1 double the default width (set by the autotuner)
+  // -1 half, 0 default, +1 double, +2 four times the default width (set by the autotuner)
   signed char txs[2][2][8] = {};
 };
 

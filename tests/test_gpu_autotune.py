@@ -21,12 +21,13 @@ DEV = "cuda:0"
 
 
 def _widths(lib, ctx, fp64):
-    """Compiled widths of each tuned pass: the default, half and double when they exist."""
+    """Compiled widths of each tuned pass: the default, and half, double and four
+    times it when they exist."""
     base = lib.acm_get_tiles(ctx, fp64)
     out = {}
     for k, w in base.items():
         opts = [w]
-        for cand in (w // 2, w * 2):
+        for cand in (w // 2, w * 2, w * 4):
             t = dict(base)
             t[k] = cand
             try:
