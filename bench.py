@@ -62,6 +62,13 @@ def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float) -> float:
     }.get(kind, 0.0)
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel at the default workload (256^3, porosity 0.35, 3 problems per launch),
+# from the ncu capture summarised in profiles/x_passes_and_z_pass_256_full.md.
+# An entry holds only while the kernel is unchanged since that capture.
+MEASURED_TRAFFIC = {"x_solute": 858.760704e6 + 566.645248e6}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -290,7 +297,8 @@ def run_gpu(args, rank, world, dist):
                          if v[1] and algorithmic_bytes_per_voxel(k, N, porosity) else None)}
             for k, v in prof.items() if v[1]}
 
-    ttk = time_to_permeability(acm, ctx, Hd, stream, args.ttk_long) if args.ttk else None
+    # time to permeability on one GPU only (several ranks would each hold a GPU for it)
+    ttk = time_to_permeability(acm, ctx, Hd, stream, args.ttk_long) if (args.ttk and world == 1) else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -310,7 +318,10 @@ def run_gpu(args, rank, world, dist):
                    "parallelism": f"independent cells x{world}", "tiles": tiles,
                    "autotune_s": round(tune_s, 3)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": MEASURED_TRAFFIC.get(dom) if (N == 256 and abs(POROSITY - 0.35) < 1e-9) else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, "
+                                       "profiles/x_passes_and_z_pass_256_full.md" if dom in MEASURED_TRAFFIC else None,
                      "peak_source": peak_src, "bytes_per_launch": bytes_per_launch},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * V),
@@ -526,7 +537,7 @@ def main():
     ap.add_argument("--iters", type=int, default=20, help="iterations per problem per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ttk", action="store_true",
+    ap.add_argument("--ttk", action=argparse.BooleanOptionalAction, default=True,
                     help="also measure time-to-permeability (K within 1e-4 of a long-run reference)")
     ap.add_argument("--ttk-long", type=int, default=20000, help="iterations of the reference run")
     ap.add_argument("--config", default="cell256", choices=["cell256", "batched", "grf512"],

@@ -415,7 +415,7 @@ acm_status stokes_step1(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
   g.hs = hs;
   g.lph = lph;
   const long long ps = 3 * g.S;
-  LK(ACM_K_X_STOKES_RHS, Ops<T>::x_stokes_rhs(g, nprob, w.spec, w.u, w.lam, Hdev, c->sprm, w.tw, c->st));
+  LK(ACM_K_X_STOKES_RHS, Ops<T>::x_stokes_rhs(g, nprob, w.spec, w.u, w.lam, Hdev, c->Hb, c->sprm, w.tw, c->st));
   LK(ACM_K_Y_FWD_STOKES, Ops<T>::pass(g, 1, P_FWD, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, c->sprm, nullptr, nullptr, c->st));
   LK(ACM_K_Z_STOKES, Ops<T>::pass(g, 0, P_STOKES, 3, nprob, w.spec, ps, sym, w.tw, w.st0, w.st1, c->sprm, nullptr, c->part_z, c->st));
   LK(ACM_K_Y_INV_STOKES, Ops<T>::pass(g, 1, P_INV, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, c->sprm, nullptr, nullptr, c->st));

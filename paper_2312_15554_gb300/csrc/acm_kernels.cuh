@@ -353,40 +353,89 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
 // Stokes x-pass 2: w = b u~ - a (Eq. 7 right-hand side), R2C along x
 // ---------------------------------------------------------------------------
 template <typename T, int N2>
-__global__ void __launch_bounds__(3 * 64) k_x_stokes_rhs(cx<T>* __restrict__ spec, const T* __restrict__ u,
-                                                        const T* __restrict__ lam, const uint8_t* __restrict__ H,
-                                                        const StokesDev* __restrict__ prm, Geo g,
-                                                        const cx<T>* __restrict__ twg) {
-  using C = XCfg<T, N2>;
+__global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
+    k_x_stokes_rhs(cx<T>* __restrict__ spec, const T* __restrict__ u, const T* __restrict__ lam,
+                   const uint8_t* __restrict__ H, const uint32_t* __restrict__ Hb, const StokesDev* __restrict__ prm,
+                   Geo g, const cx<T>* __restrict__ twg) {
+  using L = XL<T, N2>;
+  constexpr int M = L::M, E = L::E, TL = L::TL, LPW = L::LPW;
+  constexpr int LB = L::template lb<1>();
+  constexpr int CH = E < 8 ? E : 8;  // voxel pairs per chunk of loads
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* tw = sm + 3 * C::LPB * C::LS;
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* lines = tw + xs_tw_slots<T, N2>();
   const int p = blockIdx.y;
   const StokesDev* P = prm + p;
   if (P->done) return;
+  load_tw_x<T, N2>(tw, twg);
+  __syncthreads();
   const T b = (T)P->psi[2];
+  // u~^n on solid voxels = s_prev u^n with the penalties of the iteration just taken
   const T s_prev = (T)(P->psi_prev[2] / (P->psi_prev[2] + P->psi_prev[0]));
-  const int line0 = blockIdx.x * C::LPB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ll = lane / TL, t = lane % TL;
+  const unsigned mask = xl_mask();
+  cx<T>* bl = lines + (warp * LPW + ll) * LB;
   cx<T>* sp = spec + (long long)p * 3 * g.S;
   const T* up = u + (long long)p * 3 * g.V;
   const T* lp = lam + (long long)p * 3 * g.V;
-  const uint8_t* Hp = H + (long long)(p / g.lph) * g.hs;
-  load_tw_x<T, N2>(tw, twg);
-  for (int idx = threadIdx.x; idx < C::LPB * N2; idx += blockDim.x) {
-    const int l = idx / N2, n = idx & (N2 - 1);
-    const long long v = (long long)(line0 + l) * N2 + n;
-    const bool solid = Hp[v] != 0;
+  const long long hcell = (long long)(p / g.lph) * g.hs;
+  const int ngroups = g.n0 * g.n1 / LPW;
+  const int gbase = (blockIdx.x * XS_WARPS + warp) * XS_GPW;
+#pragma unroll 1
+  for (int gi = 0; gi < XS_GPW; ++gi) {
+    const int grp = gbase + gi;
+    if (grp >= ngroups) break;
+    const long long line = (long long)grp * LPW + ll;
+    const long long v0 = line * N2;
+    if (lane == 0 && gi + 1 < XS_GPW && grp + 1 < ngroups) {
+      // the next group's rows of u^n and H lambda^n on their way to L2
+      const long long w1 = (long long)(grp + 1) * LPW * N2;
+      constexpr unsigned RB = LPW * N2 * sizeof(T);
 #pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        prefetch_l2(up + c * g.V + w1, RB);
+        prefetch_l2(lp + c * g.V + w1, RB);
+      }
+    }
+    const unsigned hm = xl_hmask<N2, TL, E>(Hb + hcell / 32, H + hcell, line, t);
+    cx<T> v[E];
+#pragma unroll 1
     for (int c = 0; c < 3; ++c) {
-      const T uu = up[c * g.V + v];
-      const T w = solid ? b * (s_prev * uu) - lp[c * g.V + v] : b * uu;
-      re_at(sm + (c * C::LPB + l) * C::LS, n) = w;
+      // Eq. 7 right-hand side w = b u~ - a with a = H lambda (the Green step adds g and -i d q)
+      const T* uc = up + c * g.V + v0;
+      const T* lc = lp + c * g.V + v0;
+#pragma unroll
+      for (int m0 = 0; m0 < E; m0 += CH) {
+        T2 uu[CH], l0[CH];
+#pragma unroll
+        for (int jj = 0; jj < CH; ++jj) {
+          const int k = t + TL * (m0 + jj);
+          uu[jj] = *reinterpret_cast<const T2*>(uc + 2 * k);
+          if ((hm >> (2 * (m0 + jj))) & 3u) {
+            l0[jj] = *reinterpret_cast<const T2*>(lc + 2 * k);
+          } else {
+            l0[jj].x = (T)0;
+            l0[jj].y = (T)0;
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < CH; ++jj) {
+          const int m = m0 + jj;
+          const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
+          v[m] = mk<T>(sa ? b * (s_prev * uu[jj].x) - l0[jj].x : b * uu[jj].x,
+                       sb ? b * (s_prev * uu[jj].y) - l0[jj].y : b * uu[jj].y);
+        }
+      }
+      cx<T> xn;
+      xl_forward<T, N2>(bl, tw, t, mask, v, v, xn);
+      cx<T>* dst = sp + c * g.S + line * g.P;
+#pragma unroll
+      for (int m = 0; m < E; ++m) dst[t + TL * m] = v[m];
+      if (t == 0) dst[M] = xn;
     }
   }
-  __syncthreads();
-  x_fft<T, N2, 3, -1>(sm, tw);
-  __syncthreads();
-  x_post_store_spec<T, N2, 3>(sm, sp, g.S, g.P, line0, tw);
 }
 
 // ---------------------------------------------------------------------------

@@ -27,7 +27,8 @@ struct Ops {
                                     const uint8_t* H, const uint32_t* Hb, StokesDev* prm, double* part,
                                     const void* tw, cudaStream_t s);
   static cudaError_t x_stokes_rhs(const Geo& g, int nprob, void* spec, const void* u, const void* lam,
-                                  const uint8_t* H, const StokesDev* prm, const void* tw, cudaStream_t s);
+                                  const uint8_t* H, const uint32_t* Hb, const StokesDev* prm, const void* tw,
+                                  cudaStream_t s);
   static cudaError_t x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
                               const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym,
                               cudaStream_t s);

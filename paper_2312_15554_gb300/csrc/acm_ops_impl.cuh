@@ -48,13 +48,13 @@ static cudaError_t l_x_local(const Geo& g, int nprob, const void* spec, void* u,
 
 template <typename T, int N2>
 static cudaError_t l_x_rhs(const Geo& g, int nprob, void* spec, const void* u, const void* lam, const uint8_t* H,
-                           const StokesDev* prm, const void* tw, cudaStream_t s) {
-  constexpr int smem = x_smem_bytes<T, N2, 3>();
+                           const uint32_t* Hb, const StokesDev* prm, const void* tw, cudaStream_t s) {
+  constexpr int smem = xs_smem_bytes<T, N2, 1, 0>();
   static const cudaError_t attr = set_smem(k_x_stokes_rhs<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
-  dim3 grid(g.n0 * g.n1 / XCfg<T, N2>::LPB, nprob);
-  k_x_stokes_rhs<T, N2><<<grid, 3 * 64, smem, s>>>((cx<T>*)spec, (const T*)u, (const T*)lam, H, prm, g,
-                                                   (const cx<T>*)tw);
+  dim3 grid(xs_blocks(g.n0 * g.n1, XL<T, N2>::LPW), nprob);
+  k_x_stokes_rhs<T, N2><<<grid, XS_WARPS * 32, smem, s>>>((cx<T>*)spec, (const T*)u, (const T*)lam, H, Hb, prm, g,
+                                                          (const cx<T>*)tw);
   return cudaGetLastError();
 }
 
@@ -287,8 +287,9 @@ cudaError_t Ops<T>::x_stokes_local(const Geo& g, int nprob, const void* spec, vo
 
 template <typename T>
 cudaError_t Ops<T>::x_stokes_rhs(const Geo& g, int nprob, void* spec, const void* u, const void* lam,
-                                 const uint8_t* H, const StokesDev* prm, const void* tw, cudaStream_t s) {
-  ACM_DISPATCH_N(g.n2, l_x_rhs, g, nprob, spec, u, lam, H, prm, tw, s)
+                                 const uint8_t* H, const uint32_t* Hb, const StokesDev* prm, const void* tw,
+                                 cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_rhs, g, nprob, spec, u, lam, H, Hb, prm, tw, s)
 }
 
 template <typename T>
