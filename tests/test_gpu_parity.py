@@ -72,10 +72,16 @@ def test_fft_r2c_c2r_matches_oracle_transform(lib, shape, fp64):
 # ---------------------------------------------------------------------------
 # Stokes ADMM: fixed-iteration parity
 # ---------------------------------------------------------------------------
+# the x passes are specialised per line length n2: 8 (one lane, 4 elements),
+# 16 and 32 (one lane), 64 (four lanes), 512 (sixteen lanes) are covered here,
+# 128 and 256 by the bench-workload test below
 CASES = [
     ("sphere16", lambda: I.single_sphere((16, 16, 16), 0.3)),
     ("rand8x16x32", lambda: I.random_indicator((8, 16, 32), 0.35, 4)),
     ("pack32", lambda: I.sphere_pack((32, 32, 32), 0.45, 4.0, 11)[0]),
+    ("rand16x16x8", lambda: I.random_indicator((16, 16, 8), 0.3, 5)),
+    ("pack16x8x64", lambda: I.sphere_pack((16, 8, 64), 0.5, 3.0, 12)[0]),
+    ("rand8x16x512", lambda: I.random_indicator((8, 16, 512), 0.35, 6)),
 ]
 
 
@@ -198,8 +204,8 @@ def test_stokes_tensor_and_gradient_form_match_oracle(lib):
 @pytest.mark.parametrize("deriv", [O.CENTRAL, O.EXACT])
 @pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("explicit_B0", [False, True])
-def test_solute_fixed_iterations_match_oracle(lib, deriv, fp64, explicit_B0):
-    shape = (16, 8, 32)
+@pytest.mark.parametrize("shape", [(16, 8, 32), (8, 8, 8), (8, 8, 64), (8, 8, 512)])
+def test_solute_fixed_iterations_match_oracle(lib, deriv, fp64, explicit_B0, shape):
     H = I.random_indicator(shape, 0.4, 8)
     u = 0.3 * I.random_field((3,) + shape, 9) * (1 - H)[None]
     Pe, gchi = 7.0, [0.3, 1.0, -0.2]
