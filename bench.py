@@ -387,6 +387,47 @@ def run_batched(args, rank, world, dist):
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
     ms = e0.elapsed_time(e1)
+    ttk = None
+    if args.ttk_batched > 0 and world == 1:
+        # time to permeability of the batched form: every problem's K after every
+        # iteration (batch history), crossing iterations per cell against the
+        # cell's own last tensor, times the batch's time per iteration
+        n_it = args.ttk_batched
+        acm.acm_batch_history_enable(batch, n_it)
+        pl = acm.stokes_params(eps=0.0, max_iter=n_it, precision=acm.FP32)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        acm.acm_batch_stokes(batch, Hd, pl)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        per_iter = f0.elapsed_time(f1) / 1e3 / n_it
+        crossing = {r: [] for r in (1e-1, 3e-2, 1e-2)}
+        tails = []
+        for cell in range(len(shapes)):
+            hs = [acm.acm_batch_history(batch, cell, j) for j in range(3)]
+            m = min(len(h) for h in hs)
+            Kn = np.stack([hs[j][:m, 15:18] for j in range(3)], axis=-1)
+            Kr = Kn[-1]
+            err = np.linalg.norm(Kn - Kr, axis=(1, 2)) / np.linalg.norm(Kr)
+            tail = float(np.linalg.norm(Kn[-1] - Kn[max(0, m - 1 - m // 10)]) / np.linalg.norm(Kr))
+            tails.append(tail)
+            for rel in crossing:
+                bad = np.nonzero(err > rel)[0]
+                ok = rel > tail and (len(bad) == 0 or bad[-1] + 1 < m)
+                crossing[rel].append((int(bad[-1]) + 2 if len(bad) else 1) if ok else None)
+        acm.acm_batch_history_enable(batch, 0)
+        ttk = {"iterations": n_it, "seconds_per_batch_iteration": per_iter,
+               "reference": "each cell's tensor after the last iteration",
+               "reference_last10pct_change_median": float(np.median(tails)), "thresholds": {}}
+        for rel, xs in crossing.items():
+            got = [x for x in xs if x is not None]
+            ttk["thresholds"][f"{rel:g}"] = {
+                "cells_resolved": len(got), "cells": len(xs),
+                "iterations_median": float(np.median(got)) if got else None,
+                "iterations_max": int(max(got)) if got else None,
+                "seconds_all_resolved_cells": (max(got) * per_iter) if got else None}
     # per-kernel shares of one more step, host-launched with CUDA events
     acm.acm_batch_profile_read(batch)
     acm.acm_batch_profile_enable(batch, True)
@@ -410,6 +451,8 @@ def run_batched(args, rank, world, dist):
         "K_mean_diag_cell0": [float(K_all[0, i, i]) for i in range(3)],
         "cells_all_ranks": int(K_all.shape[0]),
     }
+    if ttk is not None:
+        line["time_to_permeability"] = ttk
     print(json.dumps(line), flush=True)
 
 
@@ -548,6 +591,8 @@ def main():
     ap.add_argument("--c5-max-iter", type=int, default=20000)
     ap.add_argument("--c5-nu", type=float, default=1.0, help="grf512: viscosity of the accuracy runs")
     ap.add_argument("--cells", type=int, default=384, help="cells of the batched configuration")
+    ap.add_argument("--ttk-batched", type=int, default=0,
+                    help="batched: also follow K of every cell for this many iterations (time to permeability)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
