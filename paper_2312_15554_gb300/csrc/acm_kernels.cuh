@@ -274,32 +274,29 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
     __syncwarp(mask);
     T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
     cx<T> v[E];
+    static_assert(E % CH == 0 && E / CH <= 2, "two chunks per component");
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
       cx<T>* bc = c == 1 ? b1 : b0;
-      xl_inverse<T, N2>(bc, tw, t, mask, v, nullptr);
-      if (c == 0) {
-        // the row of component 2 into b0, behind components 0 and 1
-        __syncwarp(mask);
-        for (int e = t; e <= M; e += TL) cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[2 * g.S + e]);
-        cp_async_commit();
-      }
       T* uc = up + c * g.V + v0;
       T* lc = lp + c * g.V + v0;
-#pragma unroll
-      for (int m0 = 0; m0 < E; m0 += CH) {
-        T2 u0[CH], l0[CH];
+      // old state of the component: the first chunk travels during the inverse
+      // transform, the second during the first chunk's arithmetic
+      T2 ua[CH], la[CH], ub[CH], lb[CH];
+      auto load_chunk = [&](int m0, T2 (&uu)[CH], T2 (&ll)[CH]) {
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
           const int k = t + TL * (m0 + j);
-          u0[j] = *reinterpret_cast<const T2*>(uc + 2 * k);
+          uu[j] = *reinterpret_cast<const T2*>(uc + 2 * k);
           if ((hm >> (2 * (m0 + j))) & 3u) {
-            l0[j] = *reinterpret_cast<const T2*>(lc + 2 * k);
+            ll[j] = *reinterpret_cast<const T2*>(lc + 2 * k);
           } else {
-            l0[j].x = (T)0;
-            l0[j].y = (T)0;
+            ll[j].x = (T)0;
+            ll[j].y = (T)0;
           }
         }
+      };
+      auto step_chunk = [&](int m0, const T2 (&u0)[CH], const T2 (&l0)[CH]) {
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
           const int m = m0 + j, k = t + TL * m;
@@ -334,7 +331,18 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
             *reinterpret_cast<T2*>(lc + 2 * k) = ln;   // lambda stays 0 on pore voxels
           }
         }
+      };
+      load_chunk(0, ua, la);
+      xl_inverse<T, N2>(bc, tw, t, mask, v, nullptr);
+      if (c == 0) {
+        // the row of component 2 into b0, behind components 0 and 1
+        __syncwarp(mask);
+        for (int e = t; e <= M; e += TL) cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[2 * g.S + e]);
+        cp_async_commit();
       }
+      if constexpr (E / CH == 2) load_chunk(CH, ub, lb);
+      step_chunk(0, ua, la);
+      if constexpr (E / CH == 2) step_chunk(CH, ub, lb);
       if (c == 1) {
         cp_async_wait<0>();
         __syncwarp(mask);
