@@ -795,7 +795,16 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
     }
     // The operator state (q^ and div^, or chi^) is read and rewritten in place:
     // each chunk loads its state before any store (see k_x_stokes_local).
+    // The block size is a multiple of TX, so a thread keeps one tile column and
+    // its kx symbols and Parseval weight stay in registers.
+    static_assert(C::NT % TX == 0, "one column per thread");
     constexpr int TOT = N * TX, CH = 4;
+    const int col = threadIdx.x % TX, kx = kx0 + col;
+    const bool colok = col < w;
+    const T d2 = colok ? a.sym.d2[kx] : (T)0, l2 = colok ? a.sym.l2[kx] : (T)0;
+    const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
+    const T l12 = l1 + l2, d12 = d1 * d1 + d2 * d2;
+    const long long gcol = (long long)p * a.compStride + (long long)outer * a.outerStride + kx0 + col;
 #pragma unroll 1
     for (int base = 0; base < TOT; base += CH * C::NT) {
       bool ok[CH];
@@ -804,9 +813,9 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
 #pragma unroll
       for (int k = 0; k < CH; ++k) {
         const int idx = base + k * C::NT + threadIdx.x;
-        const int col = idx % TX, j = idx / TX;
-        ok[k] = idx < TOT && col < w;
-        gis[k] = (long long)p * a.compStride + (long long)j * a.rowStride + (long long)outer * a.outerStride + kx0 + col;
+        const int j = idx / TX;
+        ok[k] = idx < TOT && colok;
+        gis[k] = gcol + (long long)j * a.rowStride;
         sa[k] = ok[k] ? a.st0[gis[k]] : mk<T>(0, 0);
         if constexpr (OP == OP_STOKES) sb[k] = ok[k] ? a.st1[gis[k]] : mk<T>(0, 0);
       }
@@ -814,11 +823,10 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
       for (int k = 0; k < CH; ++k) {
         if (!ok[k]) continue;
         const int idx = base + k * C::NT + threadIdx.x;
-        const int col = idx % TX, j = idx / TX, kx = kx0 + col;
+        const int j = idx / TX;
         const long long gi = gis[k];
-        const T d0 = a.sym.d0[j], l0 = a.sym.l0[j], d2 = a.sym.d2[kx], l2 = a.sym.l2[kx];
-        const T L = l0 + l1 + l2, dd = d0 * d0 + d1 * d1 + d2 * d2;
-        const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
+        const T d0 = a.sym.d0[j], l0 = a.sym.l0[j];
+        const T L = l0 + l12, dd = d0 * d0 + d12;
         const bool k0 = (j == 0 && ky == 0 && kx == 0);
         cx<T>* s0 = &sm[(0 * TX + col) * C::LS + pad(j)];
         cx<T>* s1 = &sm[(1 * TX + col) * C::LS + pad(j)];
