@@ -189,5 +189,24 @@ def random_field(shape, seed: int, scale: float = 1.0) -> np.ndarray:
     return scale * rng.standard_normal(tuple(shape))
 
 
+def dissolve(H: np.ndarray, layers: int = 1, fraction: float = 1.0, seed: int = 0) -> np.ndarray:
+    """Dissolve solid at the pore interface, `layers` times: a solid voxel with a
+    pore voxel among its six periodic face neighbours becomes pore, each with
+    probability `fraction` (numpy PCG64, seeded); fraction 1 removes whole
+    layers. The geometry sequence of an evolving medium."""
+    H = np.asarray(H, dtype=np.uint8).copy()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for _ in range(layers):
+        pore = H == 0
+        touch = np.zeros_like(pore)
+        for ax in range(3):
+            touch |= np.roll(pore, 1, axis=ax) | np.roll(pore, -1, axis=ax)
+        front = (H == 1) & touch
+        if fraction < 1.0:
+            front &= rng.random(H.shape) < fraction
+        H[front] = 0
+    return H
+
+
 def porosity(H: np.ndarray) -> float:
     return 1.0 - float(np.count_nonzero(H)) / H.size
