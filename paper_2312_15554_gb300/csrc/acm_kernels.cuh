@@ -397,16 +397,6 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
     if (grp >= ngroups) break;
     const long long line = (long long)grp * LPW + ll;
     const long long v0 = line * N2;
-    if (lane == 0 && gi + 1 < XS_GPW && grp + 1 < ngroups) {
-      // the next group's rows of u^n and H lambda^n on their way to L2
-      const long long w1 = (long long)(grp + 1) * LPW * N2;
-      constexpr unsigned RB = LPW * N2 * sizeof(T);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        prefetch_l2(up + c * g.V + w1, RB);
-        prefetch_l2(lp + c * g.V + w1, RB);
-      }
-    }
     const unsigned hm = xl_hmask<N2, TL, E>(Hb + hcell / 32, H + hcell, line, t);
     cx<T> v[E];
 #pragma unroll 1
