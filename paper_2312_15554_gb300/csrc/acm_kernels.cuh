@@ -501,21 +501,6 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
         cp_async<(int)sizeof(cx<T>)>(&b1[pad(e)], &srow[g.S + e]);
       }
       cp_async_commit();
-      if (lane == 0) {
-        // the group's velocity rows (once for problems that share them) and the
-        // next group's spectrum rows, on their way to L2
-        const long long w0 = (long long)grp * LPW * N2;
-        constexpr unsigned RB = LPW * N2 * sizeof(T);
-        if (p == pbeg || !shared) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) prefetch_l2(up + c * g.V + w0, RB);
-        }
-        if (gi + 1 < gpw && grp + 1 < ngroups) {
-          const unsigned SB = (unsigned)(LPW * g.P * sizeof(cx<T>));
-#pragma unroll
-          for (int c = 0; c < 3; ++c) prefetch_l2(sp + c * g.S + (long long)(grp + 1) * LPW * g.P, SB);
-        }
-      }
 #pragma unroll
       for (int m = 0; m < 2 * E; ++m) acc[m * 32 + lane] = (T)0;
       cp_async_wait<0>();
