@@ -64,9 +64,10 @@ def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float) -> float:
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel at the default workload (256^3, porosity 0.35, 3 problems per launch),
-# from the ncu capture summarised in profiles/x_passes_and_z_pass_256_full.md.
-# An entry holds only while the kernel is unchanged since that capture.
-MEASURED_TRAFFIC = {"x_solute": 858.760704e6 + 566.645248e6}
+# from the ncu capture summarised in profiles/dram_traffic_256.md (mean of four
+# launches). An entry holds only while the kernel is unchanged since that capture.
+MEASURED_TRAFFIC = {"x_solute": 834.515e6 + 563.697e6, "x_stokes_local": 2407.267e6 + 1127.518e6,
+                    "x_stokes_rhs": 1223.515e6 + 588.359e6}
 
 
 def measured_peaks():
@@ -320,8 +321,8 @@ def run_gpu(args, rank, world, dist):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": MEASURED_TRAFFIC.get(dom) if (N == 256 and abs(POROSITY - 0.35) < 1e-9) else None,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, "
-                                       "profiles/x_passes_and_z_pass_256_full.md" if dom in MEASURED_TRAFFIC else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                                       "profiles/dram_traffic_256.md" if dom in MEASURED_TRAFFIC else None,
                      "peak_source": peak_src, "bytes_per_launch": bytes_per_launch},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * V),

@@ -254,15 +254,13 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
     }
     cp_async_commit();
     if (lane == 0) {
-      // the group's rows of u^n and H lambda^n (consecutive lines are contiguous),
-      // and the next group's spectrum rows, on their way to L2
+      // the group's rows of u^n (consecutive lines are contiguous) and the next
+      // group's spectrum rows, on their way to L2; H lambda^n is needed on solid
+      // voxels only and is left to the predicated loads
       const long long w0 = (long long)grp * LPW * N2;
       constexpr unsigned RB = LPW * N2 * sizeof(T);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        prefetch_l2(up + c * g.V + w0, RB);
-        prefetch_l2(lp + c * g.V + w0, RB);
-      }
+      for (int c = 0; c < 3; ++c) prefetch_l2(up + c * g.V + w0, RB);
       if (gi + 1 < XS_GPW && grp + 1 < ngroups) {
         const unsigned SB = (unsigned)(LPW * g.P * sizeof(cx<T>));
 #pragma unroll
