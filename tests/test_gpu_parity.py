@@ -346,3 +346,45 @@ def test_mixed_precision_reports_split_iterations_per_load(lib):
     for r in dreps:
         assert r.converged and 0 < r.iters_fp64 < r.iters
     ctx.close()
+
+
+def test_fp32_error_of_every_result_against_the_fp64_oracle(lib, capsys):
+    """The FP32 path (FP32 transforms and local steps, FP64 reductions) against
+    the FP64 oracle on the same iterations, one number per result: fields within
+    1e-5 of their largest magnitude, the permeability and the diffusivity within
+    1e-6 (the volume averages are accumulated in FP64)."""
+    shape = (32, 32, 32)
+    H = I.sphere_pack(shape, 0.45, 4.0, 21)[0]
+    pen = dict(alpha0=250.0, beta0=180.0, b0=300.0)
+    n_st, n_so = 60, 30
+    P = O.StokesParams(eps=0.0, adaptive=False, max_iter=n_st, **pen)
+    Km, Kg, res = O.permeability_tensor(H, P)
+    ctx = lib.acm_ctx(shape)
+    Hd = dev(H, torch.uint8)
+    u3 = torch.zeros((3, 3) + shape, dtype=torch.float32, device=DEV)
+    s, K, Kgg, reps = lib.acm_stokes_tensor(ctx, Hd, lib.stokes_params(eps=0.0, adaptive=0, max_iter=n_st,
+                                                                       precision=lib.FP32, **pen), u3, grad_form=True)
+    u_ref = np.stack([r.state.u for r in res])
+    g = [1.0, 0.0, 0.0]
+    s1, Kc, rep, u1, p1, l1 = run_stokes(lib, H, g, False, eps=0.0, adaptive=0, max_iter=n_st, **pen)
+    errs = {"u": relerr(u3.cpu().numpy(), u_ref), "p": relerr(p1, res[0].p), "lambda": relerr(l1, res[0].state.lam),
+            "K (mean form)": relerr(K, Km), "K (Eq. 2 gradient form)": relerr(Kgg, Kg)}
+    # solute on the converged-direction flow of load e_0 (unit-cell units)
+    u0 = res[0].state.u
+    Pe = 10.0
+    AP = O.AdvDiffParams(eps=0.0, max_iter=n_so)
+    Dm, Dx, sres = O.diffusivity_tensor(H, u0, Pe, AP)
+    chi3 = torch.zeros((3,) + shape, dtype=torch.float32, device=DEV)
+    s2, D, DxG, dreps = lib.acm_advdiff_tensor(ctx, Hd, dev(u0, torch.float32), Pe,
+                                                lib.advdiff_params(eps=0.0, max_iter=n_so, precision=lib.FP32), chi3)
+    chi_ref = np.stack([r.chi for r in sres])
+    errs.update({"chi": relerr(chi3.cpu().numpy(), chi_ref), "D (Eq. 3)": relerr(D, Dm),
+                 "D (extended domain)": relerr(DxG, Dx)})
+    ctx.close()
+    with capsys.disabled():
+        print("\nFP32 error against the FP64 oracle, 32^3 pack: " +
+              ", ".join(f"{k} {v:.1e}" for k, v in errs.items()))
+    for k in ("u", "p", "lambda", "chi"):
+        assert errs[k] < 1e-5, (k, errs[k])
+    for k in ("K (mean form)", "K (Eq. 2 gradient form)", "D (Eq. 3)", "D (extended domain)"):
+        assert errs[k] < 1e-6, (k, errs[k])
