@@ -388,3 +388,27 @@ def test_fp32_error_of_every_result_against_the_fp64_oracle(lib, capsys):
         assert errs[k] < 1e-5, (k, errs[k])
     for k in ("K (mean form)", "K (Eq. 2 gradient form)", "D (Eq. 3)", "D (extended domain)"):
         assert errs[k] < 1e-6, (k, errs[k])
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_shear_flow_dispersion_matches_the_closed_form(lib, fp64):
+    """No solid, u = (0, U sin 2 pi x0, 0): D_11 = 1 + Pe^2 U^2 / (8 pi^2) and
+    chi = -Pe U sin(2 pi x0) / (2 pi)^2 with the exact symbols (the FP64 oracle
+    pins the same closed form)."""
+    shape = (16, 8, 8)
+    x0 = (np.arange(shape[0]) + 0.5) / shape[0]
+    U, Pe = 1.0, 3.0
+    H = np.zeros(shape, dtype=np.uint8)
+    u = np.zeros((3,) + shape)
+    u[1] = U * np.sin(2 * np.pi * x0)[:, None, None]
+    dt = torch.float64 if fp64 else torch.float32
+    ctx = lib.acm_ctx(shape)
+    chi = torch.zeros(shape, dtype=dt, device=DEV)
+    prm = lib.advdiff_params(eps=1e-12 if fp64 else 1e-7, max_iter=20000, deriv=O.EXACT,
+                             precision=lib.FP64 if fp64 else lib.FP32)
+    s, Dg, Dx, rep = lib.acm_advdiff(ctx, dev(H, torch.uint8), dev(u, dt), Pe, [0.0, 1.0, 0.0], prm, chi)
+    ctx.close()
+    assert rep.converged
+    ref = -Pe * U * np.sin(2 * np.pi * x0)[:, None, None] / (2 * np.pi) ** 2 * np.ones(shape)
+    assert relerr(chi.cpu().numpy(), ref) < (1e-10 if fp64 else 1e-5)
+    assert Dg[1] == pytest.approx(1 + Pe ** 2 * U ** 2 / (8 * np.pi ** 2), rel=1e-10 if fp64 else 1e-6)

@@ -429,3 +429,24 @@ def test_taylor_dispersion_in_plane_poiseuille_flow():
         assert abs(R.Dg[1]) < 1e-10 and abs(R.Dg[2]) < 1e-10
     assert errs[2] < errs[1] < errs[0]
     assert errs[2] < 2e-3
+
+
+def test_shear_flow_manufactured_solution_and_dispersion_closed_form():
+    """No solid, shear flow u = (0, U sin 2 pi x0, 0) (divergence free, zero
+    pore mean), composition gradient e_1. The fixed point of Eq. 17 (with A = 1,
+    B = Pe u, F = 0) reduces to chi'' = Pe U sin 2 pi x0, so
+    chi = -Pe U sin(2 pi x0) / (2 pi)^2 (a single Fourier mode: exact with the
+    exact symbols), and Eq. 3 gives D_11 = 1 + Pe^2 U^2 / (8 pi^2), D_01 = 0."""
+    shape = (16, 8, 8)
+    n0 = shape[0]
+    x0 = (np.arange(n0) + 0.5) / n0
+    U, Pe = 1.0, 3.0
+    H = np.zeros(shape, dtype=np.uint8)
+    u = np.zeros((3,) + shape)
+    u[1] = U * np.sin(2 * np.pi * x0)[:, None, None]
+    R = O.advdiff(H, u, Pe, [0.0, 1.0, 0.0], O.AdvDiffParams(eps=1e-13, max_iter=20000, deriv=O.EXACT))
+    assert R.converged
+    chi = -Pe * U * np.sin(2 * np.pi * x0)[:, None, None] / (2 * np.pi) ** 2 * np.ones(shape)
+    np.testing.assert_allclose(R.chi, chi, atol=1e-10 * np.abs(chi).max())
+    assert R.Dg[1] == pytest.approx(1 + Pe ** 2 * U ** 2 / (8 * np.pi ** 2), rel=1e-10)
+    assert abs(R.Dg[0]) < 1e-10 and abs(R.Dg[2]) < 1e-10
