@@ -607,6 +607,11 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         tdist.init_process_group("nccl")
         dist = tdist
+        # one rank (re)builds the library if needed; the others wait for it
+        if int(os.environ.get("LOCAL_RANK", "0")) == 0:
+            from paper_2312_15554_gb300 import build as B
+            B.build()
+        dist.barrier()
     if args.config == "batched":
         run_batched(args, rank, world, dist)
     elif args.config == "grf512":
