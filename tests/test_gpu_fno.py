@@ -32,7 +32,8 @@ def _case(shape, width, modes, layers, B, seed):
 
 
 @pytest.mark.parametrize("shape,width,modes,layers,B", [((16, 16, 16), 8, 3, 2, 2), ((8, 16, 32), 4, 2, 3, 3),
-                                                       ((32, 32, 32), 32, 4, 2, 1)])
+                                                       ((32, 32, 32), 32, 4, 2, 1),
+                                                       ((64, 64, 64), 32, 12, 4, 1)])  # the trained size
 def test_fno_forward_loss_and_gradient_match_oracle(lib, shape, width, modes, layers, B):
     theta, Hs, tgt = _case(shape, width, modes, layers, B, 7)
     fno = lib.acm_fno(shape, width, modes, layers, max_batch=4)
