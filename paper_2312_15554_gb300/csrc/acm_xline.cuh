@@ -165,10 +165,11 @@ __device__ __forceinline__ void xl_forward(cx<T>* sl, const cx<T>* tw, int t, un
     for (int m = 0; m < E; ++m) sl[pad(t + TL * m)] = v[m];
   }
   __syncwarp(mask);
+  // Z_k is the lane's own value (still in v); only Z_{M-k} comes from another lane
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int k = t + TL * m;
-    const cx<T> Zk = sl[pad(k)];
+    const cx<T> Zk = v[m];
     if (k == 0) {
       X[m] = mk<T>(Zk.x + Zk.y, (T)0);
       xn = mk<T>(Zk.x - Zk.y, (T)0);
