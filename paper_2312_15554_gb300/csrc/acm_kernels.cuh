@@ -59,13 +59,6 @@ __device__ __forceinline__ void load_tw_x(cx<T>* tw, const cx<T>* __restrict__ t
   for (int k = threadIdx.x; k <= N2 / 2; k += blockDim.x) post[k] = twg[k * (TW_MAX / N2)];
 }
 
-// contiguous real segment of n values (n * sizeof(T) a multiple of 16) into shared memory
-template <typename T>
-__device__ __forceinline__ void stage_real(T* dst, const T* __restrict__ src, int n) {
-  constexpr int V = 16 / (int)sizeof(T);
-  for (int i = threadIdx.x; i < n / V; i += blockDim.x) cp_async<16>(dst + i * V, src + i * V);
-}
-
 // Real transforms of length N2 run as complex transforms of length M = N2/2 on
 // z_j = x_{2j} + i x_{2j+1}, with W = exp(-2 pi i / N2):
 //   inverse: from the half spectrum X[0..M],
@@ -90,42 +83,6 @@ __device__ __forceinline__ void x_load_spec_pre(cx<T>* sm, const cx<T>* __restri
     cx<T>* s = sm + cl * C::LS;
     for (int k = lane; k <= M / 2; k += 32) {
       const cx<T> X = src[k], Y = src[M - k];
-      const cx<T> e1 = X + cconj(Y), o1 = cmul(X - cconj(Y), cconj(tw[k]));
-      const cx<T> e2 = Y + cconj(X), o2 = cmul(Y - cconj(X), cconj(tw[M - k]));
-      s[pad(k)] = e1 + mul_i(o1);
-      if (k != 0) s[pad(M - k)] = e2 + mul_i(o2);
-    }
-  }
-}
-
-// x_load_spec_raw_async: rows of NC half-spectrum components copied as they are
-// (cp.async) into the lines, X[M] into nyq[component line]; x_pre_smem then
-// turns them into Z[0..M-1] in place.
-template <typename T, int N2, int NC>
-__device__ __forceinline__ void x_load_spec_raw_async(cx<T>* sm, cx<T>* nyq, const cx<T>* __restrict__ spec,
-                                                      long long S, int P, int line0) {
-  using C = XCfg<T, N2>;
-  constexpr int M = C::M;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
-    const int c = cl / C::LPB, l = cl - c * C::LPB;
-    const cx<T>* src = spec + c * S + (long long)(line0 + l) * P;
-    cx<T>* dst = sm + cl * C::LS;
-    for (int k = lane; k < M; k += 32) cp_async<(int)sizeof(cx<T>)>(&dst[pad(k)], &src[k]);
-    if (lane == 0) cp_async<(int)sizeof(cx<T>)>(&nyq[cl], &src[M]);
-  }
-}
-
-template <typename T, int N2, int NC>
-__device__ __forceinline__ void x_pre_smem(cx<T>* sm, const cx<T>* nyq, const cx<T>* twx) {
-  using C = XCfg<T, N2>;
-  constexpr int M = C::M;
-  const cx<T>* tw = twx + tw_total(M);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int cl = warp; cl < NC * C::LPB; cl += nw) {
-    cx<T>* s = sm + cl * C::LS;
-    for (int k = lane; k <= M / 2; k += 32) {
-      const cx<T> X = s[pad(k)], Y = (k == 0) ? nyq[cl] : s[pad(M - k)];
       const cx<T> e1 = X + cconj(Y), o1 = cmul(X - cconj(Y), cconj(tw[k]));
       const cx<T> e2 = Y + cconj(X), o2 = cmul(Y - cconj(X), cconj(tw[M - k]));
       s[pad(k)] = e1 + mul_i(o1);
