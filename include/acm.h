@@ -106,7 +106,8 @@ typedef struct acm_advdiff_params {
   double eps;          /* tolerance of Eq. 19 (default 1e-5) */
   int max_iter;        /* iteration cap (default 20000) */
   int deriv;           /* acm_deriv (default ACM_DERIV_CENTRAL) */
-  int precision;       /* acm_precision (default ACM_FP32) */
+  int precision;       /* acm_precision (default ACM_FP32); with ACM_FP32_THEN_FP64 the
+                          FP32 iterations run to max(eps, 1e-5), then FP64 ones to eps */
   int check_every;     /* iterations between host checks of the stop flag (default 16) */
 } acm_advdiff_params;
 
@@ -175,7 +176,9 @@ acm_status acm_stokes_tensor(acm_ctx* ctx, const uint8_t* H, const acm_stokes_pa
  *             (D g)_i = (1/V) sum_pore [g_i + Pe (ubar - u)_i chi + d_i chi].
  *   Dg_ext    out (host, 3 doubles, nullable): extended-domain average
  *             (1/V) sum_Y A (g + grad chi)_i + the same Pe term.
- * The real type of u, chi and grad_chi follows prm->precision. */
+ * The real type of u, chi and grad_chi follows prm->precision (double for the
+ * mixed mode). A device u aligned to 16 bytes is read in place; any other u
+ * is first copied into the context's workspace. */
 acm_status acm_advdiff(acm_ctx* ctx, const uint8_t* H, const void* u, double Pe,
                        const double g_chi[3], const acm_advdiff_params* prm,
                        void* chi, void* grad_chi, double Dg[3], double Dg_ext[3],
