@@ -30,8 +30,9 @@
  *           host<->device transfers. Scalars and reports are host memory.
  * Ownership the library never frees or retains caller memory. A context owns
  *           its workspace (allocated on first use of a precision, freed by
- *           acm_destroy). Calls on one context are not thread safe; distinct
- *           contexts are independent.
+ *           acm_destroy); an acm_batch and an acm_fno own theirs likewise
+ *           (freed by acm_batch_destroy / acm_fno_destroy). Calls on one object
+ *           are not thread safe; distinct objects are independent.
  * Streams   all device work of a context is ordered on the stream given at
  *           acm_create (NULL = legacy default stream). Every solver entry point
  *           returns after its results are complete on the host side (K, D,
