@@ -66,8 +66,8 @@ def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float) -> float:
 # kernel at the default workload (256^3, porosity 0.35, 3 problems per launch),
 # from the ncu capture summarised in profiles/dram_traffic_256.md (mean of four
 # launches). An entry holds only while the kernel is unchanged since that capture.
-MEASURED_TRAFFIC = {"x_solute": 834.515e6 + 563.697e6, "x_stokes_local": 2407.267e6 + 1127.518e6,
-                    "x_stokes_rhs": 1223.515e6 + 588.359e6}
+MEASURED_TRAFFIC = {"x_solute": 835.536e6 + 563.574e6, "x_stokes_local": 2399.122e6 + 1126.956e6,
+                    "x_stokes_rhs": 1223.510e6 + 587.490e6}
 
 
 def measured_peaks():
