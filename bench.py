@@ -66,8 +66,8 @@ def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float) -> float:
 # kernel at the default workload (256^3, porosity 0.35, 3 problems per launch),
 # from the ncu capture summarised in profiles/dram_traffic_256.md (mean of four
 # launches). An entry holds only while the kernel is unchanged since that capture.
-MEASURED_TRAFFIC = {"x_solute": 835.536e6 + 563.574e6, "x_stokes_local": 2399.122e6 + 1126.956e6,
-                    "x_stokes_rhs": 1223.510e6 + 587.490e6}
+MEASURED_TRAFFIC = {"x_solute": 833.302e6 + 563.497e6, "x_stokes_local": 2394.871e6 + 1127.122e6,
+                    "x_stokes_rhs": 1223.463e6 + 587.302e6}
 
 
 def measured_peaks():

@@ -843,7 +843,7 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
     remaining -= chunk;
     for (int k = 0; k < chunk; ++k) {
       // spectral components per problem: x -> (tau_0, tau_1, s + d2 tau_2), y forward -> (tau_0, s''),
-      // z -> (d0 chi, chi), y inverse -> (d0 chi, d1 chi, chi); the x pass takes d2 of the last
+      // z -> (d0 chi, chi), y inverse -> (d0 chi, d1 chi, d2 chi)
       LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym, c->st));
       LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
                       nullptr, c->st));
@@ -874,10 +874,8 @@ acm_status solute_outputs(acm_ctx* c, int nprob, const uint8_t* Hdev, const void
   CKS(ensure_aux<T>(c));
   T* grad = (T*)w.aux;
   T* chi = (T*)w.aux + (size_t)c->B * 3 * g.V;
-  // grad chi^{n+1}: the last passes left i d0 chi^, i d1 chi^ and chi^ (inverse along z
-  // and y) in components 0..2; the axis-2 derivative is taken here
-  const Sym<T> symp = sym_of<T>(c, c->solute_deriv);
-  LK(ACM_K_OTHER, Ops<T>::mul_id2(g, nprob, w.spec, 4 * g.S, symp, c->st));
+  // grad chi^{n+1}: the last passes left i d0 chi^, i d1 chi^ and i d2 chi^ (inverse
+  // along z and y) in components 0..2
   LK(ACM_K_OTHER, Ops<T>::x_c2r(g, nprob, 3, w.spec, 4 * g.S, grad, 3 * g.V, w.tw, c->st));
   // chi^{n+1}
   LK(ACM_K_OTHER, Ops<T>::pass(g, 0, P_INV_SCALE, 1, nprob, w.st0, g.S, sym, w.tw, nullptr, nullptr, nullptr, nullptr, nullptr,

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace acm {
 
 template <typename T>
@@ -101,6 +103,46 @@ __device__ __forceinline__ cx<T> tw16(cx<T> a) {
     const T s = (T)(SIGN * sn[m]);
     return mk<T>(a.x * c - a.y * s, a.x * s + a.y * c);
   }
+}
+
+// multiply by W32^m = exp(SIGN * 2 pi i m / 32) for compile-time m
+template <int SIGN, int M, typename T>
+__device__ __forceinline__ cx<T> tw32(cx<T> a) {
+  constexpr int m = M & 31;
+  if constexpr (m % 2 == 0) {
+    return tw16<SIGN, m / 2>(a);
+  } else {
+    // cos and sin of m * pi / 16 for odd m < 16; m + 16 is the negation
+    constexpr double C1 = 0.98078528040323044913, S1 = 0.19509032201612826785;
+    constexpr double C3 = 0.83146961230254523708, S3 = 0.55557023301960222474;
+    constexpr double cs[8] = {C1, C3, S3, S1, -S1, -S3, -C3, -C1};
+    constexpr double sn[8] = {S1, S3, C3, C1, C1, C3, S3, S1};
+    constexpr double neg = m > 16 ? -1.0 : 1.0;
+    const T c = (T)(neg * cs[(m & 15) / 2]);
+    const T s = (T)(SIGN * neg * sn[(m & 15) / 2]);
+    return mk<T>(a.x * c - a.y * s, a.x * s + a.y * c);
+  }
+}
+
+// multiply by exp(SIGN * 2 pi i m / R) for compile-time m and R in {1, 2, 4, 8, 16, 32}
+template <int SIGN, int M, int R, typename T>
+__device__ __forceinline__ cx<T> root_mul(cx<T> a) {
+  static_assert(R >= 1 && R <= 32 && (R & (R - 1)) == 0, "R must be a power of two up to 32");
+  return tw32<SIGN, M * (32 / R)>(a);
+}
+
+// f(ic<i>{}) for i = 0..N-1: inside f, decltype(arg)::value is the constant expression i
+template <int I>
+struct ic {
+  static constexpr int value = I;
+};
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(ic<I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
 }
 
 // ---------------------------------------------------------------------------

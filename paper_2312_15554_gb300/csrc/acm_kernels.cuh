@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
         }
       };
       load_chunk(0, ua, la);
-      xl_inverse<T, N2>(bc, tw, t, mask, v, nullptr);
+      xl_inverse<T, N2>(bc, tw, t, mask, v);
       if (c == 0) {
         // the row of component 2 into b0, behind components 0 and 1
         __syncwarp(mask);
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
       for (int c = 0; c < 4; ++c) {
         cx<T>* bc = c == 1 ? b1 : b0;
         if (c < 3) {
-          xl_inverse<T, N2>(bc, tw, t, mask, v, c == 2 ? d2 : nullptr);
+          xl_inverse<T, N2>(bc, tw, t, mask, v);
           const T gc = (T)(c == 0 ? P->g[0] : c == 1 ? P->g[1] : P->g[2]);
           const T Bc = (T)(c == 0 ? P->B0[0] : c == 1 ? P->B0[1] : P->B0[2]);
           const T A0 = (T)P->A0, eta = (T)P->eta, Pe = (T)P->Pe;
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(NC * 64) k_x_c2r(const cx<T>* __restrict__ spe
 // OP_FWD_SOL (y forward of the solute iteration): lines (tau_0, tau_1, s') in,
 //   (tau_0, s' + i d1 tau_1) out.
 // OP_SOLUTE (z): (tau_0, s'') in, F^ = s'' + i d0 tau_0, Green step, (i d0 chi^, chi^) out.
-// OP_INV_SOL (y inverse): (a, b) in, lines (a, i d1 b, b) inverse-transformed out.
+// OP_INV_SOL (y inverse): (a, b) in, lines (a, i d1 b, i d2 b) inverse-transformed out.
 enum { OP_FWD = 0, OP_INV = 1, OP_INV_SCALE = 2, OP_STOKES = 3, OP_SOLUTE = 4, OP_DERIV = 5, OP_FWD_SOL = 6,
        OP_INV_SOL = 7 };
 
@@ -662,7 +662,8 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
   __syncthreads();
   if constexpr (OP == OP_INV || OP == OP_INV_SCALE || OP == OP_INV_SOL) {
     if constexpr (OP == OP_INV_SOL) {
-      // line 1 = i d1(ky) b: the axis-1 derivative of chi before its inverse transform
+      // line 1 = i d1(ky) b: the axis-1 derivative of chi before its inverse
+      // transform (the axis-2 one, a factor per column, is applied at the store)
       for (int idx = threadIdx.x; idx < N * TX; idx += blockDim.x) {
         const int col = idx % TX, j = idx / TX;
         const cx<T> b = sm[(2 * TX + col) * C::LS + pad(j)];
@@ -832,9 +833,20 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
     s_fft<T, N, OP, NC, TX, +1, NOUT * TX>(sm, tw);
   }
   __syncthreads();
+  // OP_INV_SOL: line 2 leaves as i d2(kx) b; with NT a multiple of TX every
+  // thread stores one column, whose symbol is read once
+  constexpr bool fixed_col = C::NT % TX == 0;
+  T d2c = (T)0;
+  if constexpr (OP == OP_INV_SOL && fixed_col)
+    if ((int)threadIdx.x % TX < w) d2c = a.sym.d2[kx0 + (int)threadIdx.x % TX];
   for (int idx = threadIdx.x; idx < NOUT * N * TX; idx += blockDim.x) {
     const int col = idx % TX, j = (idx / TX) % N, c = idx / (TX * N);
-    if (col < w) base[c * a.compStride + j * a.rowStride + col] = sm[(c * TX + col) * C::LS + pad(j)];
+    if (col < w) {
+      cx<T> x = sm[(c * TX + col) * C::LS + pad(j)];
+      if constexpr (OP == OP_INV_SOL)
+        if (c == 2) x = cscale(mul_i(x), fixed_col ? d2c : a.sym.d2[kx0 + col]);
+      base[c * a.compStride + j * a.rowStride + col] = x;
+    }
   }
 }
 
@@ -979,18 +991,6 @@ __global__ void k_div_spec(const cx<T>* __restrict__ uh, cx<T>* __restrict__ dv,
     }
     const cx<T> s = cscale(uh[i], sym.d0[kz]) + cscale(uh[g.S + i], sym.d1[ky]) + cscale(uh[2 * g.S + i], sym.d2[kx]);
     dv[i] = mul_i(s);
-  }
-}
-
-// spec[c] *= i d2(kx) on the half spectrum of one component per problem
-template <typename T>
-__global__ void k_mul_id2(cx<T>* __restrict__ spec, long long ps, Geo g, const T* __restrict__ d2) {
-  const int p = blockIdx.y;
-  cx<T>* sp = spec + (long long)p * ps;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)g.n0 * g.n1 * g.P;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % g.P);
-    if (kx < g.Pu) sp[i] = cscale(mul_i(sp[i]), d2[kx]);
   }
 }
 

@@ -300,12 +300,6 @@ cudaError_t Ops<T>::x_solute(const Geo& g, int nprob, void* spec, const void* u,
 }
 
 template <typename T>
-cudaError_t Ops<T>::mul_id2(const Geo& g, int nprob, void* spec, long long ps, const Sym<T>& sym, cudaStream_t s) {
-  k_mul_id2<T><<<dim3(304, nprob), 256, 0, s>>>((cx<T>*)spec + 2 * g.S, ps, g, sym.d2);
-  return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t Ops<T>::x_r2c(const Geo& g, int nprob, int nc, void* spec, long long sps, const void* in, long long ips,
                           const void* tw, cudaStream_t s) {
   ACM_DISPATCH_N(g.n2, l_x_r2c, g, nprob, nc, spec, sps, in, ips, tw, s)

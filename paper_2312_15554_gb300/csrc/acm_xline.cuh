@@ -72,66 +72,71 @@ __device__ __forceinline__ unsigned xl_hmask(const uint32_t* __restrict__ Hb, co
 // Mask of the lanes of a warp that own lines (all of them when the warp is full).
 __device__ __forceinline__ unsigned xl_mask() { return 0xffffffffu; }
 
-// Z_k from the half spectrum: (X_k + conj X_{M-k}) + i (X_k - conj X_{M-k}) conj(W^k)
-template <typename T>
-__device__ __forceinline__ cx<T> xl_pre(cx<T> X, cx<T> Y, cx<T> w) {
-  const cx<T> e = X + cconj(Y), o = cmul(X - cconj(Y), cconj(w));
+// Pre- and post-processing twiddles. Lane t of a line holds k = t + TL m, and
+// W^k = W^t exp(-2 pi i m / (2E)) with W = exp(-2 pi i / N2), because N2 = 2 E TL:
+// the lane reads W^t once and multiplies by compile-time roots.
+
+// Z_k from the half spectrum: (X_k + conj X_{M-k}) + i (X_k - conj X_{M-k}) conj(W^k),
+// with wt = W^t and k = t + TL m
+template <int m, int E, typename T>
+__device__ __forceinline__ cx<T> xl_pre(cx<T> X, cx<T> Y, cx<T> wt) {
+  const cx<T> e = X + cconj(Y), o = root_mul<+1, m, 2 * E>(cmul(X - cconj(Y), cconj(wt)));
   return e + mul_i(o);
 }
 
 // X_k from Z: (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2  (k = 1..M-1)
-template <typename T>
-__device__ __forceinline__ cx<T> xl_post(cx<T> Zk, cx<T> Zm, cx<T> w) {
+template <int m, int E, typename T>
+__device__ __forceinline__ cx<T> xl_post(cx<T> Zk, cx<T> Zm, cx<T> wt) {
   const T h = (T)0.5;
   const cx<T> a = cscale(Zk + cconj(Zm), h), b = cscale(Zk - cconj(Zm), h);
-  return a - mul_i(cmul(w, b));
+  return a - mul_i(root_mul<-1, m, 2 * E>(cmul(wt, b)));
 }
 
 // Second Stockham stage (radix TL, span E) between shared memory and v:
 // reads positions t + TL i + E r, writes nothing; v[i + NB r] = outputs.
+// Its twiddles W_M^{j r} (j = t + TL i) are W_M^{t r} exp(-2 pi i i r / E):
+// the lane reads the TL - 1 values of i = 0 and rotates by compile-time roots.
 template <typename T, int N2, int SIGN>
 __device__ __forceinline__ void xl_stage2(const cx<T>* sl, const cx<T>* tw, int t, cx<T> (&v)[XL<T, N2>::E]) {
   using L = XL<T, N2>;
   constexpr int M = L::M, E = L::E, TL = L::TL, NB = L::NB;
+  cx<T> w0[TL];
+  const cx<T>* tws = tw + tw_offset(M, E) + t;
 #pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    const int j = t + TL * i;  // j < E: jm = j
+  for (int r = 1; r < TL; ++r) {
+    w0[r] = tws[(r - 1) * E];
+    if constexpr (SIGN > 0) w0[r].y = -w0[r].y;
+  }
+  static_for<NB>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int j = t + TL * i;
     cx<T> w2[TL];
 #pragma unroll
     for (int r = 0; r < TL; ++r) w2[r] = sl[pad(j + E * r)];
-    const cx<T>* tws = tw + tw_offset(M, E) + j;
-#pragma unroll
-    for (int r = 1; r < TL; ++r) {
-      cx<T> w = tws[(r - 1) * E];
-      if constexpr (SIGN > 0) w.y = -w.y;
-      w2[r] = cmul(w2[r], w);
-    }
+    static_for<TL - 1>([&](auto R1) {
+      constexpr int r = decltype(R1)::value + 1;
+      w2[r] = root_mul<SIGN, i * r, E>(cmul(w2[r], w0[r]));
+    });
     dft<TL, SIGN>(w2);
 #pragma unroll
     for (int r = 0; r < TL; ++r) v[i + NB * r] = w2[r];
-  }
+  });
 }
 
 // Inverse real transform of one line. sl holds the half spectrum X[0..M]
-// (at pad(k)) and is visible to all lanes of the line. With d non-null, X_k is
-// first multiplied by i d[k] (the derivative along the line). On return v[m] =
+// (at pad(k)) and is visible to all lanes of the line. On return v[m] =
 // z[t + TL m]; sl is free for reuse by the line's lanes.
 template <typename T, int N2>
 __device__ __forceinline__ void xl_inverse(cx<T>* sl, const cx<T>* tw, int t, unsigned mask,
-                                           cx<T> (&v)[XL<T, N2>::E], const T* __restrict__ d) {
+                                           cx<T> (&v)[XL<T, N2>::E]) {
   using L = XL<T, N2>;
   constexpr int M = L::M, E = L::E, TL = L::TL;
-  const cx<T>* twp = tw + tw_total(M);
-#pragma unroll
-  for (int r = 0; r < E; ++r) {
+  const cx<T> wt = tw[tw_total(M) + t];
+  static_for<E>([&](auto R) {
+    constexpr int r = decltype(R)::value;
     const int k = t + TL * r;
-    cx<T> X = sl[pad(k)], Y = sl[pad(M - k)];
-    if (d) {
-      X = cscale(mul_i(X), d[k]);
-      Y = cscale(mul_i(Y), d[M - k]);
-    }
-    v[r] = xl_pre(X, Y, twp[k]);
-  }
+    v[r] = xl_pre<r, E>(sl[pad(k)], sl[pad(M - k)], wt);
+  });
   dft<E, +1>(v);
   if constexpr (TL > 1) {
     __syncwarp(mask);  // every lane has read its X pairs
@@ -151,7 +156,7 @@ __device__ __forceinline__ void xl_forward(cx<T>* sl, const cx<T>* tw, int t, un
                                            cx<T> (&v)[XL<T, N2>::E], cx<T> (&X)[XL<T, N2>::E], cx<T>& xn) {
   using L = XL<T, N2>;
   constexpr int M = L::M, E = L::E, TL = L::TL;
-  const cx<T>* twp = tw + tw_total(M);
+  const cx<T> wt = tw[tw_total(M) + t];
   dft<E, -1>(v);
   __syncwarp(mask);  // earlier readers of sl are done
 #pragma unroll
@@ -166,17 +171,17 @@ __device__ __forceinline__ void xl_forward(cx<T>* sl, const cx<T>* tw, int t, un
   }
   __syncwarp(mask);
   // Z_k is the lane's own value (still in v); only Z_{M-k} comes from another lane
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
+  static_for<E>([&](auto I) {
+    constexpr int m = decltype(I)::value;
     const int k = t + TL * m;
     const cx<T> Zk = v[m];
     if (k == 0) {
       X[m] = mk<T>(Zk.x + Zk.y, (T)0);
       xn = mk<T>(Zk.x - Zk.y, (T)0);
     } else {
-      X[m] = xl_post(Zk, sl[pad(M - k)], twp[k]);
+      X[m] = xl_post<m, E>(Zk, sl[pad(M - k)], wt);
     }
-  }
+  });
 }
 
 }  // namespace acm
