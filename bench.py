@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -172,10 +173,14 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def time_to_permeability(acm, ctx, Hd, stream, n_long):
+def time_to_permeability(acm, ctx, Hd, stream, n_long, deriv=None, fixed_penalty=None):
     """Seconds until the permeability tensor stays within a relative error
-    (Frobenius) of the tensor after n_long iterations, for the plain solve with
-    default parameters, at 1e-1 ... 1e-4.
+    (Frobenius) of the tensor after n_long iterations, for the plain solve,
+    at 1e-1 ... 1e-4. deriv selects the derivative symbols of the Stokes solve
+    (None: the library default, the exact symbols of Eq. 13; DERIV_CENTRAL: the
+    approximate derivatives of Eq. 21). fixed_penalty = f runs with alpha = beta
+    = b = f times the default initial penalty and no Eq. 22 adaptation; None keeps
+    the library defaults (adaptive).
 
     The k = 0 Fourier coefficient of each Green solve gives the volume average of
     u for every iteration (history), so the crossing iteration n* is found from one
@@ -185,7 +190,12 @@ def time_to_permeability(acm, ctx, Hd, stream, n_long):
     """
     import torch
     u3 = torch.zeros((3, 3) + tuple(Hd.shape), dtype=torch.float32, device=Hd.device)
-    prm = acm.stokes_params(eps=0.0, max_iter=n_long, precision=acm.FP32, check_every=500)
+    kw = {} if deriv is None else {"deriv": deriv}
+    if fixed_penalty is not None:
+        n = float(np.prod(Hd.shape)) ** (1.0 / 3.0)
+        psi = fixed_penalty * (math.pi * n) ** 2 / 8.0   # nu = 1
+        kw.update(adaptive=0, alpha0=psi, beta0=psi, b0=psi)
+    prm = acm.stokes_params(eps=0.0, max_iter=n_long, precision=acm.FP32, check_every=500, **kw)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -210,7 +220,11 @@ def time_to_permeability(acm, ctx, Hd, stream, n_long):
             out[f"{rel:g}"] = {"reached": True, "iterations": n_star, "seconds": n_star * per_iter}
     return {"thresholds": out, "reference_iterations": n_long, "reference_last10pct_change": tail,
             "seconds_per_iteration": per_iter, "K_ref": Kref.tolist(),
-            "form": "plain (FP32, adaptive penalties of Eq. 22, library defaults, unit cell, nu = 1)"}
+            "form": "plain (FP32, unit cell, nu = 1), "
+                    + ("adaptive penalties of Eq. 22 (library defaults), " if fixed_penalty is None
+                       else f"fixed penalties {fixed_penalty:g} x the default initial penalty, ")
+                    + ("exact derivative symbols (Eq. 13)" if deriv is None or deriv == acm.DERIV_EXACT
+                       else "approximate derivative symbols (Eq. 21)")}
 
 
 def run_gpu(args, rank, world, dist):
@@ -300,6 +314,9 @@ def run_gpu(args, rank, world, dist):
 
     # time to permeability on one GPU only (several ranks would each hold a GPU for it)
     ttk = time_to_permeability(acm, ctx, Hd, stream, args.ttk_long) if (args.ttk and world == 1) else None
+    ttk_c = (time_to_permeability(acm, ctx, Hd, stream, args.ttk_long_central, deriv=acm.DERIV_CENTRAL,
+                                  fixed_penalty=4.0)
+             if (args.ttk and world == 1 and args.ttk_long_central > 0) else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -334,6 +351,8 @@ def run_gpu(args, rank, world, dist):
     }
     if ttk is not None:
         line["time_to_permeability"] = ttk
+    if ttk_c is not None:
+        line["time_to_permeability_central"] = ttk_c
     print(json.dumps(line), flush=True)
 
 
@@ -584,6 +603,8 @@ def main():
     ap.add_argument("--ttk", action=argparse.BooleanOptionalAction, default=True,
                     help="also measure time-to-permeability (K within 1e-4 of a long-run reference)")
     ap.add_argument("--ttk-long", type=int, default=20000, help="iterations of the reference run")
+    ap.add_argument("--ttk-long-central", type=int, default=8000,
+                    help="iterations of the reference run with the Eq. 21 symbols (0: skip that form)")
     ap.add_argument("--config", default="cell256", choices=["cell256", "batched", "grf512"],
                     help="cell256: the 256^3 cell (default); batched: 384 cells (192 at 64^3, 192 at 128^3); "
                          "grf512: the 512^3 Gaussian random field with the FP32/FP64 comparison")
