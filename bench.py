@@ -55,7 +55,7 @@ def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float) -> float:
         "y_fwd_stokes": 6 * cspec,
         "z_stokes": 10 * cspec,
         "y_inv_stokes": 6 * cspec,
-        # solute passes carry (tau_0, tau_1, s') -> (tau_0, s'') -> (d0 chi, chi) -> (d0 chi, d1 chi, chi)
+        # solute passes carry (tau_0, tau_1, s') -> (tau_0, s'') -> (d0 chi, chi) -> (d0 chi, d1 chi, d2 chi)
         "x_solute": 3 * cspec + 12.0 * porosity + 1.0 + 3 * cspec,
         "y_fwd_solute": 5 * cspec,
         "z_solute": 6 * cspec,
@@ -69,6 +69,25 @@ def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float) -> float:
 # launches). An entry holds only while the kernel is unchanged since that capture.
 MEASURED_TRAFFIC = {"x_solute": 833.302e6 + 563.497e6, "x_stokes_local": 2394.871e6 + 1127.122e6,
                     "x_stokes_rhs": 1223.463e6 + 587.302e6}
+
+
+def step_roofline(kern: dict, peak: float) -> dict:
+    """Algorithmic bandwidth of the whole step: the algorithmic bytes of every
+    kernel kind that has a byte count, summed, over their summed CUDA-event time
+    (the time-weighted mean over the pass kernels), against the peak; time_share
+    is the part of all timed kernel time those kinds cover."""
+    tot_b = tot_s = all_s = 0.0
+    for v in kern.values():
+        s = v["ms"] / 1e3
+        all_s += s
+        if v.get("GBps"):
+            tot_b += v["GBps"] * 1e9 * s
+            tot_s += s
+    if tot_s <= 0:
+        return None
+    achieved = tot_b / tot_s / 1e9
+    return {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "time_share": round(tot_s / all_s, 4), "basis": "algorithmic bytes, time-weighted over the pass kernels"}
 
 
 def measured_peaks():
@@ -341,6 +360,7 @@ def run_gpu(args, rank, world, dist):
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
                                        "profiles/dram_traffic_256.md" if dom in MEASURED_TRAFFIC else None,
                      "peak_source": peak_src, "bytes_per_launch": bytes_per_launch},
+        "roofline_step": step_roofline(kern, peak),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * V),
                 "d2h_bytes_per_step": int(8 * 9 * (1 + len(PECLETS)))},
