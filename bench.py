@@ -41,22 +41,27 @@ WORKLOAD = (f"{N}^3 Boolean sphere pack (radius {RADIUS:g} vox, porosity {POROSI
             f"solute Pe 1/10/100 x 3 loads")
 
 
-def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float) -> float:
+def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float, share: int = 3) -> float:
     """Bytes a kernel of the given kind must move per voxel and per problem (FP32).
 
     cspec: one complex FP32 component of the half spectrum (n2/2 + 1 of n2 columns).
-    Multiplier lambda lives on solid voxels only, the solute velocity on pore voxels only.
+    Multiplier lambda lives on solid voxels only, the solute velocity on pore voxels
+    only. share: problems of one launch that read the same indicator (the loads of
+    one cell) and, in the solute pass, the same velocity (the composition loads of
+    one flow field); data they share is counted once per launch. The indicator is
+    read as bits (1/8 byte per voxel).
     """
     cspec = 8.0 * (n2 // 2 + 1) / n2
     solid = 1.0 - porosity
+    hbits = 1.0 / 8.0
     return {
-        "x_stokes_local": 3 * cspec + 24.0 + 24.0 * solid + 1.0,
-        "x_stokes_rhs": 12.0 + 12.0 * solid + 1.0 + 3 * cspec,
+        "x_stokes_local": 3 * cspec + 24.0 + 24.0 * solid + hbits / share,
+        "x_stokes_rhs": 12.0 + 12.0 * solid + hbits / share + 3 * cspec,
         "y_fwd_stokes": 6 * cspec,
         "z_stokes": 10 * cspec,
         "y_inv_stokes": 6 * cspec,
         # solute passes carry (tau_0, tau_1, s') -> (tau_0, s'') -> (d0 chi, chi) -> (d0 chi, d1 chi, d2 chi)
-        "x_solute": 3 * cspec + 12.0 * porosity + 1.0 + 3 * cspec,
+        "x_solute": 3 * cspec + (12.0 * porosity + hbits) / share + 3 * cspec,
         "y_fwd_solute": 5 * cspec,
         "z_solute": 6 * cspec,
         "y_inv_solute": 5 * cspec,
@@ -558,8 +563,8 @@ def run_grf512(args, rank, world, dist):
     per_problem = {"x_stokes_local": 3, "x_stokes_rhs": 3, "y_fwd_stokes": 3, "z_stokes": 3, "y_inv_stokes": 3}
     nprob_of = lambda k: 1 if k in per_problem else 3
     kern = {k: {"ms": round(v[0], 3), "launches": v[1],
-                "GBps": (round(algorithmic_bytes_per_voxel(k, n, porosity) * V * nprob_of(k) * v[1] / (v[0] / 1e3) / 1e9,
-                               1) if v[1] and algorithmic_bytes_per_voxel(k, n, porosity) else None)}
+                "GBps": (round(algorithmic_bytes_per_voxel(k, n, porosity, nprob_of(k)) * V * nprob_of(k) * v[1]
+                               / (v[0] / 1e3) / 1e9, 1) if v[1] and algorithmic_bytes_per_voxel(k, n, porosity) else None)}
             for k, v in prof.items() if v[1]}
     peak, peak_src = measured_peaks()
     achieved = kern[dom]["GBps"]
