@@ -346,6 +346,28 @@ def test_converged_ls_matches_dense_fixed_point(shape, seed):
     np.testing.assert_allclose(R.chi, chi, atol=1e-10 * np.abs(chi).max())
 
 
+def test_central_ls_fixed_point_depends_on_a0_as_the_dense_solve_says():
+    """R6: with the Eq. 21 symbols L != |d|^2, so the converged chi keeps an
+    A0 (L - |d|^2) term; two comparison media give two fixed points, each the
+    dense stencil solve for its own A0."""
+    shape = (6, 4, 6)
+    H = I.random_indicator(shape, 0.4, 63)
+    u = 0.2 * I.random_field((3,) + shape, 64)
+    Pe, eta = 2.0, 0.1
+    B0 = np.array([0.1, 0.0, -0.1])
+    g = np.array([1.0, 0.3, 0.0])
+    D, Lneg = DO.central_ops(shape)
+    chis = []
+    for A0 in (0.7, 1.3):
+        R = O.advdiff(H, u, Pe, g, O.AdvDiffParams(eta=eta, A0=A0, B0=B0, eps=1e-14, max_iter=8000,
+                                                    deriv=O.CENTRAL))
+        assert R.converged
+        ref = DO.advdiff_fixed_point(H, u, Pe, g, D, Lneg, A0, B0, eta)
+        np.testing.assert_allclose(R.chi, ref, atol=1e-10 * np.abs(ref).max())
+        chis.append(R.chi)
+    assert np.abs(chis[0] - chis[1]).max() > 1e-4 * np.abs(chis[0]).max()
+
+
 @pytest.mark.parametrize("deriv", [O.EXACT, O.CENTRAL])
 def test_laminate_diffusivity_parallel_is_pore_fraction(deriv):
     n, s = 16, 6                              # solid layers normal to axis 0
