@@ -70,8 +70,8 @@ def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float, share: int 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel at the default workload (256^3, porosity 0.35, 3 problems per launch),
-# from the ncu capture summarised in profiles/dram_traffic_256.md (mean of four
-# launches). An entry holds only while the kernel is unchanged since that capture.
+# from one ncu capture of that kernel (mean over its captured launches). An
+# entry holds only while the kernel is unchanged since that capture.
 MEASURED_TRAFFIC = {"x_solute": 833.302e6 + 563.497e6, "x_stokes_local": 2394.871e6 + 1127.122e6,
                     "x_stokes_rhs": 1223.463e6 + 587.302e6}
 
@@ -158,6 +158,12 @@ def make_inputs(rank: int):
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
+def oracle_threads() -> int:
+    """Host threads the oracle's transforms run on (its pointwise numpy work is single-threaded)."""
+    from oracle import fft as FFT
+    return FFT.threads()
+
+
 def oracle_sample(H, iters: int = 1):
     """Oracle Stokes + solute iterations on one load each; returns (voxel-iterations, seconds)."""
     from oracle import acm_oracle as O
@@ -186,9 +192,10 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "sample": "1 Stokes + 1 solute iteration (1 load each) per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                          "sample": "per step: 1 ADMM iteration (load e_0) + 1 Lippmann-Schwinger iteration "
-                                   "(Pe 10, g_chi e_0) at 256^3, numpy FP64"},
+                                   "(Pe 10, g_chi e_0) at 256^3, FP64 oracle (own radix-2 FFT in C over "
+                                   "the host threads, pointwise steps in numpy)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -345,9 +352,10 @@ def run_gpu(args, rank, world, dist):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         vi_c, s_c = oracle_sample(H, 1)
-        cpu = {"value": vi_c / s_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": vi_c / s_c, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                "sample": "1 ADMM iteration (load e_0) + 1 Lippmann-Schwinger iteration (Pe 10) at 256^3, "
-                         f"numpy FP64, {s_c:.1f} s"}
+                         f"FP64 oracle (own radix-2 FFT in C over the host threads, pointwise steps in numpy), "
+                         f"{s_c:.1f} s"}
     ctx.close()
     if rank != 0:
         return
@@ -362,8 +370,8 @@ def run_gpu(args, rank, world, dist):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": MEASURED_TRAFFIC.get(dom) if (N == 256 and abs(POROSITY - 0.35) < 1e-9) else None,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                                       "profiles/dram_traffic_256.md" if dom in MEASURED_TRAFFIC else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
+                                       if dom in MEASURED_TRAFFIC else None,
                      "peak_source": peak_src, "bytes_per_launch": bytes_per_launch},
         "roofline_step": step_roofline(kern, peak),
         "cpu_baseline": cpu,

@@ -5,7 +5,7 @@ this module; only the tests, `__graft_entry__.smoke()` and the CPU-baseline leg 
 `bench.py` use it. It shares no code with the CUDA path.
 
 It is a slow, literal restatement of the paper in numpy (double precision,
-full complex spectra from `numpy.fft`), in
+full complex spectra from the oracle's own radix-2 FFT in `oracle/fft.py`), in
 the order and notation of the paper:
 
 * Stokes flow, Section 3.1: ADMM steps 1-4 (Eq. 7-13) with the adaptive
@@ -18,7 +18,7 @@ the order and notation of the paper:
 Conventions (unit cube, grid (n0, n1, n2), h_c = 1/n_c, component c of a vector
 field is along array axis c):
 
-* forward DFT  f^(m) = sum_x f(x) exp(-2 pi i m.x), unnormalised (numpy.fft.fftn);
+* forward DFT  f^(m) = sum_x f(x) exp(-2 pi i m.x), unnormalised (oracle/fft.py);
 * wavenumber k_c = 2 pi m_c;
 * first-derivative symbol d_c (d/dx_c <-> i d_c), Laplacian symbol L (-Laplacian <-> L):
   EXACT    d_c = k_c (0 on the Nyquist plane of axis c), L = |k|^2;
@@ -40,6 +40,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from oracle import fft as FFT
+
 EXACT = 0
 CENTRAL = 1
 
@@ -53,12 +55,12 @@ def axis_symbols(n: int, deriv: int):
     """First-derivative and second-derivative symbols on one axis of n points.
 
     Returns (d, l) with d/dx <-> i*d and -d^2/dx^2 <-> l, for integer
-    frequencies m in numpy.fft order (0..n/2-1, -n/2..-1).
+    frequencies m in DFT order (0..n/2-1, -n/2..-1).
     """
     if n < 2 or n % 2:
         raise ValueError("axis length must be even and >= 2")
     h = 1.0 / n
-    m = np.fft.fftfreq(n, d=1.0 / n)
+    m = np.concatenate([np.arange(0, n // 2), np.arange(-(n // 2), 0)]).astype(np.float64)
     k = 2.0 * np.pi * m
     if deriv == EXACT:
         d = k.copy()
@@ -85,11 +87,13 @@ def symbols(shape, deriv: int):
 
 
 def fft3(f):
-    return np.fft.fftn(f, axes=(-3, -2, -1))
+    """Forward DFT over the three grid axes (the last three array axes)."""
+    return FFT.fftn(f, axes=(-3, -2, -1))
 
 
 def ifft3(fh):
-    return np.fft.ifftn(fh, axes=(-3, -2, -1)).real
+    """Inverse DFT over the three grid axes; the real part (every field of the method is real)."""
+    return FFT.ifftn(fh, axes=(-3, -2, -1)).real
 
 
 def spectral_grad(f, d):
@@ -215,6 +219,26 @@ def stokes_step1(state: StokesState, g, nu, beta, b, d, L):
     return u_new, div_new, u_h
 
 
+def adapt_penalties(psi, r, phi, tau, psi_min):
+    """Eq. 22: the penalties of the next iteration from this iteration's residuals.
+
+    Constraint pair k = 0, 1, 2 (primal r[2k], dual r[2k + 1]) drives psi[k] =
+    alpha, beta, b. The penalty grows by phi_k when the primal residual exceeds
+    tau_k times the dual one, shrinks by phi_k (not below psi_min[k]) when the
+    dual residual exceeds tau_k times the primal one, and stays otherwise. The
+    ratios are compared as products (r_p > tau r_d), so a zero residual needs no
+    division.
+    """
+    out = list(psi)
+    for k in range(3):
+        rp, rd = r[2 * k], r[2 * k + 1]
+        if rp > tau[k] * rd:
+            out[k] = phi[k] * psi[k]
+        elif rd > tau[k] * rp:
+            out[k] = max(psi[k] / phi[k], psi_min[k])
+    return out
+
+
 def stokes(H, g, params: StokesParams = None, init: StokesState = None,
            record_mean_u: bool = False) -> StokesResult:
     """Algorithm 1, Problem 1: ADMM for Stokes flow in the periodic cell.
@@ -277,13 +301,7 @@ def stokes(H, g, params: StokesParams = None, init: StokesState = None,
             converged = True
             break
         if P.adaptive:
-            # Eq. 22: pair k = 1, 2, 3 drives psi_k = alpha, beta, b
-            for k in range(3):
-                rp, rd = r[2 * k], r[2 * k + 1]
-                if rp > P.tau[k] * rd:
-                    psi[k] = P.phi[k] * psi[k]
-                elif rd > P.tau[k] * rp:
-                    psi[k] = max(psi[k] / P.phi[k], psi_min[k])
+            psi = adapt_penalties(psi, r, P.phi, P.tau, psi_min)
     p = st.q - st.q.mean()
     return StokesResult(state=st, p=p, iters=it, converged=converged,
                         residuals=np.array(res_h), tolerances=np.array(tol_h),

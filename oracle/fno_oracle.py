@@ -30,6 +30,8 @@ import math
 import numpy as np
 from scipy.special import erf
 
+from oracle import fft as FFT
+
 
 def kept_modes(shape, modes):
     """Index arrays (i0, i1, i2) of the kept modes in the rfftn layout, mode order
@@ -83,7 +85,7 @@ def gelu_grad(z):
 
 def _fwd_dft(v, idx):
     """F(v) on the kept modes: (C, M) complex."""
-    vh = np.fft.rfftn(v, axes=(1, 2, 3))
+    vh = FFT.rfftn(v, axes=(1, 2, 3))
     return vh[:, idx[0], idx[1], idx[2]]
 
 
@@ -92,7 +94,7 @@ def _inv_dft(Y, idx, shape):
     C = Y.shape[0]
     yh = np.zeros((C, shape[0], shape[1], shape[2] // 2 + 1), dtype=np.complex128)
     yh[:, idx[0], idx[1], idx[2]] = Y
-    return np.fft.irfftn(yh, s=shape, axes=(1, 2, 3))
+    return FFT.irfftn(yh, s=shape, axes=(1, 2, 3))
 
 
 def forward(theta, H, width, modes, layers):

@@ -223,6 +223,122 @@ def test_plane_poiseuille_exact_symbol_bracketed_and_converging():
 
 
 # --------------------------------------------------------------------------
+# Eq. 2 literally: K_ij = integral over Y_p of grad u^i : grad u^j
+# --------------------------------------------------------------------------
+def _poiseuille_profile(n, s):
+    """Discrete central-symbol Poiseuille profile of a slab (s solid layers at
+    the start of axis 1, m = n - s fluid layers), g = nu = 1: u_j = h^2 j (m + 1 - j) / 2."""
+    m = n - s
+    h = 1.0 / n
+    prof = np.zeros(n)
+    j = np.arange(1, m + 1)
+    prof[s:] = h * h * j * (m + 1 - j) / 2.0
+    return prof
+
+
+def test_gradient_form_of_the_discrete_poiseuille_profile():
+    """With the central symbol the gradient of u_j = h^2 j (m + 1 - j)/2 at fluid
+    layer j is the central difference (u_{j+1} - u_{j-1}) / 2h = h (m + 1 - 2j)/2
+    (u = 0 in the walls), so over the pore Eq. 2 gives
+    h^3 N^2 sum_j h^2 (m + 1 - 2j)^2 / 4 = h^3 m (m^2 - 1) / 12 (unit cube)."""
+    n, s = 16, 5
+    m, h = n - s, 1.0 / n
+    H = I.slab((4, n, 4), s, normal_axis=1)
+    u = np.zeros((3,) + H.shape)
+    u[0] = _poiseuille_profile(n, s)[None, :, None]
+    Kg = O.permeability_grad_form(H, [u], O.CENTRAL)
+    closed = h**3 * m * (m * m - 1) / 12.0
+    assert Kg[0, 0] == pytest.approx(closed, rel=1e-12)
+    # the same sum with the stencils written out (pore voxels only)
+    grad = np.stack([DO.grad_fd(u[c]) for c in range(3)])
+    pore = H == 0
+    assert np.sum((grad * grad)[:, :, pore]) / H.size == pytest.approx(closed, rel=1e-12)
+    # the integral over all of Y (walls included) is a different number: the
+    # central difference at the wall layers next to the fluid is not zero
+    assert np.sum(grad * grad) / H.size > closed * (1 + 1e-2)
+    # and so is the exact symbol's gradient of the same field
+    assert abs(O.permeability_grad_form(H, [u], O.EXACT)[0, 0] / closed - 1) > 1e-2
+
+
+def test_gradient_form_of_a_single_mode_over_half_the_cell():
+    """u = (cos 2 pi m x1, 0, 0) with the exact symbols has |grad u|^2 =
+    (2 pi m)^2 sin^2(2 pi m x1); over a pore that is the half x0 < 1/2 of the
+    cell Eq. 2 gives (2 pi m)^2 / 4. The cross term of two loads follows the
+    product of their gradients."""
+    shape = (8, 16, 4)
+    m = 3
+    x1 = (np.arange(shape[1]) + 0.5) / shape[1]
+    H = np.zeros(shape, np.uint8)
+    H[shape[0] // 2:] = 1
+    u = np.zeros((3,) + shape)
+    u[0] = np.cos(2 * np.pi * m * x1)[None, :, None]
+    v = np.zeros((3,) + shape)
+    v[0] = np.sin(2 * np.pi * m * x1)[None, :, None]
+    K = O.permeability_grad_form(H, [u, v], O.EXACT)
+    k2 = (2 * np.pi * m) ** 2
+    assert K[0, 0] == pytest.approx(k2 / 4, rel=1e-12)
+    assert K[1, 1] == pytest.approx(k2 / 4, rel=1e-12)
+    assert abs(K[0, 1]) < 1e-12 * k2       # sin cos integrates to zero over whole periods
+    Kall = O.permeability_grad_form(np.zeros(shape, np.uint8), [u], O.EXACT)
+    assert Kall[0, 0] == pytest.approx(k2 / 2, rel=1e-12)
+
+
+def test_converged_slab_flow_gives_the_gradient_form_closed_form():
+    """The oracle's converged central-symbol slab flow, through
+    permeability_tensor, reproduces h^3 m (m^2 - 1)/12 for K_grad[0, 0]."""
+    n, s = 16, 5
+    m, h = n - s, 1.0 / n
+    H = I.slab((4, n, 4), s, normal_axis=1)
+    P = O.StokesParams(eps=1e-12, alpha0=300, beta0=300, b0=300, adaptive=False, max_iter=60000,
+                       deriv=O.CENTRAL)
+    R = O.stokes(H, [1.0, 0.0, 0.0], P)
+    assert R.converged
+    Kg = O.permeability_grad_form(H, [R.state.u], O.CENTRAL)
+    assert Kg[0, 0] == pytest.approx(h**3 * m * (m * m - 1) / 12.0, rel=1e-7)
+
+
+# --------------------------------------------------------------------------
+# Eq. 22: adaptive penalties
+# --------------------------------------------------------------------------
+def test_adaptive_penalty_rule_on_hand_built_residuals():
+    """Each case is Eq. 22 read off its text: psi_k grows by phi_k when
+    r_p / r_d > tau_k, shrinks by phi_k but not below psi_min when
+    r_d / r_p > tau_k, and stays otherwise; pair k drives (alpha, beta, b)[k]."""
+    psi = [10.0, 20.0, 30.0]
+    phi = (1.1, 1.2, 1.5)
+    tau = (5.0, 10.0, 5.0)
+    psi_min = [1.0, 1.0, 29.0]
+    # pair 1: r_p / r_d = 6 > 5 -> 11; pair 2: r_d / r_p = 11 > 10 -> 20 / 1.2;
+    # pair 3: r_d / r_p = 10 > 5 -> max(30 / 1.5, 29) = 29
+    out = O.adapt_penalties(psi, [60.0, 10.0, 1.0, 11.0, 1.0, 10.0], phi, tau, psi_min)
+    np.testing.assert_allclose(out, [11.0, 20.0 / 1.2, 29.0], rtol=1e-15)
+    # ratios at or inside the band leave every penalty alone
+    out = O.adapt_penalties(psi, [5.0, 1.0, 1.0, 9.0, 1.0, 4.0], phi, tau, psi_min)
+    np.testing.assert_allclose(out, psi, rtol=0)
+    # zero residuals: 0 > tau * 0 is false, a positive primal over a zero dual grows,
+    # a positive dual over a zero primal shrinks
+    out = O.adapt_penalties(psi, [0.0, 0.0, 1e-3, 0.0, 0.0, 1e-3], phi, tau, psi_min)
+    np.testing.assert_allclose(out, [10.0, 24.0, 29.0], rtol=1e-15)
+    # shrinking stops at psi_min exactly
+    out = O.adapt_penalties([1.05, 20.0, 30.0], [1.0, 100.0, 1.0, 1.0, 1.0, 1.0], phi, tau, psi_min)
+    np.testing.assert_allclose(out, [1.0, 20.0, 30.0], rtol=0)
+
+
+def test_admm_takes_the_next_penalties_from_this_iterations_residuals():
+    """In an adaptive run the penalties of iteration n + 1 are Eq. 22 applied to
+    the penalties and residuals of iteration n, and both directions occur."""
+    H = I.sphere_pack((8, 8, 8), 0.5, 2.0, 3)[0]
+    P = O.StokesParams(eps=0.0, adaptive=True, max_iter=40, alpha0=1.0, beta0=2000.0, b0=300.0)
+    R = O.stokes(H, [1.0, 0.0, 0.0], P)
+    psi_min = [P.psi_min_frac * x for x in (1.0, 2000.0, 300.0)]
+    for n in range(R.iters - 1):
+        nxt = O.adapt_penalties(list(R.penalties[n]), R.residuals[n], P.phi, P.tau, psi_min)
+        np.testing.assert_allclose(R.penalties[n + 1], nxt, rtol=0)
+    steps = np.diff(np.log(R.penalties), axis=0)
+    assert (steps > 0).any() and (steps < 0).any()
+
+
+# --------------------------------------------------------------------------
 # periodic simple-cubic sphere array (Hasimoto 1959; Sangani & Acrivos 1982)
 # --------------------------------------------------------------------------
 def hasimoto_sangani_acrivos(c):
@@ -347,7 +463,7 @@ def test_converged_ls_matches_dense_fixed_point(shape, seed):
 
 
 def test_central_ls_fixed_point_depends_on_a0_as_the_dense_solve_says():
-    """R6: with the Eq. 21 symbols L != |d|^2, so the converged chi keeps an
+    """With the Eq. 21 symbols L != |d|^2, so the converged chi keeps an
     A0 (L - |d|^2) term; two comparison media give two fixed points, each the
     dense stencil solve for its own A0."""
     shape = (6, 4, 6)
