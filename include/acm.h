@@ -88,7 +88,9 @@ typedef struct acm_stokes_params {
   double phi[3];       /* Eq. 22 growth factors for (alpha, beta, b) (default 1.1) */
   double tau[3];       /* Eq. 22 residual-balance ratios (default {5, 10, 5}) */
   double psi_min_frac; /* psi_min = psi_min_frac * psi0 (default 1e-3) */
-  double eps32;        /* FP32 phase tolerance of ACM_FP32_THEN_FP64 (default 1e-5) */
+  double eps32;        /* FP32 phase tolerance of ACM_FP32_THEN_FP64 (default 1e-5); a load
+                          whose FP32 residuals stop gaining on it (no 2 % gain in 500
+                          iterations: the FP32 rounding floor) moves on to FP64 early */
   int max_iter;        /* iteration cap (default 20000) */
   int adaptive;        /* 1: Eq. 22 penalty updates; 0: fixed penalties (default 1) */
   int deriv;           /* acm_deriv (default ACM_DERIV_EXACT) */
@@ -108,8 +110,12 @@ typedef struct acm_advdiff_params {
   int max_iter;        /* iteration cap (default 20000) */
   int deriv;           /* acm_deriv (default ACM_DERIV_CENTRAL) */
   int precision;       /* acm_precision (default ACM_FP32); with ACM_FP32_THEN_FP64 the
-                          FP32 iterations run to max(eps, 1e-5), then FP64 ones to eps */
-  int check_every;     /* iterations between host checks of the stop flag (default 16) */
+                          FP32 iterations run to max(eps, 1e-5) (or until they stop
+                          gaining on it, their rounding floor), then FP64 ones to eps */
+  int check_every;     /* iterations between host checks of the stop flag when the
+                          loop is host-launched (default 16) */
+  int device_loop;     /* 1: the whole iteration loop is one device-resident CUDA graph
+                          launch (default); 0: host-launched chunks of check_every */
 } acm_advdiff_params;
 
 /* Per-solve report. For Stokes res/tol hold r_p1, r_d1, r_p2, r_d2, r_p3, r_d3
@@ -349,13 +355,14 @@ acm_status acm_profile_read(acm_ctx* ctx, double* ms, long long* launches);
  *                ACM_ERR_UNSUPPORTED_SIZE before any device work.
  *   fp64         0: float input, 1: double input.
  *   in           device pointer, real [n0][n1][n2]; out: device pointer,
- *                complex interleaved [n0][n1][n2/2 + 1]; host pointers return
- *                ACM_ERR_ARG.
+ *                complex interleaved [n0][n1][n2/2 + 1]; both in memory of the
+ *                current device (or managed memory). Host pointers and memory
+ *                of another device return ACM_ERR_ARG before any device work.
  *   cuda_stream  stream of the work (NULL = default stream); the call returns
  *                once the work is enqueued.
  * The first call on a device (with that device current) resolves the array's
- * device address with cudaGetSymbolAddress and uploads a twiddle table with a
- * synchronous copy; make that first call before any stream capture. Every call
+ * device address with cudaGetSymbolAddress, uploads a twiddle table and
+ * synchronises the device; make that first call before any stream capture. Every call
  * on a device shares the one array and overwrites every part of it that it
  * later reads, so nothing has to start at zero; calls whose work overlaps on the
  * GPU (other streams, other host threads) race on the array. */

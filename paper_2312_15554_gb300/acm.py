@@ -46,7 +46,7 @@ class acm_stokes_params(C.Structure):
 class acm_advdiff_params(C.Structure):
     _fields_ = [("eta", C.c_double), ("A0", C.c_double), ("B0", C.c_double * 3), ("B0_explicit", C.c_int),
                 ("eps", C.c_double), ("max_iter", C.c_int), ("deriv", C.c_int), ("precision", C.c_int),
-                ("check_every", C.c_int)]
+                ("check_every", C.c_int), ("device_loop", C.c_int)]
 
 
 class acm_report(C.Structure):
@@ -295,10 +295,35 @@ def acm_history(ctx, index: int = 0, cap: int = 20000):
     return np.array(buf[:]).reshape(k, ln.value)
 
 
-def acm_fft_r2c_static(x, out, fp64: bool, stream: int = 0):
-    """The allocation-free transform (no context; device buffers only)."""
-    n0, n1, n2 = (int(s) for s in x.shape[-3:])
-    _check(load().acm_fft_r2c_static(n0, n1, n2, int(fp64), _ptr(x), _ptr(out), C.c_void_p(stream)),
+def acm_fft_r2c_static(x, out, fp64: bool, stream: int = None):
+    """The allocation-free transform (no context; device buffers only).
+
+    x: real [n0][n1][n2] (float64 when fp64, else float32); out: [n0][n1][n2/2 + 1][2]
+    of the same dtype. The C side cannot see buffer sizes or dtypes, so they are
+    checked here; stream defaults to torch's current stream of x's device.
+    """
+    fp64 = bool(fp64)
+    want = "float64" if fp64 else "float32"
+    for name, t in (("x", x), ("out", out)):
+        if not hasattr(t, "data_ptr") or not hasattr(t, "is_cuda"):
+            raise ValueError(f"{name} must be a torch tensor")
+        if str(t.dtype).replace("torch.", "") != want:
+            raise ValueError(f"{name} must be {want} for fp64={fp64}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if x.dim() != 3:
+        raise ValueError("x must be a 3-D real field [n0][n1][n2]")
+    n0, n1, n2 = (int(s) for s in x.shape)
+    if tuple(out.shape) != (n0, n1, n2 // 2 + 1, 2):
+        raise ValueError(f"out must have shape {(n0, n1, n2 // 2 + 1, 2)}, got {tuple(out.shape)}")
+    if x.is_cuda:
+        import torch
+        cur = torch.cuda.current_device()
+        if x.device.index != cur or not out.is_cuda or out.device.index != cur:
+            raise ValueError("x and out must be on the current CUDA device")
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device).cuda_stream
+    _check(load().acm_fft_r2c_static(n0, n1, n2, int(fp64), _ptr(x), _ptr(out), C.c_void_p(stream or 0)),
            "acm_fft_r2c_static")
 
 

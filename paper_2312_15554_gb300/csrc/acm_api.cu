@@ -23,6 +23,9 @@ namespace {
 constexpr int BMAX = 3;          // problems of the single-cell entry points (three loads)
 constexpr int HIST_CAP = 20000;  // per-problem history records
 constexpr int NRED = 304;        // blocks of the FP64 field reductions
+// iterations without a 2 % gain towards the tolerance after which the FP32
+// phase of ACM_FP32_THEN_FP64 hands a problem over to FP64
+constexpr int STALL_WINDOW = 500;
 
 struct Prec {
   bool ready = false;
@@ -43,10 +46,24 @@ struct CxT {
 
 }  // namespace
 
-struct GraphCache {
-  cudaGraphExec_t exec = nullptr;
+// What a captured loop depends on beyond its buffers: precision, problems,
+// derivative symbols, kind (1 Stokes, 2 solute), iteration cap and the caller
+// buffers it reads in place (the solute's velocity and indicator).
+struct GraphKey {
   int prec = -1, nprob = -1, deriv = -1, kind = -1;
   unsigned cap = 0;
+  const void* kp = nullptr;
+  const void* kq = nullptr;
+  long long kx = 0;
+  bool operator==(const GraphKey& o) const {
+    return prec == o.prec && nprob == o.nprob && deriv == o.deriv && kind == o.kind && cap == o.cap &&
+           kp == o.kp && kq == o.kq && kx == o.kx;
+  }
+};
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  GraphKey key;
   unsigned int* counter = nullptr;  // device iteration counter of the loop
 };
 
@@ -57,7 +74,8 @@ struct acm_ctx {
   int B = BMAX;       // problem capacity of the workspace
   int ncells = 1;     // indicator slots in Hd (cells of a batch)
   int spec_comps = 4; // spectral components per problem (3 suffice for Stokes-only batches)
-  GraphCache graph;
+  GraphCache graph;      // the Stokes loop
+  GraphCache graph_sol;  // the solute loop
   cudaStream_t cap = nullptr;  // non-blocking stream used only to capture graphs
   Prec pf, pd;
   StokesDev* sprm = nullptr;
@@ -155,6 +173,15 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// captured loops hold kernel arguments (tile widths, buffers): drop them
+// whenever those change
+void drop_graphs(acm_ctx* c) {
+  for (GraphCache* g : {&c->graph, &c->graph_sol}) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
 }
 
 template <typename T>
@@ -338,7 +365,7 @@ double default_penalty(const Geo& g, double nu) {
 template <typename T>
 acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int lph, const double (*gs)[3],
                         const acm_stokes_params& P, double eps, const void* const* init_u,
-                        const void* const* init_lam, const int* preset_status = nullptr) {
+                        const void* const* init_lam, const int* preset_status = nullptr, int stall_win = 0) {
   CKS(ensure_prec<T>(c));
   Prec& w = prec<T>(c);
   Geo g = c->g;
@@ -397,6 +424,8 @@ acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
     for (int k = 0; k < 3; ++k) d.psi_last[k] = d.psi[k];
     d.adaptive = P.adaptive;
     d.max_iter = P.max_iter;
+    d.stall_win = stall_win;
+    d.stall_best = 1e300;
     if (preset_status && preset_status[p] != ACM_OK) {  // degenerate cell: not iterated
       d.done = 1;
       d.status = preset_status[p];
@@ -449,19 +478,15 @@ struct StokesGroup {
   int lph;
 };
 
-// Device-resident loop: a CUDA graph whose while node repeats [step 1, steps
-// 2-4] of every group until all stop flags are set (or `cap` iterations); the
-// host launches it once and waits. The graph is cached in `cache` for reuse
-// while the key (precision, problems, symbols, kind) and the buffers are the same.
-template <typename T>
-acm_status stokes_graph_run(std::vector<StokesGroup>& grp, int deriv, unsigned cap, GraphCache& cache,
-                            cudaStream_t st) {
-  const int key_prec = (int)sizeof(T);
-  int total = 0;
-  for (auto& x : grp) total += x.nprob;
-  const bool valid = cache.exec && cache.prec == key_prec && cache.nprob == total && cache.deriv == deriv &&
-                     cache.kind == 1;
-  if (!valid) {
+// Device-resident loop: a CUDA graph whose while node repeats the work that
+// `capture` enqueues (one iteration of every context in `ctxs`) followed by
+// the loop-control kernel, until every stop flag of `lc` is set or `cap`
+// iterations have run; the host launches it once and waits. The instantiated
+// graph is cached in `cache` while its key and the contexts' buffers stay the same.
+template <typename Capture>
+acm_status graph_loop_run(GraphCache& cache, const GraphKey& key, std::vector<acm_ctx*>& ctxs, Capture&& capture,
+                          LoopCtl lc, cudaStream_t st) {
+  if (!(cache.exec && cache.key == key)) {
     if (cache.exec) {
       cudaGraphExecDestroy(cache.exec);
       cache.exec = nullptr;
@@ -491,41 +516,29 @@ acm_status stokes_graph_run(std::vector<StokesGroup>& grp, int deriv, unsigned c
     }
     cudaGraph_t body = np.conditional.phGraph_out[0];
     // capture on a private non-blocking stream (the caller's stream may be the
-    // legacy default stream, which cannot be captured); every group launches
+    // legacy default stream, which cannot be captured); every context launches
     // on it during the capture
-    cudaStream_t capst = grp[0].c->cap;
+    cudaStream_t capst = ctxs[0]->cap;
     if (!capst) {
       cudaGraphDestroy(graph);
       return ACM_ERR_CUDA;
     }
     std::vector<cudaStream_t> saved;
-    for (auto& x : grp) {
-      saved.push_back(x.c->st);
-      x.c->st = capst;
+    for (acm_ctx* x : ctxs) {
+      saved.push_back(x->st);
+      x->st = capst;
     }
     const cudaError_t eb = cudaStreamBeginCaptureToGraph(capst, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (eb != cudaSuccess) {
-      for (size_t i = 0; i < grp.size(); ++i) grp[i].c->st = saved[i];
+      for (size_t i = 0; i < ctxs.size(); ++i) ctxs[i]->st = saved[i];
       note_error(eb, "cudaStreamBeginCaptureToGraph", __LINE__);
       cudaGraphDestroy(graph);
       cudaGetLastError();
       return ACM_ERR_CUDA;
     }
-    acm_status s = ACM_OK;
-    LoopCtl lc = {};
-    for (size_t i = 0; i < grp.size() && s == ACM_OK; ++i) {
-      StokesGroup& x = grp[i];
-      const Sym<T> sym = sym_of<T>(x.c, deriv);
-      s = stokes_step1<T>(x.c, x.nprob, x.H, x.hs, x.lph, sym);
-      if (s == ACM_OK) s = stokes_body<T>(x.c, x.nprob, x.H, x.hs, x.lph, sym, true);
-      lc.base[i] = (const char*)x.c->sprm;
-      lc.n[i] = x.nprob;
-      lc.stride[i] = (int)sizeof(StokesDev);
-    }
-    lc.ngroups = (int)grp.size();
-    lc.done_off = (int)offsetof(StokesDev, done);
+    acm_status s = capture();
     lc.counter = cache.counter;
-    lc.cap = cap;
+    lc.cap = key.cap;
     lc.handle = handle;
     if (s == ACM_OK) {
       const cudaError_t el = loop_control(lc, capst);
@@ -536,7 +549,7 @@ acm_status stokes_graph_run(std::vector<StokesGroup>& grp, int deriv, unsigned c
     }
     cudaGraph_t captured = body;
     const cudaError_t e = cudaStreamEndCapture(capst, &captured);
-    for (size_t i = 0; i < grp.size(); ++i) grp[i].c->st = saved[i];
+    for (size_t i = 0; i < ctxs.size(); ++i) ctxs[i]->st = saved[i];
     if (s != ACM_OK || e != cudaSuccess) {
       if (e != cudaSuccess) note_error(e, "cudaStreamEndCapture", __LINE__);
       cudaGraphDestroy(graph);
@@ -551,21 +564,46 @@ acm_status stokes_graph_run(std::vector<StokesGroup>& grp, int deriv, unsigned c
       cache.exec = nullptr;
       return ACM_ERR_CUDA;
     }
-    cache.prec = key_prec;
-    cache.nprob = total;
-    cache.deriv = deriv;
-    cache.kind = 1;
-    cache.cap = cap;
-  }
-  if (cache.cap != cap) {
-    // the cap is a kernel argument: rebuild with the new one
-    cache.nprob = -1;
-    return stokes_graph_run<T>(grp, deriv, cap, cache, st);
+    cache.key = key;
   }
   CK(cudaMemsetAsync(cache.counter, 0, sizeof(unsigned int), st));
   CK(cudaGraphLaunch(cache.exec, st));
   CK(cudaStreamSynchronize(st));
   return ACM_OK;
+}
+
+// The Stokes loop of every group as one device-resident graph: [step 1, steps 2-4].
+template <typename T>
+acm_status stokes_graph_run(std::vector<StokesGroup>& grp, int deriv, unsigned cap, GraphCache& cache,
+                            cudaStream_t st) {
+  GraphKey key;
+  key.prec = (int)sizeof(T);
+  key.nprob = 0;
+  for (auto& x : grp) key.nprob += x.nprob;
+  key.deriv = deriv;
+  key.kind = 1;
+  key.cap = cap;
+  std::vector<acm_ctx*> ctxs;
+  LoopCtl lc = {};
+  for (size_t i = 0; i < grp.size(); ++i) {
+    ctxs.push_back(grp[i].c);
+    lc.base[i] = (const char*)grp[i].c->sprm;
+    lc.n[i] = grp[i].nprob;
+    lc.stride[i] = (int)sizeof(StokesDev);
+  }
+  lc.ngroups = (int)grp.size();
+  lc.done_off = (int)offsetof(StokesDev, done);
+  auto capture = [&]() -> acm_status {
+    acm_status s = ACM_OK;
+    for (size_t i = 0; i < grp.size() && s == ACM_OK; ++i) {
+      StokesGroup& x = grp[i];
+      const Sym<T> sym = sym_of<T>(x.c, deriv);
+      s = stokes_step1<T>(x.c, x.nprob, x.H, x.hs, x.lph, sym);
+      if (s == ACM_OK) s = stokes_body<T>(x.c, x.nprob, x.H, x.hs, x.lph, sym, true);
+    }
+    return s;
+  };
+  return graph_loop_run(cache, key, ctxs, capture, lc, st);
 }
 
 // Iterations of the device-resident loop. With device_loop (and the profiler
@@ -617,6 +655,7 @@ acm_status stokes_promote(acm_ctx* c, int nprob, double eps) {
     x.converged = 0;
     x.status = 0;
     x.eps = eps;
+    x.stall_win = 0;
   }
   CK(cudaMemcpyAsync(c->sprm, hp.data(), nprob * sizeof(StokesDev), cudaMemcpyHostToDevice, c->st));
   return ACM_OK;
@@ -732,7 +771,7 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
     // FP32 iterations to eps32 (warm start given in double is cast on the host side by the caller)
     const double e32 = P.eps < P.eps32 ? P.eps32 : P.eps;
     if (init_u || init_lam) return ACM_ERR_ARG;  // warm starts are taken in the FP32 or FP64 modes
-    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, e32, nullptr, nullptr));
+    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, e32, nullptr, nullptr, nullptr, STALL_WINDOW));
     CKS(stokes_iterate<float>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     std::vector<StokesDev> hp(nprob);
     CK(cudaMemcpy(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost));
@@ -744,7 +783,8 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
     for (int p = 0; p < nprob; ++p) {
       it32[p] = hp[p].iter;
       it32_min = std::min(it32_min, it32[p]);
-      ok = ok && hp[p].status == ACM_OK;
+      // a problem stopped at the FP32 rounding floor continues in FP64
+      ok = ok && (hp[p].status == ACM_OK || hp[p].status == ST_STALLED);
     }
     if (ok && P.eps < e32) {
       CKS(stokes_promote(c, nprob, P.eps));
@@ -797,15 +837,38 @@ acm_status perm_grad(acm_ctx* c, const uint8_t* Hdev, int deriv, double Kg[9]) {
 // ---------------------------------------------------------------------------
 // solute (Section 3.2, Algorithm 1 Problem 2)
 // ---------------------------------------------------------------------------
+// One solute iteration of nprob problems (Algorithm 1, Problem 2): the x pass
+// with the local terms of Eq. 18, the y forward pass, the z pass with Eq. 20
+// and the Eq. 19 residuals, the y inverse pass, and the FP64 finalize.
 template <typename T>
-acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us,
-                      const double (*gchi)[3], double Pe, const acm_advdiff_params& P, double eps, bool setup,
-                      const double* B0, const double* ubar, int iters_done = 0) {
-  CKS(ensure_prec<T>(c));
+acm_status solute_body(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us, const Sym<T>& sym) {
   Prec& w = prec<T>(c);
   Geo g = c->g;
   g.hs = 0;
   g.us = us;
+  const int nbz = Ops<T>::z_blocks(g, P_SOLUTE);
+  const long long ps = 4 * g.S;
+  // spectral components per problem: x -> (tau_0, tau_1, s + d2 tau_2), y forward -> (tau_0, s''),
+  // z -> (d0 chi, chi), y inverse -> (d0 chi, d1 chi, d2 chi)
+  LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym, c->st));
+  LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
+                                     nullptr, c->st));
+  LK(ACM_K_Z_SOLUTE, Ops<T>::pass(g, 0, P_SOLUTE, 2, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm,
+                                  c->part_z, c->st));
+  LK(ACM_K_Y_INV_SOLUTE, Ops<T>::pass(g, 1, P_INV_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
+                                     nullptr, c->st));
+  LK(ACM_K_FINALIZE, solute_finalize(nprob, c->cprm, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
+  return ACM_OK;
+}
+
+// stall_win > 0: an FP32 phase that stops at its rounding floor (see StokesDev)
+template <typename T>
+acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us,
+                      const double (*gchi)[3], double Pe, const acm_advdiff_params& P, double eps, bool setup,
+                      const double* B0, const double* ubar, int iters_done = 0, int stall_win = 0) {
+  CKS(ensure_prec<T>(c));
+  Prec& w = prec<T>(c);
+  const Geo& g = c->g;
   const size_t cs = 2 * sizeof(T);
   const Sym<T> sym = sym_of<T>(c, P.deriv);
   c->solute_deriv = P.deriv;
@@ -830,29 +893,41 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
       d.Fc = Pe * ug;
       d.max_iter = P.max_iter;
       d.rmin = 1e300;
+      d.stall_win = stall_win;
+      d.stall_best = 1e300;
     }
     CK(cudaMemcpyAsync(c->cprm, hp.data(), nprob * sizeof(SoluteDev), cudaMemcpyHostToDevice, c->st));
   }
-  const int nbz = Ops<T>::z_blocks(g, P_SOLUTE);
-  const long long ps = 4 * g.S;
+  int remaining = P.max_iter - (setup ? 0 : iters_done);
+  if (remaining <= 0) return ACM_OK;
+  if (P.device_loop && !c->prof) {
+    // the whole loop as one device-resident graph launch
+    GraphKey key;
+    key.prec = (int)sizeof(T);
+    key.nprob = nprob;
+    key.deriv = P.deriv;
+    key.kind = 2;
+    key.cap = (unsigned)remaining;
+    key.kp = udev;
+    key.kq = Hdev;
+    key.kx = us;
+    std::vector<acm_ctx*> ctxs = {c};
+    LoopCtl lc = {};
+    lc.base[0] = (const char*)c->cprm;
+    lc.n[0] = nprob;
+    lc.stride[0] = (int)sizeof(SoluteDev);
+    lc.ngroups = 1;
+    lc.done_off = (int)offsetof(SoluteDev, done);
+    auto capture = [&]() -> acm_status { return solute_body<T>(c, nprob, Hdev, udev, us, sym); };
+    return graph_loop_run(c->graph_sol, key, ctxs, capture, lc, c->st);
+  }
+  // host-launched chunks of check_every iterations; the stop flags are read between chunks
   CKS(pin_scratch(c, (size_t)c->B * sizeof(SoluteDev)));
   const int ce = P.check_every < 1 ? 1 : P.check_every;
-  int remaining = P.max_iter - (setup ? 0 : iters_done);
   while (remaining > 0) {
     const int chunk = ce < remaining ? ce : remaining;
     remaining -= chunk;
-    for (int k = 0; k < chunk; ++k) {
-      // spectral components per problem: x -> (tau_0, tau_1, s + d2 tau_2), y forward -> (tau_0, s''),
-      // z -> (d0 chi, chi), y inverse -> (d0 chi, d1 chi, d2 chi)
-      LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym, c->st));
-      LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
-                      nullptr, c->st));
-      LK(ACM_K_Z_SOLUTE, Ops<T>::pass(g, 0, P_SOLUTE, 2, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm, c->part_z,
-                      c->st));
-      LK(ACM_K_Y_INV_SOLUTE, Ops<T>::pass(g, 1, P_INV_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
-                      nullptr, c->st));
-      LK(ACM_K_FINALIZE, solute_finalize(nprob, c->cprm, c->part_z, nbz, (double)g.V, c->hist, HIST_CAP, c->st));
-    }
+    for (int k = 0; k < chunk; ++k) CKS(solute_body<T>(c, nprob, Hdev, udev, us, sym));
     CK(cudaMemcpyAsync(c->pin, c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     const SoluteDev* hp = (const SoluteDev*)c->pin;
@@ -915,6 +990,7 @@ acm_status solute_promote(acm_ctx* c, int nprob, double eps) {
     x.converged = 0;
     x.status = 0;
     x.eps = eps;
+    x.stall_win = 0;
   }
   CK(cudaMemcpyAsync(c->cprm, hp.data(), nprob * sizeof(SoluteDev), cudaMemcpyHostToDevice, c->st));
   return ACM_OK;
@@ -957,7 +1033,7 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
   acm_advdiff_default_params(&P);
   if (prm) P = *prm;
   if (!u || !(P.A0 > 0) || !(P.eta >= 0) || !(P.eps >= 0) || P.max_iter < 1 || (P.deriv != 0 && P.deriv != 1) ||
-      P.precision < 0 || P.precision > 2 || !std::isfinite(Pe))
+      P.precision < 0 || P.precision > 2 || !std::isfinite(Pe) || (P.device_loop != 0 && P.device_loop != 1))
     return ACM_ERR_ARG;
   const double t0 = now_ms();
   const uint8_t* Hdev = nullptr;
@@ -1022,7 +1098,7 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
     CKS(ensure_prec<float>(c));
     LK(ACM_K_OTHER, convert_d2f((const double*)ud, (float*)c->pf.u, 3 * g.V, c->st));
     const double e32 = P.eps < 1e-5 ? 1e-5 : P.eps;
-    CKS(solute_run<float>(c, nprob, Hdev, c->pf.u, 0, gchi, Pe, P, e32, true, B0, ubar));
+    CKS(solute_run<float>(c, nprob, Hdev, c->pf.u, 0, gchi, Pe, P, e32, true, B0, ubar, 0, STALL_WINDOW));
     std::vector<SoluteDev> hp(nprob);
     CK(cudaMemcpy(hp.data(), c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost));
     std::vector<int> it32(nprob);
@@ -1031,7 +1107,8 @@ acm_status advdiff_solve(acm_ctx* c, int nprob, const uint8_t* H, const void* u,
     for (int p = 0; p < nprob; ++p) {
       it32[p] = hp[p].iter;
       it32_min = std::min(it32_min, it32[p]);
-      ok = ok && hp[p].status == ACM_OK;
+      // a problem stopped at the FP32 rounding floor continues in FP64
+      ok = ok && (hp[p].status == ACM_OK || hp[p].status == ST_STALLED);
     }
     CKS(solute_promote(c, nprob, P.eps));
     const bool refine = ok && P.eps < e32;
@@ -1253,10 +1330,7 @@ acm_status autotune_ctx(acm_ctx* c, int nprob, int deriv) {
     return st;
   }
   // a captured loop holds the old launches
-  if (c->graph.exec) {
-    cudaGraphExecDestroy(c->graph.exec);
-    c->graph.exec = nullptr;
-  }
+  drop_graphs(c);
   CK(cudaStreamSynchronize(c->st));
   return ACM_OK;
 }
@@ -1315,6 +1389,7 @@ acm_status ctx_create(acm_ctx** out, int n0, int n1, int n2, void* stream, int B
             cudaMalloc(&c->Hb, (size_t)ncells * g.V / 8) == cudaSuccess &&
             cudaMalloc(&c->cnt, sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&c->graph.counter, sizeof(unsigned int)) == cudaSuccess &&
+            cudaMalloc(&c->graph_sol.counter, sizeof(unsigned int)) == cudaSuccess &&
             cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess &&
             cudaMalloc(&c->hist, (size_t)BMAX * HIST_CAP * STOKES_HIST * sizeof(double)) == cudaSuccess;
   if (!ok) {
@@ -1371,6 +1446,7 @@ acm_status acm_advdiff_default_params(acm_advdiff_params* p) {
   p->deriv = ACM_DERIV_CENTRAL;
   p->precision = ACM_FP32;
   p->check_every = 16;
+  p->device_loop = 1;
   return ACM_OK;
 }
 
@@ -1384,10 +1460,10 @@ acm_status acm_destroy(acm_ctx* c) {
   else cudaDeviceSynchronize();
   free_prec(c->pf);
   free_prec(c->pd);
-  if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+  drop_graphs(c);
   if (c->cap) cudaStreamDestroy(c->cap);
   void* ps[] = {c->sprm, c->cprm, c->part_x, c->part_z, c->part_r, c->Hd, c->Hb, c->cnt, c->hist, c->hist_b,
-                c->graph.counter};
+                c->graph.counter, c->graph_sol.counter};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (c->pin) cudaFreeHost(c->pin);
@@ -1674,10 +1750,7 @@ acm_status acm_set_tiles(acm_ctx* c, int fp64, const int tiles[NTUNE]) {
     if (!found) return ACM_ERR_ARG;
   }
   c->g = g;
-  if (c->graph.exec) {
-    cudaGraphExecDestroy(c->graph.exec);
-    c->graph.exec = nullptr;
-  }
+  drop_graphs(c);
   return ACM_OK;
 }
 

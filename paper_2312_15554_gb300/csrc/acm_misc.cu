@@ -17,6 +17,21 @@ __device__ __forceinline__ void sum_partials(const double* __restrict__ part, in
   __syncthreads();
 }
 
+// Stagnation test of an FP32 phase (off when win = 0): the distance to the
+// tolerance m = max_k r[k] / t[k] must fall below STALL_DROP times its best
+// value within `win` iterations, else the phase has reached its rounding floor.
+__device__ __forceinline__ bool stalled(int win, int& n, double& best, const double* r, const double* t, int k) {
+  if (win <= 0) return false;
+  double m = 0.0;
+  for (int i = 0; i < k; ++i) m = fmax(m, t[i] > 0.0 ? r[i] / t[i] : r[i]);
+  if (m < STALL_DROP * best) {
+    best = m;
+    n = 0;
+    return false;
+  }
+  return ++n >= win;
+}
+
 __global__ void __launch_bounds__(256) k_stokes_finalize(StokesDev* __restrict__ prm, const double* __restrict__ part_x,
                                                         int nbx, const double* __restrict__ part_z, int nbz,
                                                         double V, double* __restrict__ hist, int hist_cap) {
@@ -83,6 +98,9 @@ __global__ void __launch_bounds__(256) k_stokes_finalize(StokesDev* __restrict__
     P->done = 1;
     P->converged = 1;
     P->status = ST_OK;
+  } else if (stalled(P->stall_win, P->stall_n, P->stall_best, r, t, 6)) {
+    P->done = 1;
+    P->status = ST_STALLED;
   } else if (it >= P->max_iter) {
     P->done = 1;
     P->status = ST_MAXITER;
@@ -131,6 +149,12 @@ __global__ void __launch_bounds__(256) k_solute_finalize(SoluteDev* __restrict__
     return;
   }
   if (rn < P->rmin) P->rmin = rn;
+  const double rr[2] = {r1, r2}, tt[2] = {t1, t2};
+  if (stalled(P->stall_win, P->stall_n, P->stall_best, rr, tt, 2)) {
+    P->done = 1;
+    P->status = ST_STALLED;
+    return;
+  }
   if (it >= P->max_iter) {
     P->done = 1;
     P->status = ST_MAXITER;

@@ -78,8 +78,11 @@ acm_status setup_current_device(int dev, DeviceSetup** out) {
       h32[2 * k] = (float)h64[2 * k];
       h32[2 * k + 1] = (float)h64[2 * k + 1];
     }
+    // a copy from pageable memory may return before its DMA lands; the device
+    // synchronisation orders the tables before work on any (non-blocking) stream
     if (cudaMemcpy(s.tw64, h64, sizeof(h64), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s.tw32, h32, sizeof(h32), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(s.tw32, h32, sizeof(h32), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
       cudaGetLastError();
       return ACM_ERR_CUDA;
     }
@@ -89,13 +92,15 @@ acm_status setup_current_device(int dev, DeviceSetup** out) {
   return ACM_OK;
 }
 
-bool on_device(const void* p) {
+// device memory of the current device `dev` (the kernels run there and read
+// and write the buffers directly), or managed memory
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
 }
 
 template <typename T>
@@ -134,12 +139,12 @@ extern "C" acm_status acm_fft_r2c_static(int n0, int n1, int n2, int fp64, const
   g.lph = 1;
   const size_t need = (size_t)g.S * (fp64 ? 2 * sizeof(double) : 2 * sizeof(float));
   if (need > STATIC_SCRATCH_BYTES) return ACM_ERR_UNSUPPORTED_SIZE;
-  if (!on_device(in) || !on_device(out)) return ACM_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
     cudaGetLastError();
     return ACM_ERR_CUDA;
   }
+  if (!on_device(in, dev) || !on_device(out, dev)) return ACM_ERR_ARG;
   DeviceSetup* s = nullptr;
   acm_status st = setup_current_device(dev, &s);
   if (st != ACM_OK) return st;

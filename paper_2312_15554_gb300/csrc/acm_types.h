@@ -24,7 +24,11 @@ struct StokesDev {
   double mean_u[3];    // k = 0 tap of the last Green step (volume average of u)
   int iter, done, status, converged;
   int iter_base;       // iterations of earlier phases (history indexing)
-  int pad_;
+  // stagnation of an FP32 phase (stall_win > 0): the solve stops with
+  // ST_STALLED when max_k res[k] / tol[k] has not fallen below STALL_DROP times
+  // its best value for stall_win iterations (its FP32 rounding floor)
+  int stall_win, stall_n;
+  double stall_best;
 };
 
 struct SoluteDev {
@@ -35,11 +39,19 @@ struct SoluteDev {
   double res[2], tol[2];
   double rmin;
   int iter, done, status, converged;
-  int iter_base, pad_;
+  int iter_base;
+  int stall_win, stall_n;  // as in StokesDev
+  double stall_best;
 };
+
+// improvement factor that resets the stagnation count of an FP32 phase
+constexpr double STALL_DROP = 0.98;
 
 // status codes mirrored from acm.h
 enum { ST_OK = 0, ST_MAXITER = -4, ST_DIVERGED = -5, ST_NONFINITE = -6 };
+// internal: an FP32 phase stopped at its rounding floor (the driver continues
+// that problem in FP64; never returned to the caller)
+enum { ST_STALLED = -100 };
 
 // Geometry of one grid and its half spectrum.
 struct Geo {

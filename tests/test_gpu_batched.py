@@ -66,3 +66,58 @@ def test_batched_degenerate_cell_is_reported_not_iterated(lib):
     assert np.isfinite(K[0]).all() and np.isnan(K[1]).all()
     assert all(r.status == -7 and r.iters == 0 for r in reps[1])
     assert all(r.status in (0, -4) for r in reps[0])
+
+
+def test_batched_cells_of_the_c3_recipe_match_the_oracle(lib):
+    """Two 64^3 and two 128^3 cells of the batched workload's recipe (porosity
+    U[0.2, 0.6], sphere radii U[3, 10] voxels), all three loads of every cell in
+    one device-resident graph, fixed penalties, 8 ADMM iterations from rest: u
+    and H lambda of every load against the FP64 oracle, element by element."""
+    from oracle import acm_oracle as Ora
+    shapes = [(64, 64, 64), (128, 128, 128), (64, 64, 64), (128, 128, 128)]
+    Hs = []
+    for i, sh in enumerate(shapes):
+        por, radii = I.cell_recipe(5000 + i)
+        Hs.append(I.sphere_pack(sh, por, radii, 5000 + i)[0])
+    n_it = 8
+    prm = lib.stokes_params(precision=lib.FP32, eps=0.0, adaptive=0, max_iter=n_it, device_loop=1)
+    batch = lib.acm_batch(shapes)
+    u_out = [torch.zeros((3, 3) + sh, dtype=torch.float32, device=DEV) for sh in shapes]
+    l_out = [torch.zeros((3, 3) + sh, dtype=torch.float32, device=DEV) for sh in shapes]
+    s, K, reps = lib.acm_batch_stokes(batch, [torch.as_tensor(h, device=DEV) for h in Hs], prm, u_out,
+                                      lambda_out=l_out)
+    torch.cuda.synchronize()
+    batch.close()
+    for i, H in enumerate(Hs):
+        assert all(r.iters == n_it for r in reps[i])
+        for j in range(3):
+            R = Ora.stokes(H, np.eye(3)[j], Ora.StokesParams(eps=0.0, adaptive=False, max_iter=n_it))
+            u = u_out[i][j].cpu().numpy()
+            lam = l_out[i][j].cpu().numpy()
+            assert np.abs(u - R.state.u).max() < 1e-5 * np.abs(R.state.u).max(), (i, j)
+            assert np.abs(lam - R.state.lam).max() < 1e-5 * np.abs(R.state.lam).max(), (i, j)
+            np.testing.assert_allclose(K[i][:, j], R.K_col, rtol=0, atol=1e-5 * np.abs(R.K_col).max())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_solute_device_loop_equals_host_loop(lib, precision):
+    """The solute loop as one graph launch runs the same kernels in the same
+    order as the host-launched chunks: identical fields, iteration counts, D."""
+    H = I.sphere_pack((32, 16, 32), 0.45, 3.5, 22)[0]
+    shape = H.shape
+    p = lib.FP64 if precision == "fp64" else lib.FP32
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    u = torch.as_tensor(0.05 * I.random_field((3,) + shape, 23) * (1 - H)[None], dtype=dt, device=DEV)
+    out = []
+    for dl in (1, 0):
+        ctx = lib.acm_ctx(shape)
+        chi3 = torch.zeros((3,) + shape, dtype=dt, device=DEV)
+        s, D, Dx, reps = lib.acm_advdiff_tensor(ctx, torch.as_tensor(H, device=DEV), u, 10.0, lib.advdiff_params(
+            precision=p, eps=1e-7, max_iter=3000, device_loop=dl, check_every=7), chi3)
+        torch.cuda.synchronize()
+        ctx.close()
+        assert all(r.converged for r in reps)
+        out.append(([r.iters for r in reps], chi3.cpu().numpy(), D))
+    assert out[0][0] == out[1][0]
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    np.testing.assert_array_equal(out[0][2], out[1][2])

@@ -4,6 +4,8 @@ Tolerances: FP64 paths agree with the oracle to 1e-10 relative to the field's
 largest magnitude (rounding order only); FP32 fields to 1e-5 relative; converged
 permeability and diffusivity to 1e-6 relative.
 """
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -75,6 +77,8 @@ def test_fft_r2c_c2r_matches_oracle_transform(lib, shape, fp64):
 # the x passes are specialised per line length n2: 8 (one lane, 4 elements),
 # 16 and 32 (one lane), 64 (four lanes), 512 (sixteen lanes) are covered here,
 # 128 and 256 by the bench-workload test below
+RES_ERR = {}
+
 CASES = [
     ("sphere16", lambda: I.single_sphere((16, 16, 16), 0.3)),
     ("rand8x16x32", lambda: I.random_indicator((8, 16, 32), 0.35, 4)),
@@ -100,10 +104,23 @@ def test_stokes_fixed_iterations_match_oracle(lib, case, deriv, fp64):
     assert relerr(u, R.state.u) < tol
     assert relerr(p, R.p) < tol
     assert relerr(lam, R.state.lam) < tol
-    # residuals are norms of differences of consecutive iterates: FP32 cancellation
-    # leaves them at ~1e-4 relative, FP64 at rounding level
+    # residuals are norms of differences of consecutive iterates and of small
+    # constraint violations: FP32 rounding of the fields enters them relative
+    # to the fields, not to the residuals themselves (measured bound below)
+    rerr = float(np.max(np.abs(np.asarray(rep.res[:6]) - R.residuals[-1]) / R.residuals[-1]))
+    RES_ERR[(case[0], deriv, fp64)] = rerr
     np.testing.assert_allclose(rep.res[:6], R.residuals[-1], rtol=1e-8 if fp64 else 2e-3)
     assert relerr(K, R.state.u.reshape(3, -1).mean(axis=1)) < (1e-10 if fp64 else 1e-5)
+
+
+def test_report_fp32_residual_errors(capsys):
+    """Prints the worst relative error of the FP32 residuals seen above."""
+    errs = {k: v for k, v in RES_ERR.items() if not k[2]}
+    if errs:
+        worst = max(errs.items(), key=lambda kv: kv[1])
+        with capsys.disabled():
+            print(f"\nFP32 Eq. 10 residuals against the oracle after 12 iterations: worst relative error "
+                  f"{worst[1]:.2e} ({worst[0][0]}, deriv {worst[0][1]}); median {np.median(list(errs.values())):.2e}")
 
 
 def test_stokes_adaptive_penalties_follow_the_oracle_fp64(lib):
@@ -294,19 +311,53 @@ def test_no_solid_no_flow_identity_diffusivity(lib):
     np.testing.assert_allclose(D, np.eye(3), atol=1e-13)
 
 
+@functools.lru_cache(maxsize=2)
+def bench_pack_and_flow(n):
+    """The bench's Boolean sphere pack at n^3 (radius 8 voxels at 256^3,
+    porosity 0.35) and the oracle's e_0 flow two ADMM iterations from rest."""
+    H = I.sphere_pack((n, n, n), 0.35, 8.0 * n / 256, 2024)[0]
+    R = O.stokes(H, [1.0, 0.0, 0.0], O.StokesParams(eps=0.0, adaptive=True, max_iter=2))
+    return H, R
+
+
 @pytest.mark.parametrize("n", [128, 256])
 def test_bench_workload_first_iterations_match_oracle(lib, n):
-    """The bench's Boolean sphere pack (radius 8 voxels at 256^3, porosity 0.35):
-    the FP32 path in the bench's launch configuration against the oracle, two
-    iterations from rest, element by element."""
-    H = I.sphere_pack((n, n, n), 0.35, 8.0 * n / 256, 2024)[0]
-    g = [1.0, 0.0, 0.0]
-    n_it = 2
-    R = O.stokes(H, g, O.StokesParams(eps=0.0, adaptive=True, max_iter=n_it))
-    s, K, rep, u, p, lam = run_stokes(lib, H, g, False, eps=0.0, adaptive=1, max_iter=n_it)
+    """The bench's pack: the FP32 Stokes path in the bench's launch
+    configuration against the oracle, two iterations from rest, element by element."""
+    H, R = bench_pack_and_flow(n)
+    s, K, rep, u, p, lam = run_stokes(lib, H, [1.0, 0.0, 0.0], False, eps=0.0, adaptive=1, max_iter=2)
     assert relerr(u, R.state.u) < 1e-5
     assert relerr(lam, R.state.lam) < 1e-5
     assert relerr(p, R.p) < 1e-5
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_bench_workload_solute_matches_oracle(lib, n):
+    """The bench's solute step at full size (x lines of 128 / 256, strided
+    passes of 128 / 256): the three composition loads advected by the pack's
+    flow at Pe 10 with the library defaults (Eq. 21 symbols, B0 the mean of B,
+    A0 0.55), three Lippmann-Schwinger iterations in FP32 against the FP64
+    oracle, element by element: chi of every load and grad chi of load e_0
+    within 1e-5, D and the extended-domain D within 1e-6."""
+    H, R = bench_pack_and_flow(n)
+    u = R.state.u
+    Pe, n_it = 10.0, 3
+    Dm, Dxm, res = O.diffusivity_tensor(H, u, Pe, O.AdvDiffParams(eps=0.0, max_iter=n_it))
+    ctx = lib.acm_ctx(H.shape)
+    Hd = dev(H, torch.uint8)
+    ud = dev(u, torch.float32)
+    prm = lib.advdiff_params(eps=0.0, max_iter=n_it)
+    chi3 = torch.zeros((3,) + H.shape, dtype=torch.float32, device=DEV)
+    s, D, Dx, reps = lib.acm_advdiff_tensor(ctx, Hd, ud, Pe, prm, chi3)
+    assert s == lib.ACM_ERR_MAXITER and all(r.iters == n_it for r in reps)
+    assert relerr(chi3.cpu().numpy(), np.stack([r.chi for r in res])) < 1e-5
+    assert relerr(D, Dm) < 1e-6
+    assert relerr(Dx, Dxm) < 1e-6
+    grad = torch.zeros((3,) + H.shape, dtype=torch.float32, device=DEV)
+    s, Dg, Dgx, rep = lib.acm_advdiff(ctx, Hd, ud, Pe, [1.0, 0.0, 0.0], prm, None, grad)
+    ctx.close()
+    assert relerr(grad.cpu().numpy(), res[0].grad_chi) < 1e-5
+    assert relerr(Dg, res[0].Dg) < 1e-6
 
 
 def test_history_records_the_oracle_residuals_and_mean_velocity(lib):

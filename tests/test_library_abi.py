@@ -72,3 +72,27 @@ def test_product_path_has_no_fallback():
             acm.load("/nonexistent/libacm.so")
         finally:
             acm._LIB = saved
+
+
+def test_static_transform_binding_checks_buffers_before_the_call(libpath):
+    """acm_fft_r2c_static cannot see buffer sizes or dtypes through the C ABI,
+    so the binding rejects mismatched tensors before calling the library."""
+    import torch
+
+    from paper_2312_15554_gb300 import acm
+    acm.load(libpath)
+    x = torch.zeros((8, 8, 8), dtype=torch.float32)
+    good = torch.zeros((8, 8, 5, 2), dtype=torch.float32)
+    with pytest.raises(ValueError):   # fp64 flag with a float32 field
+        acm.acm_fft_r2c_static(x, good, True)
+    with pytest.raises(ValueError):   # output one column short
+        acm.acm_fft_r2c_static(x, torch.zeros((8, 8, 4, 2), dtype=torch.float32), False)
+    with pytest.raises(ValueError):   # output of another dtype
+        acm.acm_fft_r2c_static(x, torch.zeros((8, 8, 5, 2), dtype=torch.float64), False)
+    with pytest.raises(ValueError):   # non-contiguous input
+        acm.acm_fft_r2c_static(torch.zeros((8, 8, 16))[:, :, ::2], good, False)
+    with pytest.raises(ValueError):   # not a 3-D field
+        acm.acm_fft_r2c_static(torch.zeros((2, 8, 8, 8)), good, False)
+    with pytest.raises(ValueError):   # numpy arrays are host memory without a device
+        import numpy as np
+        acm.acm_fft_r2c_static(np.zeros((8, 8, 8), np.float32), np.zeros((8, 8, 5, 2), np.float32), False)

@@ -46,14 +46,44 @@ def test_static_transform_matches_context_transform_twice(lib, shape, fp64):
         assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("shape,fp64", [((512, 512, 8), False), ((256, 512, 8), True)])
+def test_static_transform_at_the_scratch_limit_matches_the_oracle_transform(lib, shape, fp64):
+    """Grids whose working spectrum n0 * n1 * (n2/2 + 4) fills the 16 MiB array
+    exactly, twice in a row, against the oracle's own transform."""
+    from oracle import fft as OF
+    dt = torch.float64 if fp64 else torch.float32
+    tol = 1e-12 if fp64 else 2e-6
+    for seed in (5, 6):
+        xh = I.random_field(shape, seed)
+        x = torch.as_tensor(xh, dtype=dt, device=DEV)
+        out = torch.full(shape[:2] + (shape[2] // 2 + 1, 2), float("nan"), dtype=dt, device=DEV)
+        lib.acm_fft_r2c_static(x, out, fp64)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        got = got[..., 0] + 1j * got[..., 1]
+        ref = OF.rfftn(np.asarray(x.cpu().numpy(), dtype=np.float64))
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("shape,fp64", [((128, 256, 128), False), ((64, 256, 128), True),
+                                        ((128, 128, 128), True), ((512, 512, 16), False)])
+def test_static_transform_rejects_grids_just_beyond_the_scratch(lib, shape, fp64):
+    dt = torch.float64 if fp64 else torch.float32
+    x = torch.zeros(shape, dtype=dt, device=DEV)
+    out = torch.zeros(shape[:2] + (shape[2] // 2 + 1, 2), dtype=dt, device=DEV)
+    with pytest.raises(lib.AcmError) as e:
+        lib.acm_fft_r2c_static(x, out, fp64)
+    assert e.value.status == -10
+
+
 def test_static_transform_rejects_oversized_grids_and_host_buffers(lib):
     x = torch.zeros((256, 256, 256), dtype=torch.float32, device=DEV)
     out = torch.zeros((256, 256, 129, 2), dtype=torch.float32, device=DEV)
     with pytest.raises(lib.AcmError) as e:
         lib.acm_fft_r2c_static(x, out, False)
     assert e.value.status == -10              # beyond the fixed scratch size
-    xh = np.zeros((16, 16, 16), np.float32)
-    oh = np.zeros((16, 16, 9, 2), np.float32)
-    with pytest.raises(lib.AcmError) as e:
-        lib.acm_fft_r2c_static(xh, oh, False)
-    assert e.value.status == -1               # host buffers would need staging memory
+    # host buffers would need staging memory: the C entry point refuses them
+    xh = torch.zeros((16, 16, 16), dtype=torch.float32).pin_memory()
+    oh = torch.zeros((16, 16, 9, 2), dtype=torch.float32).pin_memory()
+    s = lib.load().acm_fft_r2c_static(16, 16, 16, 0, lib._ptr(xh), lib._ptr(oh), None)
+    assert s == -1
