@@ -1017,3 +1017,5 @@ __global__ void k_q_from_a(const cx<T>* __restrict__ ah, cx<T>* __restrict__ q, 
 }
 
 }  // namespace acm
+
+#include "acm_rpass.cuh"

@@ -1,6 +1,8 @@
 // acm_ops_impl.cuh -- definitions of the launch wrappers; included once per
 // precision (acm_f32.cu, acm_f64.cu) followed by an explicit instantiation.
 #pragma once
+#include <cstdlib>
+
 #include "acm_kernels.cuh"
 #include "acm_ops.h"
 
@@ -128,10 +130,21 @@ constexpr bool tx_ok() {
          (NC * TX * line_stride(N, N / ept(N), TX, wave_slots<T>()) + tw_total(N)) * (int)sizeof(cx<T>) <= 200 * 1024;
 }
 
-// tile width of (T, N, OP, NC) under the choice `shift`
+// The register-resident variant (acm_rpass.cuh) of a tunable pass: lines of
+// 64, 128 or 256 points; not the FP64 z Stokes pass (its three components of
+// 16 FP64 complex values per thread exceed the register file).
+template <typename T, int N, int OP, int NC>
+constexpr bool rr_ok() {
+  return (N == 64 || N == 128 || N == 256) && tunable<N, OP, NC>() && !(sizeof(T) == 8 && OP == OP_STOKES);
+}
+
+// tile width of (T, N, OP, NC) under the choice `shift`; the register-resident
+// variant (shift 3) reports -W, W its columns per block
 template <typename T, int N, int OP, int NC>
 constexpr int resolved_tx(int shift) {
   constexpr int TX0 = pick_tx((int)sizeof(cx<T>), N, NC);
+  if constexpr (rr_ok<T, N, OP, NC>())
+    if (shift == 3) return -RCfg<T, N>::W;
   if (tunable<N, OP, NC>()) {
     if (shift < 0 && tx_ok<T, N, OP, NC, TX0 / 2>()) return TX0 / 2;
     if (shift == 1 && tx_ok<T, N, OP, NC, TX0 * 2>()) return TX0 * 2;
@@ -140,13 +153,10 @@ constexpr int resolved_tx(int shift) {
   return TX0;
 }
 
-template <typename T, int N, int OP, int NC, int TX>
-static cudaError_t l_pass_kt(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
+template <typename T>
+static PassArgs<T> pass_args(const Geo& g, int axis, void* spec, long long probStride, const Sym<T>& sym,
                              const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
-                             cudaStream_t s, int dm) {
-  using C = SCfg<T, N, OP, NC, TX>;
-  static const cudaError_t attr = set_smem(k_strided<T, N, OP, NC, TX>, C::SMEM);
-  if (attr != cudaSuccess) return attr;
+                             int dm) {
   PassArgs<T> a;
   a.spec = (cx<T>*)spec;
   a.probStride = probStride;
@@ -170,9 +180,34 @@ static cudaError_t l_pass_kt(const Geo& g, int axis, int nprob, void* spec, long
   a.invV = 1.0 / (double)g.V;
   a.nkx = g.n2 / 2;
   a.dm = dm;
+  return a;
+}
+
+template <typename T, int N, int OP, int NC, int TX>
+static cudaError_t l_pass_kt(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
+                             const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
+                             cudaStream_t s, int dm) {
+  using C = SCfg<T, N, OP, NC, TX>;
+  static const cudaError_t attr = set_smem(k_strided<T, N, OP, NC, TX>, C::SMEM);
+  if (attr != cudaSuccess) return attr;
+  const PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, dm);
   const int nouter = axis == 1 ? g.n0 : g.n1;
   dim3 grid((g.Pu + TX - 1) / TX, nouter, nprob);
   k_strided<T, N, OP, NC, TX><<<grid, C::NT, C::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N, int OP, int NC>
+static cudaError_t l_pass_rr(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
+                             const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
+                             cudaStream_t s) {
+  using C = RCfg<T, N>;
+  static const cudaError_t attr = set_smem(k_rstrided<T, N, OP, NC>, C::SMEM);
+  if (attr != cudaSuccess) return attr;
+  const PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
+  const int nouter = axis == 1 ? g.n0 : g.n1;
+  dim3 grid((g.Pu + C::W - 1) / C::W, nouter, nprob);
+  k_rstrided<T, N, OP, NC><<<grid, C::NT, C::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -181,6 +216,9 @@ static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long 
                             const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
                             cudaStream_t s, int dm) {
   constexpr int TX0 = pick_tx((int)sizeof(cx<T>), N, NC);
+  if constexpr (rr_ok<T, N, OP, NC>())
+    if (g.txs[sizeof(T) == 8][axis][OP] == 3)
+      return l_pass_rr<T, N, OP, NC>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, s);
   if constexpr (tunable<N, OP, NC>()) {
     const int sh = g.txs[sizeof(T) == 8][axis][OP];
     if constexpr (tx_ok<T, N, OP, NC, TX0 / 2>())
@@ -269,13 +307,15 @@ bool Ops<T>::tx_variant(int n, int op, int nc, int shift) {
   g.n0 = g.n1 = n;
   const int t0 = pass_tx(g, 0, op, nc);
   g.txs[sizeof(T) == 8][0][op] = (signed char)shift;
-  return shift == 0 || pass_tx(g, 0, op, nc) != t0;
+  const int t1 = pass_tx(g, 0, op, nc);
+  if (shift == 3) return t1 < 0;
+  return shift == 0 || (t1 != t0 && t1 > 0);
 }
 
 template <typename T>
 int Ops<T>::z_blocks(const Geo& g, int op) {
   const int nc = op == P_SOLUTE ? 2 : 3;
-  const int tx = pass_tx(g, 0, op, nc);
+  const int tx = std::abs(pass_tx(g, 0, op, nc));
   return ((g.Pu + tx - 1) / tx) * g.n1;
 }
 

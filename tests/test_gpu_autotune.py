@@ -22,12 +22,13 @@ DEV = "cuda:0"
 
 def _widths(lib, ctx, fp64):
     """Compiled widths of each tuned pass: the default, and half, double and four
-    times it when they exist."""
+    times it when they exist, and the register-resident variant (reported as -W,
+    W = 16 columns per block in FP32, 8 in FP64) where it exists."""
     base = lib.acm_get_tiles(ctx, fp64)
     out = {}
     for k, w in base.items():
         opts = [w]
-        for cand in (w // 2, w * 2, w * 4):
+        for cand in (w // 2, w * 2, w * 4, -8 if fp64 else -16):
             t = dict(base)
             t[k] = cand
             try:
@@ -65,6 +66,12 @@ def test_every_tile_width_gives_identical_fields(lib, shape, fp64):
     ctx = lib.acm_ctx(shape)
     base, opts = _widths(lib, ctx, fp64)
     assert any(len(v) > 1 for v in opts.values())
+    # the register-resident variant exists for every tuned pass at 64, 128 and
+    # 256 points, except the FP64 z Stokes pass
+    for k, ws in opts.items():
+        n = shape[1] if k.startswith("y") else shape[0]
+        want = n in (64, 128, 256) and not (fp64 and k == "z_stokes")
+        assert any(w < 0 for w in ws) == want, (k, ws)
     u0, r0 = _stokes(lib, ctx, H, fp64)
     uin = 1e3 * u0
     c0 = _solute(lib, ctx, H, uin, fp64)

@@ -105,11 +105,13 @@ def test_stokes_fixed_iterations_match_oracle(lib, case, deriv, fp64):
     assert relerr(p, R.p) < tol
     assert relerr(lam, R.state.lam) < tol
     # residuals are norms of differences of consecutive iterates and of small
-    # constraint violations: FP32 rounding of the fields enters them relative
-    # to the fields, not to the residuals themselves (measured bound below)
+    # constraint violations: FP32 rounding of the fields (~1e-7 of their size)
+    # enters them relative to the fields, not to the residuals themselves; over
+    # these twelve FP32 cases the worst measured error is 1.1e-4 (sphere16,
+    # exact symbols; median 1.3e-6), held here with a factor ~2 of margin
     rerr = float(np.max(np.abs(np.asarray(rep.res[:6]) - R.residuals[-1]) / R.residuals[-1]))
     RES_ERR[(case[0], deriv, fp64)] = rerr
-    np.testing.assert_allclose(rep.res[:6], R.residuals[-1], rtol=1e-8 if fp64 else 2e-3)
+    np.testing.assert_allclose(rep.res[:6], R.residuals[-1], rtol=1e-8 if fp64 else 2.5e-4)
     assert relerr(K, R.state.u.reshape(3, -1).mean(axis=1)) < (1e-10 if fp64 else 1e-5)
 
 
@@ -320,19 +322,48 @@ def bench_pack_and_flow(n):
     return H, R
 
 
+@functools.lru_cache(maxsize=2)
+def bench_solute_oracle(n):
+    """The oracle's three composition loads on the pack's flow, Pe 10, three iterations."""
+    H, R = bench_pack_and_flow(n)
+    return O.diffusivity_tensor(H, R.state.u, 10.0, O.AdvDiffParams(eps=0.0, max_iter=3))
+
+
+RR_TILES = [-16] * 6          # the register-resident variant of every tuned strided pass (FP32)
+
+
+def bench_ctx(lib, shape, tiles):
+    """A context with the strided passes at their default tile widths, or all
+    in the register-resident variant (the autotuner's usual pick at these sizes)."""
+    ctx = lib.acm_ctx(shape)
+    if tiles == "rr":
+        lib.acm_set_tiles(ctx, RR_TILES, False)
+    return ctx
+
+
+@pytest.mark.parametrize("tiles", ["default", "rr"])
 @pytest.mark.parametrize("n", [128, 256])
-def test_bench_workload_first_iterations_match_oracle(lib, n):
+def test_bench_workload_first_iterations_match_oracle(lib, n, tiles):
     """The bench's pack: the FP32 Stokes path in the bench's launch
     configuration against the oracle, two iterations from rest, element by element."""
     H, R = bench_pack_and_flow(n)
-    s, K, rep, u, p, lam = run_stokes(lib, H, [1.0, 0.0, 0.0], False, eps=0.0, adaptive=1, max_iter=2)
+    ctx = bench_ctx(lib, H.shape, tiles)
+    u = torch.zeros((3,) + H.shape, dtype=torch.float32, device=DEV)
+    p = torch.zeros(H.shape, dtype=torch.float32, device=DEV)
+    lam = torch.zeros((3,) + H.shape, dtype=torch.float32, device=DEV)
+    lib.acm_stokes(ctx, dev(H, torch.uint8), [1.0, 0.0, 0.0], lib.stokes_params(
+        precision=lib.FP32, eps=0.0, adaptive=1, max_iter=2), None, None, u, p, lam)
+    torch.cuda.synchronize()
+    ctx.close()
+    u, p, lam = u.cpu().numpy(), p.cpu().numpy(), lam.cpu().numpy()
     assert relerr(u, R.state.u) < 1e-5
     assert relerr(lam, R.state.lam) < 1e-5
     assert relerr(p, R.p) < 1e-5
 
 
+@pytest.mark.parametrize("tiles", ["default", "rr"])
 @pytest.mark.parametrize("n", [128, 256])
-def test_bench_workload_solute_matches_oracle(lib, n):
+def test_bench_workload_solute_matches_oracle(lib, n, tiles):
     """The bench's solute step at full size (x lines of 128 / 256, strided
     passes of 128 / 256): the three composition loads advected by the pack's
     flow at Pe 10 with the library defaults (Eq. 21 symbols, B0 the mean of B,
@@ -342,8 +373,8 @@ def test_bench_workload_solute_matches_oracle(lib, n):
     H, R = bench_pack_and_flow(n)
     u = R.state.u
     Pe, n_it = 10.0, 3
-    Dm, Dxm, res = O.diffusivity_tensor(H, u, Pe, O.AdvDiffParams(eps=0.0, max_iter=n_it))
-    ctx = lib.acm_ctx(H.shape)
+    Dm, Dxm, res = bench_solute_oracle(n)
+    ctx = bench_ctx(lib, H.shape, tiles)
     Hd = dev(H, torch.uint8)
     ud = dev(u, torch.float32)
     prm = lib.advdiff_params(eps=0.0, max_iter=n_it)
