@@ -180,7 +180,24 @@ static PassArgs<T> pass_args(const Geo& g, int axis, void* spec, long long probS
   a.invV = 1.0 / (double)g.V;
   a.nkx = g.n2 / 2;
   a.dm = dm;
+  a.nouter = axis == 1 ? g.n0 : g.n1;
+  a.nyq_blk = -1;
   return a;
+}
+
+// Grid columns of a register-resident pass: W-column blocks of the first n2/2
+// columns plus one block that packs the Nyquist column of W pencils, when n2/2
+// and the pencil count are multiples of W; otherwise ceil(Pu / W) blocks with a
+// ragged last one.
+template <typename T, int N>
+static int rr_grid_x(const Geo& g, int nouter, int* nyq_blk) {
+  constexpr int W = RCfg<T, N>::W;
+  if ((g.Pu - 1) % W == 0 && nouter % W == 0) {
+    *nyq_blk = (g.Pu - 1) / W;
+    return (g.Pu - 1) / W + 1;
+  }
+  *nyq_blk = -1;
+  return (g.Pu + W - 1) / W;
 }
 
 template <typename T, int N, int OP, int NC, int TX>
@@ -204,9 +221,9 @@ static cudaError_t l_pass_rr(const Geo& g, int axis, int nprob, void* spec, long
   using C = RCfg<T, N>;
   static const cudaError_t attr = set_smem(k_rstrided<T, N, OP, NC>, C::SMEM);
   if (attr != cudaSuccess) return attr;
-  const PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
-  const int nouter = axis == 1 ? g.n0 : g.n1;
-  dim3 grid((g.Pu + C::W - 1) / C::W, nouter, nprob);
+  PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
+  const int gx = rr_grid_x<T, N>(g, a.nouter, &a.nyq_blk);
+  dim3 grid(gx, a.nouter, nprob);
   k_rstrided<T, N, OP, NC><<<grid, C::NT, C::SMEM, s>>>(a);
   return cudaGetLastError();
 }

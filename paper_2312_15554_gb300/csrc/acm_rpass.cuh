@@ -19,7 +19,12 @@
 // warp access: W = 16 in FP32, 8 in FP64) and TL threads per column; thread
 // (col, t) = (tid % W, tid / W). Global loads and stores of a fixed m (or k)
 // are W-column row segments, coalesced. The transposes alternate between two
-// buffers, so one __syncthreads per transform suffices.
+// buffers, so one __syncthreads per transform suffices. When n2/2 and the
+// number of pencils are multiples of W, the lone Nyquist column kx = n2/2 of W
+// consecutive pencils shares one extra block (lane column `col` then takes
+// pencil outer0 + col), instead of a block with one busy column per pencil.
+// All components a thread transforms are requested from global memory before
+// the first transform, so a block keeps its loads in flight while it computes.
 #pragma once
 #include "acm_fft.cuh"
 #include "acm_types.h"
@@ -141,52 +146,76 @@ __global__ void __launch_bounds__(RCfg<T, N>::NT) k_rstrided(PassArgs<T> a) {
   cx<T>* buf1 = buf0 + W * C::BS;
   cx<T>* tw = buf1 + W * C::BS;
   __shared__ double red[4 * 32];
-  const int p = blockIdx.z, outer = blockIdx.y, kx0 = blockIdx.x * W;
-  if (a.sprm && a.sprm[p].done) return;
-  if (a.cprm && a.cprm[p].done) return;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = a.twg[k * (TW_MAX / N)];
+  const int p = blockIdx.z;
   const int col = threadIdx.x % W, t = threadIdx.x / W;
-  const int kx = kx0 + col;
-  const bool ok = kx < a.Pu;
-  cx<T>* base = a.spec + p * a.probStride + outer * a.outerStride + kx;
-  __syncthreads();
+  // the lane column's pencil and kx column: a regular block takes W columns of
+  // pencil blockIdx.y; the Nyquist block (blockIdx.x == a.nyq_blk) takes column
+  // n2/2 of the W pencils W blockIdx.y .. W blockIdx.y + W - 1
+  const bool nyq = (int)blockIdx.x == a.nyq_blk;
+  const int outer = nyq ? (int)blockIdx.y * W + col : (int)blockIdx.y;
+  const int kx = nyq ? a.Pu - 1 : (int)blockIdx.x * W + col;
+  const bool live = !nyq || (int)blockIdx.y * W < a.nouter;
+  const bool ok = live && kx < a.Pu;
+  if ((a.sprm && a.sprm[p].done) || (a.cprm && a.cprm[p].done)) return;
+  if (!live) {
+    // a Nyquist block past the last pencil: only its partial sums (zero) exist
+    if constexpr (OP == OP_STOKES || OP == OP_SOLUTE)
+      if (threadIdx.x < 3) a.part[((long long)p * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x) * 4 +
+                                  threadIdx.x] = 0.0;
+    return;
+  }
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = a.twg[k * (TW_MAX / N)];
+  cx<T>* base = a.spec + p * a.probStride + (long long)outer * a.outerStride + kx;
   cx<T> v[16];
   if constexpr (OP == OP_FWD) {
-#pragma unroll 1
+    // component c + 1 travels while component c is transformed
+    cx<T> w[16];
+    rr_load_x<T, N>(v, base, a.rowStride, t, ok);
+    __syncthreads();
+#pragma unroll
     for (int c = 0; c < NC; ++c) {
-      rr_load_x<T, N>(v, base + c * a.compStride, a.rowStride, t, ok);
-      rr_fft<T, N, -1>(v, (c & 1) ? buf1 : buf0, tw, col, t);
-      rr_store_k<T, N>(v, base + c * a.compStride, a.rowStride, t, ok);
+      cx<T>(&cur)[16] = (c & 1) ? w : v;
+      cx<T>(&nxt)[16] = (c & 1) ? v : w;
+      if (c + 1 < NC) rr_load_x<T, N>(nxt, base + (c + 1) * a.compStride, a.rowStride, t, ok);
+      rr_fft<T, N, -1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
+      rr_store_k<T, N>(cur, base + c * a.compStride, a.rowStride, t, ok);
     }
   } else if constexpr (OP == OP_INV) {
-#pragma unroll 1
+    cx<T> w[16];
+    rr_load_k<T, N>(v, base, a.rowStride, t, ok);
+    __syncthreads();
+#pragma unroll
     for (int c = 0; c < NC; ++c) {
-      rr_load_k<T, N>(v, base + c * a.compStride, a.rowStride, t, ok);
-      rr_ifft<T, N, +1>(v, (c & 1) ? buf1 : buf0, tw, col, t);
-      rr_store_x<T, N>(v, base + c * a.compStride, a.rowStride, t, ok);
+      cx<T>(&cur)[16] = (c & 1) ? w : v;
+      cx<T>(&nxt)[16] = (c & 1) ? v : w;
+      if (c + 1 < NC) rr_load_k<T, N>(nxt, base + (c + 1) * a.compStride, a.rowStride, t, ok);
+      rr_ifft<T, N, +1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
+      rr_store_x<T, N>(cur, base + c * a.compStride, a.rowStride, t, ok);
     }
   } else if constexpr (OP == OP_FWD_SOL) {
     constexpr int TL = N / 16;
+    cx<T> w[16];
     rr_load_x<T, N>(v, base, a.rowStride, t, ok);
+    rr_load_x<T, N>(w, base + a.compStride, a.rowStride, t, ok);
+    __syncthreads();
     rr_fft<T, N, -1>(v, buf0, tw, col, t);
     rr_store_k<T, N>(v, base, a.rowStride, t, ok);
-    cx<T> w[16];
-    rr_load_x<T, N>(w, base + a.compStride, a.rowStride, t, ok);
+    rr_load_x<T, N>(v, base + 2 * a.compStride, a.rowStride, t, ok);
     rr_fft<T, N, -1>(w, buf1, tw, col, t);
 #pragma unroll
     for (int e = 0; e < 16; ++e) w[e] = cscale(mul_i(w[e]), a.sym.d1[rr_krow<TL>(t, e)]);
-    rr_load_x<T, N>(v, base + 2 * a.compStride, a.rowStride, t, ok);
     rr_fft<T, N, -1>(v, buf0, tw, col, t);
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = v[e] + w[e];
     rr_store_k<T, N>(v, base + a.compStride, a.rowStride, t, ok);
   } else if constexpr (OP == OP_INV_SOL) {
     constexpr int TL = N / 16;
+    cx<T> b[16];
     rr_load_k<T, N>(v, base, a.rowStride, t, ok);
+    rr_load_k<T, N>(b, base + a.compStride, a.rowStride, t, ok);
+    __syncthreads();
     rr_ifft<T, N, +1>(v, buf0, tw, col, t);
     rr_store_x<T, N>(v, base, a.rowStride, t, ok);
-    cx<T> b[16];
-    rr_load_k<T, N>(b, base + a.compStride, a.rowStride, t, ok);
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = cscale(mul_i(b[e]), a.sym.d1[rr_krow<TL>(t, e)]);
     rr_ifft<T, N, +1>(v, buf1, tw, col, t);
@@ -202,10 +231,10 @@ __global__ void __launch_bounds__(RCfg<T, N>::NT) k_rstrided(PassArgs<T> a) {
     constexpr int NIN = OP == OP_STOKES ? 3 : 2;
     cx<T> u[NIN][16];
 #pragma unroll
-    for (int c = 0; c < NIN; ++c) {
-      rr_load_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
-      rr_fft<T, N, -1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
-    }
+    for (int c = 0; c < NIN; ++c) rr_load_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) rr_fft<T, N, -1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
     const T invV = (T)a.invV;
     const int ky = outer;
     const T d1 = a.sym.d1[ky], l1 = a.sym.l1[ky];
@@ -217,6 +246,7 @@ __global__ void __launch_bounds__(RCfg<T, N>::NT) k_rstrided(PassArgs<T> a) {
     // read before it is rewritten in place, in chunks of CH
     constexpr int CH = 4;
     const long long gst = (long long)p * a.compStride + (long long)outer * a.outerStride + kx;
+    // (the state of problem p sits at p * S: a.compStride is S)
     if constexpr (OP == OP_STOKES) {
       const T nu = (T)a.sprm[p].nu, beta = (T)a.sprm[p].psi[1], b = (T)a.sprm[p].psi[2];
 #pragma unroll

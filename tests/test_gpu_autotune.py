@@ -60,7 +60,7 @@ def _solute(lib, ctx, H, u, fp64):
 
 
 @pytest.mark.parametrize("fp64", [False, True])
-@pytest.mark.parametrize("shape", [(64, 64, 64), (128, 64, 32)])
+@pytest.mark.parametrize("shape", [(64, 64, 64), (128, 64, 32), (128, 64, 16)])
 def test_every_tile_width_gives_identical_fields(lib, shape, fp64):
     H = I.sphere_pack(shape, 0.5, 4.0, 3)[0]
     ctx = lib.acm_ctx(shape)
