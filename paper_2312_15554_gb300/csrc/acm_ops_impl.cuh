@@ -139,12 +139,15 @@ constexpr bool rr_ok() {
 }
 
 // tile width of (T, N, OP, NC) under the choice `shift`; the register-resident
-// variant (shift 3) reports -W, W its columns per block
+// variants (shift 3: W = rr_wdef, shift 4: W = rr_wdef / 2 columns per block)
+// report -W
 template <typename T, int N, int OP, int NC>
 constexpr int resolved_tx(int shift) {
   constexpr int TX0 = pick_tx((int)sizeof(cx<T>), N, NC);
-  if constexpr (rr_ok<T, N, OP, NC>())
-    if (shift == 3) return -RCfg<T, N>::W;
+  if constexpr (rr_ok<T, N, OP, NC>()) {
+    if (shift == 3) return -rr_wdef<T>();
+    if (shift == 4) return -rr_wdef<T>() / 2;
+  }
   if (tunable<N, OP, NC>()) {
     if (shift < 0 && tx_ok<T, N, OP, NC, TX0 / 2>()) return TX0 / 2;
     if (shift == 1 && tx_ok<T, N, OP, NC, TX0 * 2>()) return TX0 * 2;
@@ -189,9 +192,8 @@ static PassArgs<T> pass_args(const Geo& g, int axis, void* spec, long long probS
 // columns plus one block that packs the Nyquist column of W pencils, when n2/2
 // and the pencil count are multiples of W; otherwise ceil(Pu / W) blocks with a
 // ragged last one.
-template <typename T, int N>
+template <int W>
 static int rr_grid_x(const Geo& g, int nouter, int* nyq_blk) {
-  constexpr int W = RCfg<T, N>::W;
   if ((g.Pu - 1) % W == 0 && nouter % W == 0) {
     *nyq_blk = (g.Pu - 1) / W;
     return (g.Pu - 1) / W + 1;
@@ -214,17 +216,17 @@ static cudaError_t l_pass_kt(const Geo& g, int axis, int nprob, void* spec, long
   return cudaGetLastError();
 }
 
-template <typename T, int N, int OP, int NC>
+template <typename T, int N, int OP, int NC, int W>
 static cudaError_t l_pass_rr(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
                              const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
                              cudaStream_t s) {
-  using C = RCfg<T, N>;
-  static const cudaError_t attr = set_smem(k_rstrided<T, N, OP, NC>, C::SMEM);
+  using C = RCfg<T, N, W, rr_nst<OP>()>;
+  static const cudaError_t attr = set_smem(k_rstrided<T, N, OP, NC, W>, C::SMEM);
   if (attr != cudaSuccess) return attr;
   PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
-  const int gx = rr_grid_x<T, N>(g, a.nouter, &a.nyq_blk);
+  const int gx = rr_grid_x<W>(g, a.nouter, &a.nyq_blk);
   dim3 grid(gx, a.nouter, nprob);
-  k_rstrided<T, N, OP, NC><<<grid, C::NT, C::SMEM, s>>>(a);
+  k_rstrided<T, N, OP, NC, W><<<grid, C::NT, C::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -233,9 +235,15 @@ static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long 
                             const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
                             cudaStream_t s, int dm) {
   constexpr int TX0 = pick_tx((int)sizeof(cx<T>), N, NC);
-  if constexpr (rr_ok<T, N, OP, NC>())
-    if (g.txs[sizeof(T) == 8][axis][OP] == 3)
-      return l_pass_rr<T, N, OP, NC>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, s);
+  if constexpr (rr_ok<T, N, OP, NC>()) {
+    const int sh = g.txs[sizeof(T) == 8][axis][OP];
+    if (sh == 3)
+      return l_pass_rr<T, N, OP, NC, rr_wdef<T>()>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm, cprm,
+                                                   part, s);
+    if (sh == 4)
+      return l_pass_rr<T, N, OP, NC, rr_wdef<T>() / 2>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm,
+                                                       cprm, part, s);
+  }
   if constexpr (tunable<N, OP, NC>()) {
     const int sh = g.txs[sizeof(T) == 8][axis][OP];
     if constexpr (tx_ok<T, N, OP, NC, TX0 / 2>())
@@ -325,7 +333,7 @@ bool Ops<T>::tx_variant(int n, int op, int nc, int shift) {
   const int t0 = pass_tx(g, 0, op, nc);
   g.txs[sizeof(T) == 8][0][op] = (signed char)shift;
   const int t1 = pass_tx(g, 0, op, nc);
-  if (shift == 3) return t1 < 0;
+  if (shift >= 3) return t1 < 0;
   return shift == 0 || (t1 != t0 && t1 > 0);
 }
 

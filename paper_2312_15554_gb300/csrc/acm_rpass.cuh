@@ -31,14 +31,24 @@
 
 namespace acm {
 
-template <typename T, int N>
+// columns per block of the default register-resident variant: one 128-byte
+// row segment per warp access (16 in FP32, 8 in FP64); the narrow variant
+// takes half of that
+template <typename T>
+__host__ __device__ constexpr int rr_wdef() { return 128 / (int)sizeof(cx<T>); }
+
+// NST: operator-state values per element a z pass prefetches (2 Stokes: q^ and
+// div^; 1 solute: chi^; 0 for the y passes)
+template <typename T, int N, int W, int NST = 0>
 struct RCfg {
   static constexpr int TL = N / 16;                        // threads per line
-  static constexpr int W = 128 / (int)sizeof(cx<T>);       // columns per block
   static constexpr int NT = W * TL;                        // threads per block
   static constexpr int BS = N + 1;                         // column stride of a transpose buffer (odd)
-  static constexpr int SMEM = (2 * W * BS + N) * (int)sizeof(cx<T>);
+  static constexpr int SMEM = (2 * W * BS + N + NST * 16 * NT) * (int)sizeof(cx<T>);
 };
+
+template <int OP>
+__host__ __device__ constexpr int rr_nst() { return OP == OP_STOKES ? 2 : (OP == OP_SOLUTE ? 1 : 0); }
 
 // W_N^{e} (forward sign) or its conjugate, e taken modulo N
 template <typename T, int N, int SIGN>
@@ -52,7 +62,7 @@ __device__ __forceinline__ cx<T> rtw(const cx<T>* tw, int e) {
 // X[k1 + 16 k2] with k1 = t + TL i (the thread now owns k1 = t, t + TL, ...).
 template <typename T, int N, int SIGN>
 __device__ __forceinline__ void rr_fft(cx<T> (&v)[16], cx<T>* buf, const cx<T>* tw, int col, int t) {
-  constexpr int TL = N / 16, BS = RCfg<T, N>::BS;
+  constexpr int TL = N / 16, BS = N + 1;
   dft<16, SIGN>(v);
 #pragma unroll
   for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], rtw<T, N, SIGN>(tw, t * k1));
@@ -72,7 +82,7 @@ __device__ __forceinline__ void rr_fft(cx<T> (&v)[16], cx<T>* buf, const cx<T>* 
 // on exit v[m] = x[s + TL m].
 template <typename T, int N, int SIGN>
 __device__ __forceinline__ void rr_ifft(cx<T> (&v)[16], cx<T>* buf, const cx<T>* tw, int col, int s) {
-  constexpr int TL = N / 16, BS = RCfg<T, N>::BS;
+  constexpr int TL = N / 16, BS = N + 1;
   cx<T>* b = buf + col * BS;
 #pragma unroll
   for (int i = 0; i < 16 / TL; ++i) {
@@ -137,14 +147,16 @@ __device__ __forceinline__ void rr_store_k(const cx<T> (&v)[16], cx<T>* __restri
 //                    and the Parseval partials of the divergence residuals, inverse.
 //   OP_SOLUTE (z)    forward of (tau_0, s''), F^ = s'' + i d0 tau_0, Eq. 20 with
 //                    the Parseval partials of Eq. 19, inverse of (i d0 chi^, chi^).
-template <typename T, int N, int OP, int NC>
-__global__ void __launch_bounds__(RCfg<T, N>::NT) k_rstrided(PassArgs<T> a) {
-  using C = RCfg<T, N>;
-  constexpr int W = C::W;
+template <typename T, int N, int OP, int NC, int W>
+__global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
+  using C = RCfg<T, N, W, rr_nst<OP>()>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* buf1 = buf0 + W * C::BS;
   cx<T>* tw = buf1 + W * C::BS;
+  // z passes: the operator state of the thread's 16 wavevectors, prefetched
+  // with cp.async into slots private to the thread ([value][element][thread])
+  cx<T>* stp = tw + N;
   __shared__ double red[4 * 32];
   const int p = blockIdx.z;
   const int col = threadIdx.x % W, t = threadIdx.x / W;
@@ -229,9 +241,21 @@ __global__ void __launch_bounds__(RCfg<T, N>::NT) k_rstrided(PassArgs<T> a) {
   } else if constexpr (OP == OP_STOKES || OP == OP_SOLUTE) {
     constexpr int TL = N / 16;
     constexpr int NIN = OP == OP_STOKES ? 3 : 2;
+    constexpr int NST = rr_nst<OP>();
+    const long long gst = (long long)p * a.compStride + (long long)outer * a.outerStride + kx;
+    // (the state of problem p sits at p * S: a.compStride is S)
     cx<T> u[NIN][16];
 #pragma unroll
     for (int c = 0; c < NIN; ++c) rr_load_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
+    // the state travels while the forward transforms run
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const long long gi = gst + (long long)rr_krow<TL>(t, e) * a.rowStride;
+      cp_async_pred<(int)sizeof(cx<T>)>(&stp[e * C::NT + threadIdx.x], ok ? &a.st0[gi] : a.st0, ok);
+      if constexpr (NST == 2)
+        cp_async_pred<(int)sizeof(cx<T>)>(&stp[(16 + e) * C::NT + threadIdx.x], ok ? &a.st1[gi] : a.st1, ok);
+    }
+    cp_async_commit();
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NIN; ++c) rr_fft<T, N, -1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
@@ -242,11 +266,10 @@ __global__ void __launch_bounds__(RCfg<T, N>::NT) k_rstrided(PassArgs<T> a) {
     const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
     const T l12 = l1 + l2, d12 = d1 * d1 + d2 * d2;
     T acc0 = 0, acc1 = 0, acc2 = 0;
-    // the operator state (q^ and div^, or chi^) at the thread's wavevectors,
-    // read before it is rewritten in place, in chunks of CH
+    // the operator state (q^ and div^, or chi^) at the thread's wavevectors:
+    // read from the prefetched slots, rewritten in place in global memory
     constexpr int CH = 4;
-    const long long gst = (long long)p * a.compStride + (long long)outer * a.outerStride + kx;
-    // (the state of problem p sits at p * S: a.compStride is S)
+    cp_async_wait<0>();
     if constexpr (OP == OP_STOKES) {
       const T nu = (T)a.sprm[p].nu, beta = (T)a.sprm[p].psi[1], b = (T)a.sprm[p].psi[2];
 #pragma unroll
@@ -254,9 +277,8 @@ __global__ void __launch_bounds__(RCfg<T, N>::NT) k_rstrided(PassArgs<T> a) {
         cx<T> qs[CH], ds[CH];
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
-          const long long gi = gst + (long long)rr_krow<TL>(t, e0 + j) * a.rowStride;
-          qs[j] = ok ? a.st0[gi] : mk<T>(0, 0);
-          ds[j] = ok ? a.st1[gi] : mk<T>(0, 0);
+          qs[j] = stp[(e0 + j) * C::NT + threadIdx.x];
+          ds[j] = stp[(16 + e0 + j) * C::NT + threadIdx.x];
         }
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
@@ -313,10 +335,7 @@ __global__ void __launch_bounds__(RCfg<T, N>::NT) k_rstrided(PassArgs<T> a) {
       for (int e0 = 0; e0 < 16; e0 += CH) {
         cx<T> cs[CH];
 #pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          const long long gi = gst + (long long)rr_krow<TL>(t, e0 + j) * a.rowStride;
-          cs[j] = ok ? a.st0[gi] : mk<T>(0, 0);
-        }
+        for (int j = 0; j < CH; ++j) cs[j] = stp[(e0 + j) * C::NT + threadIdx.x];
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
           const int e = e0 + j, kz = rr_krow<TL>(t, e);
