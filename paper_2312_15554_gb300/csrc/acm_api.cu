@@ -1293,7 +1293,7 @@ acm_status autotune_ctx(acm_ctx* c, int nprob, int deriv) {
     const int n = j.axis == 1 ? c->g.n1 : c->g.n0;
     float best = 0;
     int best_sh = 0;
-    for (int sh = -1; sh <= 4 && st == ACM_OK; ++sh) {   // 3, 4: the register-resident variants
+    for (int sh = -1; sh <= 5 && st == ACM_OK; ++sh) {   // 3-5: the register-resident variants
       if (!Ops<T>::tx_variant(n, j.op, j.nc, sh)) continue;
       Geo g = c->g;
       g.txs[pr][j.axis][j.op] = (signed char)sh;
@@ -1741,7 +1741,7 @@ acm_status acm_set_tiles(acm_ctx* c, int fp64, const int tiles[NTUNE]) {
     if (j.solute && c->spec_comps < 4) continue;
     const int n = j.axis == 1 ? g.n1 : g.n0;
     bool found = false;
-    for (int sh = -1; sh <= 4 && !found; ++sh) {
+    for (int sh = -1; sh <= 5 && !found; ++sh) {
       if (!(fp64 ? Ops<double>::tx_variant(n, j.op, j.nc, sh) : Ops<float>::tx_variant(n, j.op, j.nc, sh))) continue;
       g.txs[fp64][j.axis][j.op] = (signed char)sh;
       const int tx = fp64 ? Ops<double>::pass_tx(g, j.axis, j.op, j.nc) : Ops<float>::pass_tx(g, j.axis, j.op, j.nc);

@@ -608,10 +608,7 @@ struct PassArgs {
   double invV;
   int nkx;          // n2 / 2 (Nyquist column index)
   int dm;           // OP_DERIV: axis of the derivative
-  // register-resident passes: pencils along the other strided axis, and the
-  // grid column of the shared Nyquist block (-1: none)
-  int nouter;
-  int nyq_blk;
+  int nouter;       // register-resident passes: pencils along the other strided axis
 };
 
 template <typename T, int N, int OP, int NC, int TX>

@@ -139,14 +139,15 @@ constexpr bool rr_ok() {
 }
 
 // tile width of (T, N, OP, NC) under the choice `shift`; the register-resident
-// variants (shift 3: W = rr_wdef, shift 4: W = rr_wdef / 2 columns per block)
-// report -W
+// variants (shift 3: W = rr_wdef, shift 4: W = rr_wdef / 2 columns per block,
+// shift 5: the persistent pipelined kernel with W = rr_wdef / 4) report -W
 template <typename T, int N, int OP, int NC>
 constexpr int resolved_tx(int shift) {
   constexpr int TX0 = pick_tx((int)sizeof(cx<T>), N, NC);
   if constexpr (rr_ok<T, N, OP, NC>()) {
     if (shift == 3) return -rr_wdef<T>();
     if (shift == 4) return -rr_wdef<T>() / 2;
+    if (shift == 5) return -rr_wdef<T>() / 4;   // the persistent pipelined variant
   }
   if (tunable<N, OP, NC>()) {
     if (shift < 0 && tx_ok<T, N, OP, NC, TX0 / 2>()) return TX0 / 2;
@@ -184,22 +185,7 @@ static PassArgs<T> pass_args(const Geo& g, int axis, void* spec, long long probS
   a.nkx = g.n2 / 2;
   a.dm = dm;
   a.nouter = axis == 1 ? g.n0 : g.n1;
-  a.nyq_blk = -1;
   return a;
-}
-
-// Grid columns of a register-resident pass: W-column blocks of the first n2/2
-// columns plus one block that packs the Nyquist column of W pencils, when n2/2
-// and the pencil count are multiples of W; otherwise ceil(Pu / W) blocks with a
-// ragged last one.
-template <int W>
-static int rr_grid_x(const Geo& g, int nouter, int* nyq_blk) {
-  if ((g.Pu - 1) % W == 0 && nouter % W == 0) {
-    *nyq_blk = (g.Pu - 1) / W;
-    return (g.Pu - 1) / W + 1;
-  }
-  *nyq_blk = -1;
-  return (g.Pu + W - 1) / W;
 }
 
 template <typename T, int N, int OP, int NC, int TX>
@@ -223,10 +209,35 @@ static cudaError_t l_pass_rr(const Geo& g, int axis, int nprob, void* spec, long
   using C = RCfg<T, N, W, rr_nst<OP>()>;
   static const cudaError_t attr = set_smem(k_rstrided<T, N, OP, NC, W>, C::SMEM);
   if (attr != cudaSuccess) return attr;
-  PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
-  const int gx = rr_grid_x<W>(g, a.nouter, &a.nyq_blk);
-  dim3 grid(gx, a.nouter, nprob);
-  k_rstrided<T, N, OP, NC, W><<<grid, C::NT, C::SMEM, s>>>(a);
+  const PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
+  const RTiles tl = rr_tiles(g.Pu, a.nouter, W);
+  k_rstrided<T, N, OP, NC, W><<<nprob * tl.nlive, C::NT, C::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+// The persistent pipelined variant: as many blocks as fit on the device at
+// once (at most one per tile).
+template <typename T, int N, int OP, int NC, int W>
+static cudaError_t l_pass_rp(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
+                             const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
+                             cudaStream_t s) {
+  using C = RCfg<T, N, W, rr_nst<OP>(), rr_nin<OP, NC>()>;
+  static const cudaError_t attr = set_smem(k_rpipe<T, N, OP, NC, W>, C::SMEM);
+  if (attr != cudaSuccess) return attr;
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rpipe<T, N, OP, NC, W>, C::NT, C::SMEM) !=
+            cudaSuccess)
+      return cudaGetLastError();
+    resident = (per > 0 ? per : 1) * nsm;
+  }
+  const PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
+  const RTiles tl = rr_tiles(g.Pu, a.nouter, W);
+  const int ntiles = nprob * tl.nlive;
+  k_rpipe<T, N, OP, NC, W><<<ntiles < resident ? ntiles : resident, C::NT, C::SMEM, s>>>(a, nprob);
   return cudaGetLastError();
 }
 
@@ -242,6 +253,9 @@ static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long 
                                                    part, s);
     if (sh == 4)
       return l_pass_rr<T, N, OP, NC, rr_wdef<T>() / 2>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm,
+                                                       cprm, part, s);
+    if (sh == 5)
+      return l_pass_rp<T, N, OP, NC, rr_wdef<T>() / 4>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm,
                                                        cprm, part, s);
   }
   if constexpr (tunable<N, OP, NC>()) {
@@ -340,7 +354,8 @@ bool Ops<T>::tx_variant(int n, int op, int nc, int shift) {
 template <typename T>
 int Ops<T>::z_blocks(const Geo& g, int op) {
   const int nc = op == P_SOLUTE ? 2 : 3;
-  const int tx = std::abs(pass_tx(g, 0, op, nc));
+  const int tx = pass_tx(g, 0, op, nc);
+  if (tx < 0) return rr_tiles(g.Pu, g.n1, -tx).nlive;   // register-resident: one record per live tile
   return ((g.Pu + tx - 1) / tx) * g.n1;
 }
 

@@ -15,16 +15,25 @@
 // shared memory only for two transposes per component, against twelve
 // round trips of a block-wide Stockham tile.
 //
-// A block holds W consecutive kx columns (W x 8 bytes = 128 bytes of a row per
-// warp access: W = 16 in FP32, 8 in FP64) and TL threads per column; thread
-// (col, t) = (tid % W, tid / W). Global loads and stores of a fixed m (or k)
-// are W-column row segments, coalesced. The transposes alternate between two
-// buffers, so one __syncthreads per transform suffices. When n2/2 and the
-// number of pencils are multiples of W, the lone Nyquist column kx = n2/2 of W
-// consecutive pencils shares one extra block (lane column `col` then takes
-// pencil outer0 + col), instead of a block with one busy column per pencil.
-// All components a thread transforms are requested from global memory before
-// the first transform, so a block keeps its loads in flight while it computes.
+// A tile is W consecutive kx columns of one pencil (W x 8 bytes of a row per
+// access: W = 16, 8 or 4 in FP32), held by W x TL threads; thread (col, t) =
+// (tid % W, tid / W). When n2/2 and the number of pencils are multiples of W,
+// the lone Nyquist column kx = n2/2 of W consecutive pencils forms one more
+// tile (lane column `col` takes pencil W g + col), so no tile carries idle
+// columns; the tiles of a problem are numbered regular ones first (pencil-major),
+// then the Nyquist tiles, and a z pass writes one partial-sum record per tile.
+// The transposes alternate between two buffers, so one __syncthreads per
+// transform suffices.
+//
+// Two kernels use these pieces:
+//   k_rstrided  one tile per block; its global loads go straight to registers
+//               (the next component's loads are issued before the current
+//               component's transform).
+//   k_rpipe     persistent blocks that walk over tiles; while a block
+//               transforms tile i from registers, cp.async brings the inputs of
+//               its next tile into a shared-memory stage (and, for a z pass,
+//               the operator state into slots private to each thread), so
+//               memory traffic overlaps the transforms of every resident block.
 #pragma once
 #include "acm_fft.cuh"
 #include "acm_types.h"
@@ -38,17 +47,54 @@ template <typename T>
 __host__ __device__ constexpr int rr_wdef() { return 128 / (int)sizeof(cx<T>); }
 
 // NST: operator-state values per element a z pass prefetches (2 Stokes: q^ and
-// div^; 1 solute: chi^; 0 for the y passes)
-template <typename T, int N, int W, int NST = 0>
+// div^; 1 solute: chi^; 0 for the y passes); NIN: input components of a tile
+template <int OP>
+__host__ __device__ constexpr int rr_nst() { return OP == OP_STOKES ? 2 : (OP == OP_SOLUTE ? 1 : 0); }
+template <int OP, int NC>
+__host__ __device__ constexpr int rr_nin() {
+  return OP == OP_FWD_SOL ? 3 : (OP == OP_INV_SOL ? 2 : (OP == OP_STOKES ? 3 : (OP == OP_SOLUTE ? 2 : NC)));
+}
+
+// shared memory of a block (complex elements): two transpose buffers, the
+// twiddles, the per-thread state slots and, in the pipelined kernel, the input
+// stage of one tile
+template <typename T, int N, int W, int NST = 0, int STAGE = 0>
 struct RCfg {
   static constexpr int TL = N / 16;                        // threads per line
   static constexpr int NT = W * TL;                        // threads per block
   static constexpr int BS = N + 1;                         // column stride of a transpose buffer (odd)
-  static constexpr int SMEM = (2 * W * BS + N + NST * 16 * NT) * (int)sizeof(cx<T>);
+  static constexpr int SMEM = (2 * W * BS + N + NST * 16 * NT + STAGE * N * W) * (int)sizeof(cx<T>);
 };
 
-template <int OP>
-__host__ __device__ constexpr int rr_nst() { return OP == OP_STOKES ? 2 : (OP == OP_SOLUTE ? 1 : 0); }
+// The live tiles of one problem: nreg = gxr pencils x column blocks, then (when
+// the Nyquist column is packed) nouter / W Nyquist tiles.
+struct RTiles {
+  int gxr;     // regular column blocks per pencil
+  int nouter;  // pencils
+  int nyq;     // 1: the Nyquist column is packed into tiles of its own
+  int nlive;   // tiles per problem
+};
+
+__host__ __device__ inline RTiles rr_tiles(int Pu, int nouter, int W) {
+  RTiles r;
+  r.nouter = nouter;
+  r.nyq = ((Pu - 1) % W == 0 && nouter % W == 0) ? 1 : 0;
+  r.gxr = r.nyq ? (Pu - 1) / W : (Pu + W - 1) / W;
+  r.nlive = r.gxr * nouter + (r.nyq ? nouter / W : 0);
+  return r;
+}
+
+// pencil and kx column of lane column `col` in tile r of a problem
+__device__ __forceinline__ void rr_tile_lane(const RTiles& tl, int r, int W, int col, int Pu, int* outer, int* kx) {
+  const int nreg = tl.gxr * tl.nouter;
+  if (r < nreg) {
+    *outer = r / tl.gxr;
+    *kx = (r % tl.gxr) * W + col;
+  } else {
+    *outer = (r - nreg) * W + col;
+    *kx = Pu - 1;
+  }
+}
 
 // W_N^{e} (forward sign) or its conjugate, e taken modulo N
 template <typename T, int N, int SIGN>
@@ -139,6 +185,143 @@ __device__ __forceinline__ void rr_store_k(const cx<T> (&v)[16], cx<T>* __restri
   for (int e = 0; e < 16; ++e) dst[(long long)rr_krow<TL>(s, e) * rowStride] = v[e];
 }
 
+// ---------------------------------------------------------------------------
+// The z-pass operators on a thread's 16 wavevectors (kz = rr_krow(t, e)), with
+// the operator state read from per-thread slots sq[e * ss] (q^ or chi^) and
+// sd[e * ss] (div^), and rewritten in place in global memory.
+// ---------------------------------------------------------------------------
+// Eq. 13 per wavevector, the q^ update of Eq. 9, the Parseval partials of the
+// divergence residuals (acc) and the k = 0 tap; u[c] leaves as u^_c / V.
+template <typename T, int N>
+__device__ __forceinline__ void rr_stokes_op(const PassArgs<T>& a, cx<T> (&u)[3][16], int p, int ky, int kx, bool ok,
+                                             int t, const cx<T>* sq, const cx<T>* sd, int ss, T (&acc)[3]) {
+  constexpr int TL = N / 16, CH = 4;
+  const T invV = (T)a.invV;
+  const T d1 = a.sym.d1[ky], l1 = a.sym.l1[ky];
+  const T d2 = ok ? a.sym.d2[kx] : (T)0, l2 = ok ? a.sym.l2[kx] : (T)0;
+  const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
+  const T l12 = l1 + l2, d12 = d1 * d1 + d2 * d2;
+  const long long gst = (long long)p * a.compStride + (long long)ky * a.outerStride + kx;
+  const T nu = (T)a.sprm[p].nu, beta = (T)a.sprm[p].psi[1], b = (T)a.sprm[p].psi[2];
+#pragma unroll
+  for (int e0 = 0; e0 < 16; e0 += CH) {
+    cx<T> qs[CH], ds[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      qs[j] = sq[(e0 + j) * ss];
+      ds[j] = sd[(e0 + j) * ss];
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int e = e0 + j, kz = rr_krow<TL>(t, e);
+      const long long gi = gst + (long long)kz * a.rowStride;
+      const T d0 = a.sym.d0[kz], l0 = a.sym.l0[kz];
+      const T L = l0 + l12, dd = d0 * d0 + d12;
+      const bool k0 = (kz == 0 && ky == 0 && kx == 0);
+      // r = w^ - i d q^ (+ g V at k = 0)
+      const cx<T> iq = mul_i(qs[j]);
+      cx<T> r0 = u[0][e] - cscale(iq, d0), r1 = u[1][e] - cscale(iq, d1), r2 = u[2][e] - cscale(iq, d2);
+      if (k0) {
+        const StokesDev& P = a.sprm[p];
+        const T Vt = (T)(1.0 / a.invV);
+        r0.x += (T)P.g[0] * Vt;
+        r1.x += (T)P.g[1] * Vt;
+        r2.x += (T)P.g[2] * Vt;
+      }
+      // Eq. 13: (nu L + b) u^ + beta d (d.u^) = r, solved as
+      //   d.u^ = d.r / (c + beta |d|^2),  u^ = (r - beta d (d.u^)) / c,  c = nu L + b
+      const T c0 = nu * L + b;
+      const T ic0 = (T)1 / c0;
+      const cx<T> dr = cscale(r0, d0) + cscale(r1, d1) + cscale(r2, d2);
+      const cx<T> du = cscale(dr, (T)1 / (c0 + beta * dd));
+      const cx<T> f = cscale(du, beta);
+      const cx<T> v0 = cscale(r0 - cscale(f, d0), ic0);
+      const cx<T> v1 = cscale(r1 - cscale(f, d1), ic0);
+      const cx<T> v2 = cscale(r2 - cscale(f, d2), ic0);
+      // div u^ = i d.u^ from the solve; Eq. 9: q^ <- q^ - beta div u^
+      const cx<T> dv = mul_i(du);
+      const cx<T> qn = qs[j] - cscale(dv, beta);
+      if (ok) {
+        a.st0[gi] = qn;
+        a.st1[gi] = dv;
+        const cx<T> ddv = dv - ds[j];
+        acc[0] += wgt * cabs2(dv);
+        acc[1] += wgt * cabs2(ddv);
+        acc[2] += wgt * cabs2(qn);
+      }
+      if (k0) {
+        a.sprm[p].mean_u[0] = (double)v0.x * a.invV;
+        a.sprm[p].mean_u[1] = (double)v1.x * a.invV;
+        a.sprm[p].mean_u[2] = (double)v2.x * a.invV;
+      }
+      u[0][e] = cscale(v0, invV);
+      u[1][e] = cscale(v1, invV);
+      u[2][e] = cscale(v2, invV);
+    }
+  }
+}
+
+// F^ = s'' + i d0 tau_0 (Eq. 18; the axis-2 and axis-1 terms were added in the
+// x and y passes), Eq. 20 with chi^(0) = 0, the Parseval partials of Eq. 19;
+// u leaves as (i d0 chi^, chi^) / V.
+template <typename T, int N>
+__device__ __forceinline__ void rr_solute_op(const PassArgs<T>& a, cx<T> (&u)[2][16], int p, int ky, int kx, bool ok,
+                                             int t, const cx<T>* sq, int ss, T (&acc)[3]) {
+  constexpr int TL = N / 16, CH = 4;
+  const T invV = (T)a.invV;
+  const T d1 = a.sym.d1[ky], l1 = a.sym.l1[ky];
+  const T d2 = ok ? a.sym.d2[kx] : (T)0, l2 = ok ? a.sym.l2[kx] : (T)0;
+  const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
+  const T l12 = l1 + l2, d12 = d1 * d1 + d2 * d2;
+  const long long gst = (long long)p * a.compStride + (long long)ky * a.outerStride + kx;
+  const T A0 = (T)a.cprm[p].A0, B00 = (T)a.cprm[p].B0[0], B01 = (T)a.cprm[p].B0[1], B02 = (T)a.cprm[p].B0[2];
+#pragma unroll
+  for (int e0 = 0; e0 < 16; e0 += CH) {
+    cx<T> cs[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) cs[j] = sq[(e0 + j) * ss];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int e = e0 + j, kz = rr_krow<TL>(t, e);
+      const long long gi = gst + (long long)kz * a.rowStride;
+      const T d0 = a.sym.d0[kz], l0 = a.sym.l0[kz];
+      const T L = l0 + l12, dd = d0 * d0 + d12;
+      const bool k0 = (kz == 0 && ky == 0 && kx == 0);
+      const cx<T> F = u[1][e] + mul_i(cscale(u[0][e], d0));
+      const T dre = A0 * L, dim = B00 * d0 + B01 * d1 + B02 * d2;
+      cx<T> chi = mk<T>(0, 0);
+      if (!k0 && ok) {
+        const T den = (T)1 / (dre * dre + dim * dim);
+        chi = mk<T>((F.x * dre + F.y * dim) * den, (F.y * dre - F.x * dim) * den);
+      }
+      if (ok) {
+        const cx<T> dch = chi - cs[j];
+        a.st0[gi] = chi;
+        acc[0] += wgt * cabs2(dch);
+        acc[1] += wgt * dd * cabs2(dch);
+      }
+      const cx<T> c1 = cscale(chi, invV);
+      u[0][e] = cscale(mul_i(c1), d0);
+      u[1][e] = c1;
+    }
+  }
+}
+
+// issue the cp.async copies of the operator state of a thread's 16 wavevectors
+// into its private slots slot[e * ss] (and slot[(16 + e) * ss] for div^)
+template <typename T, int N, int NST>
+__device__ __forceinline__ void rr_prefetch_state(const PassArgs<T>& a, cx<T>* slot, int ss, int p, int ky, int kx,
+                                                  bool ok, int t) {
+  constexpr int TL = N / 16;
+  const long long gst = (long long)p * a.compStride + (long long)ky * a.outerStride + kx;
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const long long gi = gst + (long long)rr_krow<TL>(t, e) * a.rowStride;
+    cp_async_pred<(int)sizeof(cx<T>)>(&slot[e * ss], ok ? &a.st0[gi] : a.st0, ok);
+    if constexpr (NST == 2) cp_async_pred<(int)sizeof(cx<T>)>(&slot[(16 + e) * ss], ok ? &a.st1[gi] : a.st1, ok);
+  }
+}
+
 // Operators (OP values of the block-wide strided kernel, acm_kernels.cuh):
 //   OP_FWD / OP_INV  NC components transformed forward / inverse.
 //   OP_FWD_SOL (y)   (tau_0, tau_1, s') in, (tau_0, s' + i d1 tau_1) out.
@@ -147,66 +330,117 @@ __device__ __forceinline__ void rr_store_k(const cx<T> (&v)[16], cx<T>* __restri
 //                    and the Parseval partials of the divergence residuals, inverse.
 //   OP_SOLUTE (z)    forward of (tau_0, s''), F^ = s'' + i d0 tau_0, Eq. 20 with
 //                    the Parseval partials of Eq. 19, inverse of (i d0 chi^, chi^).
+//
+// The work on one tile whose inputs are already in registers (x-ordered,
+// v[m] = x[t + TL m], for the forward operators; k-ordered, v[e] = X[krow(t, e)],
+// for the inverse ones), ending with the stores to global memory. sq / sd:
+// the thread's state slots (z passes). part: the tile's partial-sum record.
+template <typename T, int N, int OP, int NC, int W>
+__device__ __forceinline__ void rr_apply(const PassArgs<T>& a, cx<T> (&u)[rr_nin<OP, NC>()][16], int p, int outer,
+                                         int kx, bool ok, cx<T>* base, int col, int t, cx<T>* buf0, cx<T>* buf1,
+                                         const cx<T>* tw, const cx<T>* sq, const cx<T>* sd, int ss, double* red,
+                                         double* part) {
+  constexpr int TL = N / 16;
+  if constexpr (OP == OP_FWD) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      rr_fft<T, N, -1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
+      rr_store_k<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
+    }
+  } else if constexpr (OP == OP_INV) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      rr_ifft<T, N, +1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
+      rr_store_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
+    }
+  } else if constexpr (OP == OP_FWD_SOL) {
+    rr_fft<T, N, -1>(u[0], buf0, tw, col, t);
+    rr_store_k<T, N>(u[0], base, a.rowStride, t, ok);
+    rr_fft<T, N, -1>(u[1], buf1, tw, col, t);
+    rr_fft<T, N, -1>(u[2], buf0, tw, col, t);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) u[2][e] = u[2][e] + cscale(mul_i(u[1][e]), a.sym.d1[rr_krow<TL>(t, e)]);
+    rr_store_k<T, N>(u[2], base + a.compStride, a.rowStride, t, ok);
+  } else if constexpr (OP == OP_INV_SOL) {
+    rr_ifft<T, N, +1>(u[0], buf0, tw, col, t);
+    rr_store_x<T, N>(u[0], base, a.rowStride, t, ok);
+    cx<T> v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = cscale(mul_i(u[1][e]), a.sym.d1[rr_krow<TL>(t, e)]);
+    rr_ifft<T, N, +1>(v, buf1, tw, col, t);
+    rr_store_x<T, N>(v, base + a.compStride, a.rowStride, t, ok);
+    rr_ifft<T, N, +1>(u[1], buf0, tw, col, t);
+    // i d2(kx) applied after the (linear) transform: a factor per column
+    const T d2 = ok ? a.sym.d2[kx] : (T)0;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) u[1][m] = cscale(mul_i(u[1][m]), d2);
+    rr_store_x<T, N>(u[1], base + 2 * a.compStride, a.rowStride, t, ok);
+  } else {
+    constexpr int NIN = rr_nin<OP, NC>();
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) rr_fft<T, N, -1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
+    T acc[3] = {(T)0, (T)0, (T)0};
+    if constexpr (OP == OP_STOKES) rr_stokes_op<T, N>(a, u, p, outer, kx, ok, t, sq, sd, ss, acc);
+    else rr_solute_op<T, N>(a, u, p, outer, kx, ok, t, sq, ss, acc);
+    double v3[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
+    block_sum_store<3>(v3, red, part);
+    // the sums' barriers separate the last forward transform's buffer reads from
+    // the inverse transforms' writes
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) {
+      rr_ifft<T, N, +1>(u[c], ((c + NIN) & 1) ? buf1 : buf0, tw, col, t);
+      rr_store_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
+    }
+  }
+}
+
+// One tile per block (blockIdx.x = problem x live tiles + tile); inputs loaded
+// from global memory straight into registers.
 template <typename T, int N, int OP, int NC, int W>
 __global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
   using C = RCfg<T, N, W, rr_nst<OP>()>;
+  constexpr int NIN = rr_nin<OP, NC>(), NST = rr_nst<OP>();
+  constexpr bool FWDIN = OP == OP_FWD || OP == OP_FWD_SOL || OP == OP_STOKES || OP == OP_SOLUTE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* buf1 = buf0 + W * C::BS;
   cx<T>* tw = buf1 + W * C::BS;
-  // z passes: the operator state of the thread's 16 wavevectors, prefetched
-  // with cp.async into slots private to the thread ([value][element][thread])
-  cx<T>* stp = tw + N;
+  cx<T>* stp = tw + N;  // state slots [value][element][thread]
   __shared__ double red[4 * 32];
-  const int p = blockIdx.z;
-  const int col = threadIdx.x % W, t = threadIdx.x / W;
-  // the lane column's pencil and kx column: a regular block takes W columns of
-  // pencil blockIdx.y; the Nyquist block (blockIdx.x == a.nyq_blk) takes column
-  // n2/2 of the W pencils W blockIdx.y .. W blockIdx.y + W - 1
-  const bool nyq = (int)blockIdx.x == a.nyq_blk;
-  const int outer = nyq ? (int)blockIdx.y * W + col : (int)blockIdx.y;
-  const int kx = nyq ? a.Pu - 1 : (int)blockIdx.x * W + col;
-  const bool live = !nyq || (int)blockIdx.y * W < a.nouter;
-  const bool ok = live && kx < a.Pu;
+  const RTiles tl = rr_tiles(a.Pu, a.nouter, W);
+  const int p = blockIdx.x / tl.nlive, r = blockIdx.x % tl.nlive;
   if ((a.sprm && a.sprm[p].done) || (a.cprm && a.cprm[p].done)) return;
-  if (!live) {
-    // a Nyquist block past the last pencil: only its partial sums (zero) exist
-    if constexpr (OP == OP_STOKES || OP == OP_SOLUTE)
-      if (threadIdx.x < 3) a.part[((long long)p * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x) * 4 +
-                                  threadIdx.x] = 0.0;
-    return;
-  }
+  const int col = threadIdx.x % W, t = threadIdx.x / W;
+  int outer, kx;
+  rr_tile_lane(tl, r, W, col, a.Pu, &outer, &kx);
+  const bool ok = kx < a.Pu;
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = a.twg[k * (TW_MAX / N)];
   cx<T>* base = a.spec + p * a.probStride + (long long)outer * a.outerStride + kx;
-  cx<T> v[16];
-  if constexpr (OP == OP_FWD) {
+  if constexpr (OP == OP_FWD || OP == OP_INV) {
     // component c + 1 travels while component c is transformed
-    cx<T> w[16];
-    rr_load_x<T, N>(v, base, a.rowStride, t, ok);
+    cx<T> v[16], w[16];
+    if constexpr (OP == OP_FWD) rr_load_x<T, N>(v, base, a.rowStride, t, ok);
+    else rr_load_k<T, N>(v, base, a.rowStride, t, ok);
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       cx<T>(&cur)[16] = (c & 1) ? w : v;
       cx<T>(&nxt)[16] = (c & 1) ? v : w;
-      if (c + 1 < NC) rr_load_x<T, N>(nxt, base + (c + 1) * a.compStride, a.rowStride, t, ok);
-      rr_fft<T, N, -1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
-      rr_store_k<T, N>(cur, base + c * a.compStride, a.rowStride, t, ok);
-    }
-  } else if constexpr (OP == OP_INV) {
-    cx<T> w[16];
-    rr_load_k<T, N>(v, base, a.rowStride, t, ok);
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      cx<T>(&cur)[16] = (c & 1) ? w : v;
-      cx<T>(&nxt)[16] = (c & 1) ? v : w;
-      if (c + 1 < NC) rr_load_k<T, N>(nxt, base + (c + 1) * a.compStride, a.rowStride, t, ok);
-      rr_ifft<T, N, +1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
-      rr_store_x<T, N>(cur, base + c * a.compStride, a.rowStride, t, ok);
+      if (c + 1 < NC) {
+        if constexpr (OP == OP_FWD) rr_load_x<T, N>(nxt, base + (c + 1) * a.compStride, a.rowStride, t, ok);
+        else rr_load_k<T, N>(nxt, base + (c + 1) * a.compStride, a.rowStride, t, ok);
+      }
+      if constexpr (OP == OP_FWD) {
+        rr_fft<T, N, -1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
+        rr_store_k<T, N>(cur, base + c * a.compStride, a.rowStride, t, ok);
+      } else {
+        rr_ifft<T, N, +1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
+        rr_store_x<T, N>(cur, base + c * a.compStride, a.rowStride, t, ok);
+      }
     }
   } else if constexpr (OP == OP_FWD_SOL) {
     constexpr int TL = N / 16;
-    cx<T> w[16];
+    cx<T> v[16], w[16];
     rr_load_x<T, N>(v, base, a.rowStride, t, ok);
     rr_load_x<T, N>(w, base + a.compStride, a.rowStride, t, ok);
     __syncthreads();
@@ -220,162 +454,114 @@ __global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = v[e] + w[e];
     rr_store_k<T, N>(v, base + a.compStride, a.rowStride, t, ok);
-  } else if constexpr (OP == OP_INV_SOL) {
-    constexpr int TL = N / 16;
-    cx<T> b[16];
-    rr_load_k<T, N>(v, base, a.rowStride, t, ok);
-    rr_load_k<T, N>(b, base + a.compStride, a.rowStride, t, ok);
-    __syncthreads();
-    rr_ifft<T, N, +1>(v, buf0, tw, col, t);
-    rr_store_x<T, N>(v, base, a.rowStride, t, ok);
-#pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = cscale(mul_i(b[e]), a.sym.d1[rr_krow<TL>(t, e)]);
-    rr_ifft<T, N, +1>(v, buf1, tw, col, t);
-    rr_store_x<T, N>(v, base + a.compStride, a.rowStride, t, ok);
-    rr_ifft<T, N, +1>(b, buf0, tw, col, t);
-    // i d2(kx) applied after the (linear) transform: a factor per column
-    const T d2 = ok ? a.sym.d2[kx] : (T)0;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) b[m] = cscale(mul_i(b[m]), d2);
-    rr_store_x<T, N>(b, base + 2 * a.compStride, a.rowStride, t, ok);
-  } else if constexpr (OP == OP_STOKES || OP == OP_SOLUTE) {
-    constexpr int TL = N / 16;
-    constexpr int NIN = OP == OP_STOKES ? 3 : 2;
-    constexpr int NST = rr_nst<OP>();
-    const long long gst = (long long)p * a.compStride + (long long)outer * a.outerStride + kx;
-    // (the state of problem p sits at p * S: a.compStride is S)
+  } else {
+    // OP_INV_SOL and the z passes: every input component in registers first
     cx<T> u[NIN][16];
 #pragma unroll
-    for (int c = 0; c < NIN; ++c) rr_load_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
-    // the state travels while the forward transforms run
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const long long gi = gst + (long long)rr_krow<TL>(t, e) * a.rowStride;
-      cp_async_pred<(int)sizeof(cx<T>)>(&stp[e * C::NT + threadIdx.x], ok ? &a.st0[gi] : a.st0, ok);
-      if constexpr (NST == 2)
-        cp_async_pred<(int)sizeof(cx<T>)>(&stp[(16 + e) * C::NT + threadIdx.x], ok ? &a.st1[gi] : a.st1, ok);
-    }
-    cp_async_commit();
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < NIN; ++c) rr_fft<T, N, -1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
-    const T invV = (T)a.invV;
-    const int ky = outer;
-    const T d1 = a.sym.d1[ky], l1 = a.sym.l1[ky];
-    const T d2 = ok ? a.sym.d2[kx] : (T)0, l2 = ok ? a.sym.l2[kx] : (T)0;
-    const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
-    const T l12 = l1 + l2, d12 = d1 * d1 + d2 * d2;
-    T acc0 = 0, acc1 = 0, acc2 = 0;
-    // the operator state (q^ and div^, or chi^) at the thread's wavevectors:
-    // read from the prefetched slots, rewritten in place in global memory
-    constexpr int CH = 4;
-    cp_async_wait<0>();
-    if constexpr (OP == OP_STOKES) {
-      const T nu = (T)a.sprm[p].nu, beta = (T)a.sprm[p].psi[1], b = (T)a.sprm[p].psi[2];
-#pragma unroll
-      for (int e0 = 0; e0 < 16; e0 += CH) {
-        cx<T> qs[CH], ds[CH];
-#pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          qs[j] = stp[(e0 + j) * C::NT + threadIdx.x];
-          ds[j] = stp[(16 + e0 + j) * C::NT + threadIdx.x];
-        }
-#pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          const int e = e0 + j, kz = rr_krow<TL>(t, e);
-          const long long gi = gst + (long long)kz * a.rowStride;
-          const T d0 = a.sym.d0[kz], l0 = a.sym.l0[kz];
-          const T L = l0 + l12, dd = d0 * d0 + d12;
-          const bool k0 = (kz == 0 && ky == 0 && kx == 0);
-          // r = w^ - i d q^ (+ g V at k = 0)
-          const cx<T> iq = mul_i(qs[j]);
-          cx<T> r0 = u[0][e] - cscale(iq, d0), r1 = u[1][e] - cscale(iq, d1), r2 = u[2][e] - cscale(iq, d2);
-          if (k0) {
-            const StokesDev& P = a.sprm[p];
-            const T Vt = (T)(1.0 / a.invV);
-            r0.x += (T)P.g[0] * Vt;
-            r1.x += (T)P.g[1] * Vt;
-            r2.x += (T)P.g[2] * Vt;
-          }
-          // Eq. 13: (nu L + b) u^ + beta d (d.u^) = r, solved as
-          //   d.u^ = d.r / (c + beta |d|^2),  u^ = (r - beta d (d.u^)) / c,  c = nu L + b
-          const T c0 = nu * L + b;
-          const T ic0 = (T)1 / c0;
-          const cx<T> dr = cscale(r0, d0) + cscale(r1, d1) + cscale(r2, d2);
-          const cx<T> du = cscale(dr, (T)1 / (c0 + beta * dd));
-          const cx<T> f = cscale(du, beta);
-          const cx<T> v0 = cscale(r0 - cscale(f, d0), ic0);
-          const cx<T> v1 = cscale(r1 - cscale(f, d1), ic0);
-          const cx<T> v2 = cscale(r2 - cscale(f, d2), ic0);
-          // div u^ = i d.u^ from the solve; Eq. 9: q^ <- q^ - beta div u^
-          const cx<T> dv = mul_i(du);
-          const cx<T> qn = qs[j] - cscale(dv, beta);
-          if (ok) {
-            a.st0[gi] = qn;
-            a.st1[gi] = dv;
-            const cx<T> ddv = dv - ds[j];
-            acc0 += wgt * cabs2(dv);
-            acc1 += wgt * cabs2(ddv);
-            acc2 += wgt * cabs2(qn);
-          }
-          if (k0) {
-            a.sprm[p].mean_u[0] = (double)v0.x * a.invV;
-            a.sprm[p].mean_u[1] = (double)v1.x * a.invV;
-            a.sprm[p].mean_u[2] = (double)v2.x * a.invV;
-          }
-          u[0][e] = cscale(v0, invV);
-          u[1][e] = cscale(v1, invV);
-          u[2][e] = cscale(v2, invV);
-        }
-      }
-    } else {
-      const T A0 = (T)a.cprm[p].A0, B00 = (T)a.cprm[p].B0[0], B01 = (T)a.cprm[p].B0[1],
-              B02 = (T)a.cprm[p].B0[2];
-#pragma unroll
-      for (int e0 = 0; e0 < 16; e0 += CH) {
-        cx<T> cs[CH];
-#pragma unroll
-        for (int j = 0; j < CH; ++j) cs[j] = stp[(e0 + j) * C::NT + threadIdx.x];
-#pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          const int e = e0 + j, kz = rr_krow<TL>(t, e);
-          const long long gi = gst + (long long)kz * a.rowStride;
-          const T d0 = a.sym.d0[kz], l0 = a.sym.l0[kz];
-          const T L = l0 + l12, dd = d0 * d0 + d12;
-          const bool k0 = (kz == 0 && ky == 0 && kx == 0);
-          // F^ = s^ + i d.tau^ (Eq. 18 in Fourier space); the axis-2 and axis-1
-          // terms were added in the x and y passes, u[1] holds s''
-          const cx<T> F = u[1][e] + mul_i(cscale(u[0][e], d0));
-          // Eq. 20: chi^ = F^ / (i B0.d + A0 L), chi^(0) = 0
-          const T dre = A0 * L, dim = B00 * d0 + B01 * d1 + B02 * d2;
-          cx<T> chi = mk<T>(0, 0);
-          if (!k0 && ok) {
-            const T den = (T)1 / (dre * dre + dim * dim);
-            chi = mk<T>((F.x * dre + F.y * dim) * den, (F.y * dre - F.x * dim) * den);
-          }
-          if (ok) {
-            const cx<T> dch = chi - cs[j];
-            a.st0[gi] = chi;
-            acc0 += wgt * cabs2(dch);
-            acc1 += wgt * dd * cabs2(dch);
-          }
-          // i d0 chi^ and chi^, normalised for the inverse transforms
-          const cx<T> c1 = cscale(chi, invV);
-          u[0][e] = cscale(mul_i(c1), d0);
-          u[1][e] = c1;
-        }
-      }
-    }
-    double v3[3] = {(double)acc0, (double)acc1, (double)acc2};
-    const int nb = gridDim.x * gridDim.y;
-    block_sum_store<3>(v3, red, a.part + ((long long)p * nb + blockIdx.y * gridDim.x + blockIdx.x) * 4);
-    // the last forward transform used buf[(NIN - 1) & 1]; the sums' barriers
-    // separate its reads from the inverse transforms' writes
-#pragma unroll
     for (int c = 0; c < NIN; ++c) {
-      rr_ifft<T, N, +1>(u[c], ((c + NIN) & 1) ? buf1 : buf0, tw, col, t);
-      rr_store_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
+      if constexpr (FWDIN) rr_load_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
+      else rr_load_k<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
     }
+    if constexpr (NST > 0) {
+      rr_prefetch_state<T, N, NST>(a, stp + threadIdx.x, C::NT, p, outer, kx, ok, t);
+      cp_async_commit();
+    }
+    __syncthreads();
+    if constexpr (NST > 0) cp_async_wait<0>();
+    rr_apply<T, N, OP, NC, W>(a, u, p, outer, kx, ok, base, col, t, buf0, buf1, tw, stp + threadIdx.x,
+                              stp + 16 * C::NT + threadIdx.x, C::NT, red,
+                              a.part + ((long long)p * tl.nlive + r) * 4);
+  }
+}
+
+// Persistent, software-pipelined: block b takes the live tiles b, b + G, ...
+// (G = gridDim.x) of all problems, skipping problems that have stopped. The
+// inputs of the next tile are copied by cp.async into the stage [c][row][col]
+// while the current tile is transformed from registers; a z pass copies the
+// next tile's operator state into the thread's private slots once the current
+// operator has read them.
+template <typename T, int N, int OP, int NC, int W>
+__global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rpipe(PassArgs<T> a, int nprob) {
+  constexpr int NIN = rr_nin<OP, NC>(), NST = rr_nst<OP>();
+  using C = RCfg<T, N, W, NST, NIN>;
+  constexpr int TL = N / 16, NT = C::NT;
+  constexpr bool FWDIN = OP == OP_FWD || OP == OP_FWD_SOL || OP == OP_STOKES || OP == OP_SOLUTE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* buf1 = buf0 + W * C::BS;
+  cx<T>* tw = buf1 + W * C::BS;
+  cx<T>* stp = tw + N;                  // state slots [value][element][thread]
+  cx<T>* stage = stp + NST * 16 * NT;   // inputs [component][row][column]
+  __shared__ double red[4 * 32];
+  const RTiles tl = rr_tiles(a.Pu, a.nouter, W);
+  const int ntiles = nprob * tl.nlive;
+  const int col = threadIdx.x % W, t = threadIdx.x / W;
+  auto active = [&](int q) {
+    const int p = q / tl.nlive;
+    return !((a.sprm && a.sprm[p].done) || (a.cprm && a.cprm[p].done));
+  };
+  auto next_tile = [&](int q) {
+    while (q < ntiles && !active(q)) q += gridDim.x;
+    return q;
+  };
+  // the stage copies of tile q: element idx -> (component, row, column)
+  auto issue_inputs = [&](int q) {
+    const int p = q / tl.nlive, r = q % tl.nlive;
+    for (int idx = threadIdx.x; idx < NIN * N * W; idx += NT) {
+      const int cc = idx % W, row = (idx / W) % N, c = idx / (W * N);
+      int o, x;
+      rr_tile_lane(tl, r, W, cc, a.Pu, &o, &x);
+      const bool okc = x < a.Pu;
+      const cx<T>* src = a.spec + p * a.probStride + (long long)o * a.outerStride + x + c * a.compStride +
+                         (long long)row * a.rowStride;
+      cp_async_pred<(int)sizeof(cx<T>)>(&stage[idx], okc ? src : a.spec, okc);
+    }
+  };
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = a.twg[k * (TW_MAX / N)];
+  int q = next_tile(blockIdx.x);
+  if (q < ntiles) {
+    issue_inputs(q);
+    if constexpr (NST > 0) {
+      int o, x;
+      rr_tile_lane(tl, q % tl.nlive, W, col, a.Pu, &o, &x);
+      rr_prefetch_state<T, N, NST>(a, stp + threadIdx.x, NT, q / tl.nlive, o, x, x < a.Pu, t);
+    }
+  }
+  cp_async_commit();
+  while (q < ntiles) {
+    const int p = q / tl.nlive, r = q % tl.nlive;
+    int outer, kx;
+    rr_tile_lane(tl, r, W, col, a.Pu, &outer, &kx);
+    const bool ok = kx < a.Pu;
+    cp_async_wait<0>();
+    __syncthreads();  // the stage of tile q is complete and visible
+    cx<T> u[NIN][16];
+#pragma unroll
+    for (int c = 0; c < NIN; ++c)
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        u[c][e] = stage[(c * N + (FWDIN ? t + TL * e : rr_krow<TL>(t, e))) * W + col];
+    __syncthreads();  // every thread has read the stage
+    const int qn = next_tile(q + gridDim.x);
+    if (qn < ntiles) issue_inputs(qn);
+    cp_async_commit();
+    cx<T>* base = a.spec + p * a.probStride + (long long)outer * a.outerStride + kx;
+    if constexpr (NST > 0) {
+      // rr_apply reads the slots in its operator; the next tile's state is
+      // requested right after, below, by the same thread into the same slots
+      rr_apply<T, N, OP, NC, W>(a, u, p, outer, kx, ok, base, col, t, buf0, buf1, tw, stp + threadIdx.x,
+                                stp + 16 * NT + threadIdx.x, NT, red, a.part + ((long long)p * tl.nlive + r) * 4);
+      if (qn < ntiles) {
+        int o, x;
+        rr_tile_lane(tl, qn % tl.nlive, W, col, a.Pu, &o, &x);
+        rr_prefetch_state<T, N, NST>(a, stp + threadIdx.x, NT, qn / tl.nlive, o, x, x < a.Pu, t);
+      }
+      cp_async_commit();
+    } else {
+      rr_apply<T, N, OP, NC, W>(a, u, p, outer, kx, ok, base, col, t, buf0, buf1, tw, nullptr, nullptr, NT, red,
+                                nullptr);
+    }
+    q = qn;
   }
 }
 

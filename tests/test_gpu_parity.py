@@ -329,19 +329,21 @@ def bench_solute_oracle(n):
     return O.diffusivity_tensor(H, R.state.u, 10.0, O.AdvDiffParams(eps=0.0, max_iter=3))
 
 
-RR_TILES = [-16] * 6          # the register-resident variant of every tuned strided pass (FP32)
+# register-resident variants of every tuned strided pass (FP32): one tile per
+# block (16 columns), and the persistent pipelined kernel (4 columns)
+VARIANT_TILES = {"rr": [-16] * 6, "rp": [-4] * 6}
 
 
 def bench_ctx(lib, shape, tiles):
     """A context with the strided passes at their default tile widths, or all
-    in the register-resident variant (the autotuner's usual pick at these sizes)."""
+    in one register-resident variant (the autotuner's picks at these sizes)."""
     ctx = lib.acm_ctx(shape)
-    if tiles == "rr":
-        lib.acm_set_tiles(ctx, RR_TILES, False)
+    if tiles in VARIANT_TILES:
+        lib.acm_set_tiles(ctx, VARIANT_TILES[tiles], False)
     return ctx
 
 
-@pytest.mark.parametrize("tiles", ["default", "rr"])
+@pytest.mark.parametrize("tiles", ["default", "rr", "rp"])
 @pytest.mark.parametrize("n", [128, 256])
 def test_bench_workload_first_iterations_match_oracle(lib, n, tiles):
     """The bench's pack: the FP32 Stokes path in the bench's launch
@@ -361,7 +363,7 @@ def test_bench_workload_first_iterations_match_oracle(lib, n, tiles):
     assert relerr(p, R.p) < 1e-5
 
 
-@pytest.mark.parametrize("tiles", ["default", "rr"])
+@pytest.mark.parametrize("tiles", ["default", "rr", "rp"])
 @pytest.mark.parametrize("n", [128, 256])
 def test_bench_workload_solute_matches_oracle(lib, n, tiles):
     """The bench's solute step at full size (x lines of 128 / 256, strided
