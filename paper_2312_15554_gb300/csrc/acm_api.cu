@@ -841,7 +841,8 @@ acm_status perm_grad(acm_ctx* c, const uint8_t* Hdev, int deriv, double Kg[9]) {
 // with the local terms of Eq. 18, the y forward pass, the z pass with Eq. 20
 // and the Eq. 19 residuals, the y inverse pass, and the FP64 finalize.
 template <typename T>
-acm_status solute_body(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us, const Sym<T>& sym) {
+acm_status solute_body(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us, const Sym<T>& sym,
+                       int deriv) {
   Prec& w = prec<T>(c);
   Geo g = c->g;
   g.hs = 0;
@@ -850,7 +851,7 @@ acm_status solute_body(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* u
   const long long ps = 4 * g.S;
   // spectral components per problem: x -> (tau_0, tau_1, s + d2 tau_2), y forward -> (tau_0, s''),
   // z -> (d0 chi, chi), y inverse -> (d0 chi, d1 chi, d2 chi)
-  LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym, c->st));
+  LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym, deriv, c->st));
   LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
                                      nullptr, c->st));
   LK(ACM_K_Z_SOLUTE, Ops<T>::pass(g, 0, P_SOLUTE, 2, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm,
@@ -918,7 +919,7 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
     lc.stride[0] = (int)sizeof(SoluteDev);
     lc.ngroups = 1;
     lc.done_off = (int)offsetof(SoluteDev, done);
-    auto capture = [&]() -> acm_status { return solute_body<T>(c, nprob, Hdev, udev, us, sym); };
+    auto capture = [&]() -> acm_status { return solute_body<T>(c, nprob, Hdev, udev, us, sym, P.deriv); };
     return graph_loop_run(c->graph_sol, key, ctxs, capture, lc, c->st);
   }
   // host-launched chunks of check_every iterations; the stop flags are read between chunks
@@ -927,7 +928,7 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
   while (remaining > 0) {
     const int chunk = ce < remaining ? ce : remaining;
     remaining -= chunk;
-    for (int k = 0; k < chunk; ++k) CKS(solute_body<T>(c, nprob, Hdev, udev, us, sym));
+    for (int k = 0; k < chunk; ++k) CKS(solute_body<T>(c, nprob, Hdev, udev, us, sym, P.deriv));
     CK(cudaMemcpyAsync(c->pin, c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     const SoluteDev* hp = (const SoluteDev*)c->pin;
@@ -1293,7 +1294,7 @@ acm_status autotune_ctx(acm_ctx* c, int nprob, int deriv) {
     const int n = j.axis == 1 ? c->g.n1 : c->g.n0;
     float best = 0;
     int best_sh = 0;
-    for (int sh = -1; sh <= 5 && st == ACM_OK; ++sh) {   // 3-5: the register-resident variants
+    for (int sh = -1; sh <= 4 && st == ACM_OK; ++sh) {   // 3, 4: the register-resident variants
       if (!Ops<T>::tx_variant(n, j.op, j.nc, sh)) continue;
       Geo g = c->g;
       g.txs[pr][j.axis][j.op] = (signed char)sh;
@@ -1741,7 +1742,7 @@ acm_status acm_set_tiles(acm_ctx* c, int fp64, const int tiles[NTUNE]) {
     if (j.solute && c->spec_comps < 4) continue;
     const int n = j.axis == 1 ? g.n1 : g.n0;
     bool found = false;
-    for (int sh = -1; sh <= 5 && !found; ++sh) {
+    for (int sh = -1; sh <= 4 && !found; ++sh) {
       if (!(fp64 ? Ops<double>::tx_variant(n, j.op, j.nc, sh) : Ops<float>::tx_variant(n, j.op, j.nc, sh))) continue;
       g.txs[fp64][j.axis][j.op] = (signed char)sh;
       const int tx = fp64 ? Ops<double>::pass_tx(g, j.axis, j.op, j.nc) : Ops<float>::pass_tx(g, j.axis, j.op, j.nc);

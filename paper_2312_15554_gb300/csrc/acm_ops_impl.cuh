@@ -62,7 +62,8 @@ static cudaError_t l_x_rhs(const Geo& g, int nprob, void* spec, const void* u, c
 
 template <typename T, int N2>
 static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                              const uint32_t* Hb, const SoluteDev* prm, const void* tw, const T* d2, cudaStream_t s) {
+                              const uint32_t* Hb, const SoluteDev* prm, const void* tw, const T* d2, int central,
+                              cudaStream_t s) {
   constexpr int smem = xs_smem_bytes<T, N2, 2, 2 * XL<T, N2>::E>();
   static const cudaError_t attr = set_smem(k_x_solute<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
@@ -73,7 +74,7 @@ static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u
   const int ngroups = g.n0 * g.n1 / XL<T, N2>::LPW;
   dim3 grid((ngroups + XS_WARPS * gpw - 1) / (XS_WARPS * gpw), shared ? 1 : nprob);
   k_x_solute<T, N2><<<grid, XS_WARPS * 32, smem, s>>>((cx<T>*)spec, (const T*)u, H, Hb, prm, g, (const cx<T>*)tw,
-                                                        d2, nprob, gpw);
+                                                        d2, nprob, gpw, central);
   return cudaGetLastError();
 }
 
@@ -139,15 +140,14 @@ constexpr bool rr_ok() {
 }
 
 // tile width of (T, N, OP, NC) under the choice `shift`; the register-resident
-// variants (shift 3: W = rr_wdef, shift 4: W = rr_wdef / 2 columns per block,
-// shift 5: the persistent pipelined kernel with W = rr_wdef / 4) report -W
+// variants (shift 3: W = rr_wdef, shift 4: W = rr_wdef / 2 columns per block)
+// report -W
 template <typename T, int N, int OP, int NC>
 constexpr int resolved_tx(int shift) {
   constexpr int TX0 = pick_tx((int)sizeof(cx<T>), N, NC);
   if constexpr (rr_ok<T, N, OP, NC>()) {
     if (shift == 3) return -rr_wdef<T>();
     if (shift == 4) return -rr_wdef<T>() / 2;
-    if (shift == 5) return -rr_wdef<T>() / 4;   // the persistent pipelined variant
   }
   if (tunable<N, OP, NC>()) {
     if (shift < 0 && tx_ok<T, N, OP, NC, TX0 / 2>()) return TX0 / 2;
@@ -215,32 +215,6 @@ static cudaError_t l_pass_rr(const Geo& g, int axis, int nprob, void* spec, long
   return cudaGetLastError();
 }
 
-// The persistent pipelined variant: as many blocks as fit on the device at
-// once (at most one per tile).
-template <typename T, int N, int OP, int NC, int W>
-static cudaError_t l_pass_rp(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
-                             const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
-                             cudaStream_t s) {
-  using C = RCfg<T, N, W, rr_nst<OP>(), rr_nin<OP, NC>()>;
-  static const cudaError_t attr = set_smem(k_rpipe<T, N, OP, NC, W>, C::SMEM);
-  if (attr != cudaSuccess) return attr;
-  static int resident = 0;
-  if (resident == 0) {
-    int dev = 0, nsm = 0, per = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rpipe<T, N, OP, NC, W>, C::NT, C::SMEM) !=
-            cudaSuccess)
-      return cudaGetLastError();
-    resident = (per > 0 ? per : 1) * nsm;
-  }
-  const PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
-  const RTiles tl = rr_tiles(g.Pu, a.nouter, W);
-  const int ntiles = nprob * tl.nlive;
-  k_rpipe<T, N, OP, NC, W><<<ntiles < resident ? ntiles : resident, C::NT, C::SMEM, s>>>(a, nprob);
-  return cudaGetLastError();
-}
-
 template <typename T, int N, int OP, int NC>
 static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
                             const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
@@ -253,9 +227,6 @@ static cudaError_t l_pass_k(const Geo& g, int axis, int nprob, void* spec, long 
                                                    part, s);
     if (sh == 4)
       return l_pass_rr<T, N, OP, NC, rr_wdef<T>() / 2>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm,
-                                                       cprm, part, s);
-    if (sh == 5)
-      return l_pass_rp<T, N, OP, NC, rr_wdef<T>() / 4>(g, axis, nprob, spec, probStride, sym, tw, st0, st1, sprm,
                                                        cprm, part, s);
   }
   if constexpr (tunable<N, OP, NC>()) {
@@ -374,9 +345,9 @@ cudaError_t Ops<T>::x_stokes_rhs(const Geo& g, int nprob, void* spec, const void
 
 template <typename T>
 cudaError_t Ops<T>::x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                             const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym,
+                             const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym, int deriv,
                              cudaStream_t s) {
-  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, Hb, prm, tw, sym.d2, s)
+  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, Hb, prm, tw, sym.d2, deriv == 1 ? 1 : 0, s)
 }
 
 template <typename T>

@@ -25,15 +25,10 @@
 // The transposes alternate between two buffers, so one __syncthreads per
 // transform suffices.
 //
-// Two kernels use these pieces:
-//   k_rstrided  one tile per block; its global loads go straight to registers
-//               (the next component's loads are issued before the current
-//               component's transform).
-//   k_rpipe     persistent blocks that walk over tiles; while a block
-//               transforms tile i from registers, cp.async brings the inputs of
-//               its next tile into a shared-memory stage (and, for a z pass,
-//               the operator state into slots private to each thread), so
-//               memory traffic overlaps the transforms of every resident block.
+// k_rstrided runs one tile per block; its global loads go straight to
+// registers (in the y passes the next component's loads are issued before the
+// current component's transform; a z pass requests all its components and the
+// operator state, which cp.async brings into slots private to each thread).
 #pragma once
 #include "acm_fft.cuh"
 #include "acm_types.h"
@@ -56,14 +51,13 @@ __host__ __device__ constexpr int rr_nin() {
 }
 
 // shared memory of a block (complex elements): two transpose buffers, the
-// twiddles, the per-thread state slots and, in the pipelined kernel, the input
-// stage of one tile
-template <typename T, int N, int W, int NST = 0, int STAGE = 0>
+// twiddles and the per-thread state slots
+template <typename T, int N, int W, int NST = 0>
 struct RCfg {
   static constexpr int TL = N / 16;                        // threads per line
   static constexpr int NT = W * TL;                        // threads per block
   static constexpr int BS = N + 1;                         // column stride of a transpose buffer (odd)
-  static constexpr int SMEM = (2 * W * BS + N + NST * 16 * NT + STAGE * N * W) * (int)sizeof(cx<T>);
+  static constexpr int SMEM = (2 * W * BS + N + NST * 16 * NT) * (int)sizeof(cx<T>);
 };
 
 // The live tiles of one problem: nreg = gxr pencils x column blocks, then (when
@@ -471,97 +465,6 @@ __global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
     rr_apply<T, N, OP, NC, W>(a, u, p, outer, kx, ok, base, col, t, buf0, buf1, tw, stp + threadIdx.x,
                               stp + 16 * C::NT + threadIdx.x, C::NT, red,
                               a.part + ((long long)p * tl.nlive + r) * 4);
-  }
-}
-
-// Persistent, software-pipelined: block b takes the live tiles b, b + G, ...
-// (G = gridDim.x) of all problems, skipping problems that have stopped. The
-// inputs of the next tile are copied by cp.async into the stage [c][row][col]
-// while the current tile is transformed from registers; a z pass copies the
-// next tile's operator state into the thread's private slots once the current
-// operator has read them.
-template <typename T, int N, int OP, int NC, int W>
-__global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rpipe(PassArgs<T> a, int nprob) {
-  constexpr int NIN = rr_nin<OP, NC>(), NST = rr_nst<OP>();
-  using C = RCfg<T, N, W, NST, NIN>;
-  constexpr int TL = N / 16, NT = C::NT;
-  constexpr bool FWDIN = OP == OP_FWD || OP == OP_FWD_SOL || OP == OP_STOKES || OP == OP_SOLUTE;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* buf1 = buf0 + W * C::BS;
-  cx<T>* tw = buf1 + W * C::BS;
-  cx<T>* stp = tw + N;                  // state slots [value][element][thread]
-  cx<T>* stage = stp + NST * 16 * NT;   // inputs [component][row][column]
-  __shared__ double red[4 * 32];
-  const RTiles tl = rr_tiles(a.Pu, a.nouter, W);
-  const int ntiles = nprob * tl.nlive;
-  const int col = threadIdx.x % W, t = threadIdx.x / W;
-  auto active = [&](int q) {
-    const int p = q / tl.nlive;
-    return !((a.sprm && a.sprm[p].done) || (a.cprm && a.cprm[p].done));
-  };
-  auto next_tile = [&](int q) {
-    while (q < ntiles && !active(q)) q += gridDim.x;
-    return q;
-  };
-  // the stage copies of tile q: element idx -> (component, row, column)
-  auto issue_inputs = [&](int q) {
-    const int p = q / tl.nlive, r = q % tl.nlive;
-    for (int idx = threadIdx.x; idx < NIN * N * W; idx += NT) {
-      const int cc = idx % W, row = (idx / W) % N, c = idx / (W * N);
-      int o, x;
-      rr_tile_lane(tl, r, W, cc, a.Pu, &o, &x);
-      const bool okc = x < a.Pu;
-      const cx<T>* src = a.spec + p * a.probStride + (long long)o * a.outerStride + x + c * a.compStride +
-                         (long long)row * a.rowStride;
-      cp_async_pred<(int)sizeof(cx<T>)>(&stage[idx], okc ? src : a.spec, okc);
-    }
-  };
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = a.twg[k * (TW_MAX / N)];
-  int q = next_tile(blockIdx.x);
-  if (q < ntiles) {
-    issue_inputs(q);
-    if constexpr (NST > 0) {
-      int o, x;
-      rr_tile_lane(tl, q % tl.nlive, W, col, a.Pu, &o, &x);
-      rr_prefetch_state<T, N, NST>(a, stp + threadIdx.x, NT, q / tl.nlive, o, x, x < a.Pu, t);
-    }
-  }
-  cp_async_commit();
-  while (q < ntiles) {
-    const int p = q / tl.nlive, r = q % tl.nlive;
-    int outer, kx;
-    rr_tile_lane(tl, r, W, col, a.Pu, &outer, &kx);
-    const bool ok = kx < a.Pu;
-    cp_async_wait<0>();
-    __syncthreads();  // the stage of tile q is complete and visible
-    cx<T> u[NIN][16];
-#pragma unroll
-    for (int c = 0; c < NIN; ++c)
-#pragma unroll
-      for (int e = 0; e < 16; ++e)
-        u[c][e] = stage[(c * N + (FWDIN ? t + TL * e : rr_krow<TL>(t, e))) * W + col];
-    __syncthreads();  // every thread has read the stage
-    const int qn = next_tile(q + gridDim.x);
-    if (qn < ntiles) issue_inputs(qn);
-    cp_async_commit();
-    cx<T>* base = a.spec + p * a.probStride + (long long)outer * a.outerStride + kx;
-    if constexpr (NST > 0) {
-      // rr_apply reads the slots in its operator; the next tile's state is
-      // requested right after, below, by the same thread into the same slots
-      rr_apply<T, N, OP, NC, W>(a, u, p, outer, kx, ok, base, col, t, buf0, buf1, tw, stp + threadIdx.x,
-                                stp + 16 * NT + threadIdx.x, NT, red, a.part + ((long long)p * tl.nlive + r) * 4);
-      if (qn < ntiles) {
-        int o, x;
-        rr_tile_lane(tl, qn % tl.nlive, W, col, a.Pu, &o, &x);
-        rr_prefetch_state<T, N, NST>(a, stp + threadIdx.x, NT, qn / tl.nlive, o, x, x < a.Pu, t);
-      }
-      cp_async_commit();
-    } else {
-      rr_apply<T, N, OP, NC, W>(a, u, p, outer, kx, ok, base, col, t, buf0, buf1, tw, nullptr, nullptr, NT, red,
-                                nullptr);
-    }
-    q = qn;
   }
 }
 

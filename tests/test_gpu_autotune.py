@@ -28,7 +28,7 @@ def _widths(lib, ctx, fp64):
     out = {}
     for k, w in base.items():
         opts = [w]
-        for cand in (w // 2, w * 2, w * 4, -8 if fp64 else -16, -4 if fp64 else -8, -2 if fp64 else -4):
+        for cand in (w // 2, w * 2, w * 4, -8 if fp64 else -16, -4 if fp64 else -8):
             t = dict(base)
             t[k] = cand
             try:
