@@ -841,8 +841,7 @@ acm_status perm_grad(acm_ctx* c, const uint8_t* Hdev, int deriv, double Kg[9]) {
 // with the local terms of Eq. 18, the y forward pass, the z pass with Eq. 20
 // and the Eq. 19 residuals, the y inverse pass, and the FP64 finalize.
 template <typename T>
-acm_status solute_body(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us, const Sym<T>& sym,
-                       int deriv) {
+acm_status solute_body(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* udev, long long us, const Sym<T>& sym) {
   Prec& w = prec<T>(c);
   Geo g = c->g;
   g.hs = 0;
@@ -851,7 +850,7 @@ acm_status solute_body(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* u
   const long long ps = 4 * g.S;
   // spectral components per problem: x -> (tau_0, tau_1, s + d2 tau_2), y forward -> (tau_0, s''),
   // z -> (d0 chi, chi), y inverse -> (d0 chi, d1 chi, d2 chi)
-  LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym, deriv, c->st));
+  LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym, c->st));
   LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
                                      nullptr, c->st));
   LK(ACM_K_Z_SOLUTE, Ops<T>::pass(g, 0, P_SOLUTE, 2, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm,
@@ -919,7 +918,7 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
     lc.stride[0] = (int)sizeof(SoluteDev);
     lc.ngroups = 1;
     lc.done_off = (int)offsetof(SoluteDev, done);
-    auto capture = [&]() -> acm_status { return solute_body<T>(c, nprob, Hdev, udev, us, sym, P.deriv); };
+    auto capture = [&]() -> acm_status { return solute_body<T>(c, nprob, Hdev, udev, us, sym); };
     return graph_loop_run(c->graph_sol, key, ctxs, capture, lc, c->st);
   }
   // host-launched chunks of check_every iterations; the stop flags are read between chunks
@@ -928,7 +927,7 @@ acm_status solute_run(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* ud
   while (remaining > 0) {
     const int chunk = ce < remaining ? ce : remaining;
     remaining -= chunk;
-    for (int k = 0; k < chunk; ++k) CKS(solute_body<T>(c, nprob, Hdev, udev, us, sym, P.deriv));
+    for (int k = 0; k < chunk; ++k) CKS(solute_body<T>(c, nprob, Hdev, udev, us, sym));
     CK(cudaMemcpyAsync(c->pin, c->cprm, nprob * sizeof(SoluteDev), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     const SoluteDev* hp = (const SoluteDev*)c->pin;

@@ -395,9 +395,7 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
 // Solute x-pass: C2R of the gradient of chi^n (3 components), local terms of Eq. 18:
 //   tau = (A - A0)(grad chi + g),  s = F - (B - B0).(grad chi + g),
 //   A = (1 - H) + eta H,  B = Pe (1 - H) u,  F = Pe (1 - H) ubar.g,
-// then R2C of (tau_0, tau_1, tau_2, s), stored as (tau_0, tau_1, s + i d2 tau_2);
-// with the Eq. 21 symbols (central = 1) i d2 tau_2 is added to s in real space
-// as the central difference it stands for, and tau_2 is not transformed.
+// then R2C of (tau_0, tau_1, tau_2, s), stored as (tau_0, tau_1, s + i d2 tau_2).
 //
 // Line-resident (acm_xline.cuh): every warp owns LPW lines; their three
 // spectrum rows arrive by cp.async, then each component is inverse-transformed
@@ -408,7 +406,7 @@ template <typename T, int N2>
 __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
     k_x_solute(cx<T>* __restrict__ spec, const T* __restrict__ u, const uint8_t* __restrict__ H,
                const uint32_t* __restrict__ Hb, const SoluteDev* __restrict__ prm, Geo g,
-               const cx<T>* __restrict__ twg, const T* __restrict__ d2, int nprob, int gpw, int central) {
+               const cx<T>* __restrict__ twg, const T* __restrict__ d2, int nprob, int gpw) {
   using L = XL<T, N2>;
   constexpr int M = L::M, E = L::E, TL = L::TL, LPW = L::LPW, LS = L::LS;
   constexpr int LB = L::template lb<2>();
@@ -490,32 +488,6 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
             v[m].x = ((sa ? eta : (T)1) - A0) * ea;
             v[m].y = ((sb ? eta : (T)1) - A0) * eb;
           }
-          if (central && c == 2) {
-            // With the Eq. 21 symbol, i d2 tau_2^ is exactly the transform of the
-            // central difference (tau_2(x + h) - tau_2(x - h)) / 2h along the line:
-            // it joins s here and tau_2 needs no forward transform. The lane's
-            // voxels are 2k, 2k + 1 (k = t + TL m); their neighbours 2k - 1 and
-            // 2k + 2 belong to pairs k - 1 and k + 1 of lanes t - 1 and t + 1
-            // (lane TL - 1 of m - 1 and lane 0 of m + 1 at the ends, periodic).
-            const T h2 = (T)(N2 / 2);
-            const int lb = lane - t;
-            const int src_prev = lb + (t + TL - 1) % TL, src_next = lb + (t + 1) % TL;
-            T rp = __shfl_sync(mask, v[E - 1].y, src_prev);
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-              const T r = __shfl_sync(mask, v[m].y, src_prev);
-              acc[(2 * m) * 32 + lane] += h2 * (v[m].y - (t == 0 ? rp : r));
-              rp = r;
-            }
-            T qn = __shfl_sync(mask, v[0].x, src_next);
-#pragma unroll
-            for (int m = E - 1; m >= 0; --m) {
-              const T q = __shfl_sync(mask, v[m].x, src_next);
-              acc[(2 * m + 1) * 32 + lane] += h2 * ((t == TL - 1 ? qn : q) - v[m].x);
-              qn = q;
-            }
-            continue;
-          }
         } else {
           // s = F - (B - B0).(grad chi + g): the accumulated terms plus Pe ubar.g on pore voxels
           const T Fc = (T)P->Fc;
@@ -546,12 +518,6 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
           for (int m = 0; m < E; ++m) b1[pad(t + TL * m)] = cscale(mul_i(v[m]), d2[t + TL * m]);
           if (t == 0) b1[pad(M)] = cscale(mul_i(xn), d2[M]);
-        } else if (central) {
-          // s + i d2 tau_2 was formed in real space
-          cx<T>* dst = sp + 2 * g.S + line * g.P;
-#pragma unroll
-          for (int m = 0; m < E; ++m) dst[t + TL * m] = v[m];
-          if (t == 0) dst[M] = xn;
         } else {
           cx<T>* dst = sp + 2 * g.S + line * g.P;
 #pragma unroll

@@ -29,10 +29,9 @@ struct Ops {
   static cudaError_t x_stokes_rhs(const Geo& g, int nprob, void* spec, const void* u, const void* lam,
                                   const uint8_t* H, const uint32_t* Hb, const StokesDev* prm, const void* tw,
                                   cudaStream_t s);
-  // deriv 1 (the Eq. 21 symbols): the axis-2 derivative of tau_2 as a central difference in real space
   static cudaError_t x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
                               const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym,
-                              int deriv, cudaStream_t s);
+                              cudaStream_t s);
   // nc in {1, 3}
   static cudaError_t x_r2c(const Geo& g, int nprob, int nc, void* spec, long long specProbStride,
                            const void* in, long long inProbStride, const void* tw, cudaStream_t s);

@@ -62,8 +62,7 @@ static cudaError_t l_x_rhs(const Geo& g, int nprob, void* spec, const void* u, c
 
 template <typename T, int N2>
 static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                              const uint32_t* Hb, const SoluteDev* prm, const void* tw, const T* d2, int central,
-                              cudaStream_t s) {
+                              const uint32_t* Hb, const SoluteDev* prm, const void* tw, const T* d2, cudaStream_t s) {
   constexpr int smem = xs_smem_bytes<T, N2, 2, 2 * XL<T, N2>::E>();
   static const cudaError_t attr = set_smem(k_x_solute<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
@@ -74,7 +73,7 @@ static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u
   const int ngroups = g.n0 * g.n1 / XL<T, N2>::LPW;
   dim3 grid((ngroups + XS_WARPS * gpw - 1) / (XS_WARPS * gpw), shared ? 1 : nprob);
   k_x_solute<T, N2><<<grid, XS_WARPS * 32, smem, s>>>((cx<T>*)spec, (const T*)u, H, Hb, prm, g, (const cx<T>*)tw,
-                                                        d2, nprob, gpw, central);
+                                                        d2, nprob, gpw);
   return cudaGetLastError();
 }
 
@@ -345,9 +344,9 @@ cudaError_t Ops<T>::x_stokes_rhs(const Geo& g, int nprob, void* spec, const void
 
 template <typename T>
 cudaError_t Ops<T>::x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                             const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym, int deriv,
+                             const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym,
                              cudaStream_t s) {
-  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, Hb, prm, tw, sym.d2, deriv == 1 ? 1 : 0, s)
+  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, Hb, prm, tw, sym.d2, s)
 }
 
 template <typename T>
