@@ -16,8 +16,13 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- * Grid      (n0, n1, n2), each a power of two in [8, 512]; axis 2 is contiguous.
- *           The cell is the unit cube; h_c = 1/n_c; V = n0*n1*n2 voxels.
+ * Grid      (n0, n1, n2): n1 and n2 powers of two in [8, 512], n0 the same or 1;
+ *           axis 2 is contiguous. The cell is the unit cube; h_c = 1/n_c;
+ *           V = n0*n1*n2 voxels. n0 = 1 is a single plane: the two-dimensional
+ *           cell of the paper's experiments (Section 4), with the symbols of
+ *           axis 0 equal to zero (no variation along it); vector fields keep
+ *           three components (component 0, the flow along the cylinders of an
+ *           extruded geometry, decouples from the in-plane ones).
  * H         uint8_t[n0][n1][n2], 1 = solid, 0 = pore (Eq. 4).
  * Vectors   component-planar [3][n0][n1][n2]; component c is along array axis c.
  *           Load direction e_j therefore means array axis j.
@@ -139,8 +144,8 @@ acm_status acm_advdiff_default_params(acm_advdiff_params* p);
 
 /* Create a context for grids of shape (n0, n1, n2) whose device work runs on
  * `cuda_stream` (a cudaStream_t, NULL for the default stream) of the current
- * device. Returns ACM_ERR_UNSUPPORTED_SIZE unless every n_c is a power of two
- * in [8, 512]. */
+ * device. Returns ACM_ERR_UNSUPPORTED_SIZE unless n1 and n2 are powers of two
+ * in [8, 512] and n0 is one too or 1. */
 acm_status acm_create(acm_ctx** ctx, int n0, int n1, int n2, void* cuda_stream);
 acm_status acm_destroy(acm_ctx* ctx);
 
@@ -209,8 +214,8 @@ acm_status acm_fft_c2r(acm_ctx* ctx, int fp64, int nbatch, const void* in, void*
  * the three unit loads of every cell, solved in one device-resident loop. Cells
  * of one shape share every kernel launch; each problem keeps its own penalties
  * (Eq. 22) and stop flag, and converged problems stop doing work.
- *   acm_batch_create  ncells cells with shapes dims[ncells][3] (host), each a
- *                     power of two in [8, 512]; the workspace of all cells is
+ *   acm_batch_create  ncells cells with shapes dims[ncells][3] (host), each
+ *                     a grid acm_create accepts; the workspace of all cells is
  *                     allocated here (about 95 MB per 128^3 cell in FP32).
  *   acm_batch_stokes  H: host array of ncells indicator pointers (device or
  *                     host); prm: precision ACM_FP32 or ACM_FP64 (the mixed

@@ -57,8 +57,11 @@ def axis_symbols(n: int, deriv: int):
     Returns (d, l) with d/dx <-> i*d and -d^2/dx^2 <-> l, for integer
     frequencies m in DFT order (0..n/2-1, -n/2..-1).
     """
+    if n == 1:
+        # a single plane (two-dimensional cell): the only mode is m = 0
+        return np.zeros(1), np.zeros(1)
     if n < 2 or n % 2:
-        raise ValueError("axis length must be even and >= 2")
+        raise ValueError("axis length must be 1, or even and >= 2")
     h = 1.0 / n
     m = np.concatenate([np.arange(0, n // 2), np.arange(-(n // 2), 0)]).astype(np.float64)
     k = 2.0 * np.pi * m
@@ -132,8 +135,10 @@ class StokesParams:
 
 def default_penalty(shape, nu: float) -> float:
     """Initial penalty when none is given: nu times the squared wavenumber of the
-    geometric mean grid spacing (the stiffness of a voxel-scale mode)."""
-    n = float(np.prod(shape)) ** (1.0 / 3.0)
+    geometric mean grid spacing (the stiffness of a voxel-scale mode); the mean
+    is taken over the axes longer than one voxel (the plane of a 2D cell)."""
+    ax = [n for n in shape if n > 1]
+    n = float(np.prod(ax)) ** (1.0 / len(ax))
     return nu * (np.pi * n) ** 2 / 8.0
 
 

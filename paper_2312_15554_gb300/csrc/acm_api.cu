@@ -165,6 +165,10 @@ void prof_end(acm_ctx* c) {
 
 bool pow2_in_range(int n) { return n >= 8 && n <= 512 && (n & (n - 1)) == 0; }
 
+// Supported grids: n1, n2 powers of two in [8, 512]; n0 the same or 1 (a
+// single plane: the two-dimensional problem of the paper's experiments).
+bool shape_ok(int n0, int n1, int n2) { return (n0 == 1 || pow2_in_range(n0)) && pow2_in_range(n1) && pow2_in_range(n2); }
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -356,8 +360,9 @@ void fill_stokes_params(const acm_stokes_params* in, acm_stokes_params* out) {
 }
 
 double default_penalty(const Geo& g, double nu) {
-  // nu times the squared wavenumber of the geometric-mean grid spacing / 8
-  const double n = std::cbrt((double)g.n0 * g.n1 * g.n2);
+  // nu times the squared wavenumber of the geometric-mean grid spacing / 8, the
+  // mean taken over the axes longer than one voxel (both in-plane axes of a plane)
+  const double n = g.n0 > 1 ? std::cbrt((double)g.n0 * g.n1 * g.n2) : std::sqrt((double)g.n1 * g.n2);
   const double PI = 3.14159265358979323846;
   return nu * (PI * n) * (PI * n) / 8.0;
 }
@@ -1350,7 +1355,7 @@ void tiles_of(const acm_ctx* c, int fp64, int tiles[NTUNE]) {
 acm_status ctx_create(acm_ctx** out, int n0, int n1, int n2, void* stream, int B, int ncells) {
   if (!out || B < 1 || ncells < 1) return ACM_ERR_ARG;
   *out = nullptr;
-  if (!pow2_in_range(n0) || !pow2_in_range(n1) || !pow2_in_range(n2)) return ACM_ERR_UNSUPPORTED_SIZE;
+  if (!shape_ok(n0, n1, n2)) return ACM_ERR_UNSUPPORTED_SIZE;
   acm_ctx* c = new (std::nothrow) acm_ctx();
   if (!c) return ACM_ERR_NOMEM;
   c->n0 = n0;
@@ -1645,7 +1650,7 @@ acm_status acm_batch_create(acm_batch** out, int ncells, const int* dims, void* 
   b->ncells = ncells;
   for (int i = 0; i < ncells; ++i) {
     const int* d = dims + 3 * i;
-    if (!pow2_in_range(d[0]) || !pow2_in_range(d[1]) || !pow2_in_range(d[2])) {
+    if (!shape_ok(d[0], d[1], d[2])) {
       delete b;
       return ACM_ERR_UNSUPPORTED_SIZE;
     }

@@ -24,6 +24,21 @@ static cudaError_t set_smem(K* k, int bytes) {
                            : cudaSuccess;
 }
 
+// the strided passes also take lines of one point (axis 0 of a single plane):
+// the transform is the identity and the pass applies its operator
+#define ACM_DISPATCH_NS(n, FN, ...)             \
+  switch (n) {                                  \
+    case 1: return FN<T, 1>(__VA_ARGS__);       \
+    case 8: return FN<T, 8>(__VA_ARGS__);       \
+    case 16: return FN<T, 16>(__VA_ARGS__);     \
+    case 32: return FN<T, 32>(__VA_ARGS__);     \
+    case 64: return FN<T, 64>(__VA_ARGS__);     \
+    case 128: return FN<T, 128>(__VA_ARGS__);   \
+    case 256: return FN<T, 256>(__VA_ARGS__);   \
+    case 512: return FN<T, 512>(__VA_ARGS__);   \
+    default: return cudaErrorInvalidValue;      \
+  }
+
 #define ACM_DISPATCH_N(n, FN, ...)     \
   switch (n) {                         \
     case 8: return FN<T, 8>(__VA_ARGS__);     \
@@ -299,6 +314,7 @@ int Ops<T>::pass_tx(const Geo& g, int axis, int op, int nc) {
   const int n = axis == 1 ? g.n1 : g.n0;
   const int sh = g.txs[sizeof(T) == 8][axis][op];
   switch (n) {
+    case 1: return l_pass_tx<T, 1>(op, nc, sh);
     case 8: return l_pass_tx<T, 8>(op, nc, sh);
     case 16: return l_pass_tx<T, 16>(op, nc, sh);
     case 32: return l_pass_tx<T, 32>(op, nc, sh);
@@ -368,7 +384,7 @@ cudaError_t Ops<T>::pass(const Geo& g, int axis, int op, int nc, int nprob, void
   const int n = axis == 1 ? g.n1 : g.n0;
   if ((op == P_STOKES || op == P_SOLUTE || op == P_DERIV) && axis != 0) return cudaErrorInvalidValue;
   if ((op == P_FWD_SOL || op == P_INV_SOL) && axis != 1) return cudaErrorInvalidValue;
-  ACM_DISPATCH_N(n, l_pass, g, axis, op, nc, nprob, spec, ps, sym, tw, st0, st1, sprm, cprm, part, s, dm)
+  ACM_DISPATCH_NS(n, l_pass, g, axis, op, nc, nprob, spec, ps, sym, tw, st0, st1, sprm, cprm, part, s, dm)
 }
 
 template <typename T>

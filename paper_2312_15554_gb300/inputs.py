@@ -88,6 +88,44 @@ def single_sphere(shape, radius: float = 0.3, centre=(0.5, 0.5, 0.5)) -> np.ndar
     return H
 
 
+def single_cylinder(shape, radius: float = 0.3, centre=(0.5, 0.5)) -> np.ndarray:
+    """One solid disk of radius `radius` (unit-cell units) at `centre` of the
+    (axis 1, axis 2) plane, the same on every plane along axis 0 (a cylinder;
+    with shape (1, n, n) the two-dimensional cell)."""
+    shape = tuple(int(s) for s in shape)
+    H = np.zeros(shape, dtype=np.uint8)
+    d1 = _periodic_delta(np.arange(shape[1]), shape[1], centre[0] * shape[1]) / shape[1]
+    d2 = _periodic_delta(np.arange(shape[2]), shape[2], centre[1] * shape[2]) / shape[2]
+    H[:, d1[:, None] ** 2 + d2[None, :] ** 2 <= radius * radius] = 1
+    return H
+
+
+def disk_pack(n1: int, n2: int, target_porosity: float, radius_vox, seed: int, max_disks: int = 1_000_000):
+    """Boolean (overlapping) pack of disks in a (1, n1, n2) cell, the
+    two-dimensional analogue of sphere_pack: centres uniform in the plane from
+    SplitMix64(seed) (two uniforms per disk, then one for the radius when
+    `radius_vox` is a (lo, hi) range), added until the porosity is at most
+    `target_porosity`."""
+    H = np.zeros((1, n1, n2), dtype=np.uint8)
+    rng = SplitMix64(seed)
+    target_solid = (1.0 - target_porosity) * H.size
+    ranged = not np.isscalar(radius_vox)
+    i1, i2 = np.arange(n1) + 0.5, np.arange(n2) + 0.5
+    ndisks = 0
+    while np.count_nonzero(H) < target_solid:
+        if ndisks >= max_disks:
+            raise RuntimeError("disk_pack: disk budget exhausted")
+        c1, c2 = rng.uniform() * n1, rng.uniform() * n2
+        r = (radius_vox[0] + (radius_vox[1] - radius_vox[0]) * rng.uniform()) if ranged else float(radius_vox)
+        d1 = np.abs(i1 - c1)
+        d1 = np.minimum(d1, n1 - d1)
+        d2 = np.abs(i2 - c2)
+        d2 = np.minimum(d2, n2 - d2)
+        H[0][d1[:, None] ** 2 + d2[None, :] ** 2 <= r * r] = 1
+        ndisks += 1
+    return H
+
+
 def slab(shape, solid_layers: int, normal_axis: int = 1) -> np.ndarray:
     """Plane channel: the first `solid_layers` layers normal to `normal_axis` are solid."""
     H = np.zeros(tuple(shape), dtype=np.uint8)

@@ -117,7 +117,7 @@ def test_one_admm_iteration_satisfies_step_1_exact_dft_matrices():
 # converged ADMM = dense KKT solve of the discrete Stokes problem
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("deriv", [O.CENTRAL, O.EXACT])
-@pytest.mark.parametrize("shape,seed", [((4, 4, 4), 3), ((6, 4, 6), 5)])
+@pytest.mark.parametrize("shape,seed", [((4, 4, 4), 3), ((6, 4, 6), 5), ((1, 8, 6), 7)])
 def test_converged_stokes_matches_dense_kkt(deriv, shape, seed):
     H = I.random_indicator(shape, 0.35, seed)
     if H.sum() == 0:
@@ -364,6 +364,44 @@ def test_sphere_array_permeability_hasimoto():
 
 
 # --------------------------------------------------------------------------
+# the two-dimensional cell (one plane, n0 = 1): the paper's own setting
+# --------------------------------------------------------------------------
+def square_cylinder_array(c):
+    """Permeability of a square array of cylinders at solid fraction c (unit
+    cell, nu = 1, flow across the cylinders): the dilute expansion of the drag
+    of Sangani & Acrivos (1982) and Drummond & Tahir (1984),
+    K = (-ln c - 1.476 + 2 c - 1.774 c^2 + 4.076 c^3) / (8 pi)."""
+    return (-np.log(c) - 1.476 + 2 * c - 1.774 * c**2 + 4.076 * c**3) / (8 * np.pi)
+
+
+def test_square_cylinder_array_permeability_2d():
+    """One disk of radius 0.2 (c about 0.125) in a plane cell, central symbols:
+    within 3% of the array formula at 64^2 and closer than at 32^2 (the grid
+    converges towards it: 1.1% at 128^2); no transverse flow."""
+    errs = []
+    for n in (32, 64):
+        H = I.single_cylinder((1, n, n), 0.2)
+        R = O.stokes(H, [0.0, 0.0, 1.0], O.StokesParams(eps=1e-9, alpha0=300, beta0=300, b0=300,
+                                                        adaptive=False, max_iter=60000, deriv=O.CENTRAL))
+        assert R.converged
+        errs.append(abs(R.K_col[2] / square_cylinder_array(H.mean()) - 1))
+        assert abs(R.K_col[1]) < 1e-12 and abs(R.K_col[0]) < 1e-12
+    assert errs[1] < 0.03 and errs[1] < errs[0]
+
+
+def test_plane_poiseuille_in_a_plane_cell_central_closed_form():
+    """A channel in the plane (walls normal to axis 1, flow along axis 2) has
+    the discrete profile u_j = h^2 j (m + 1 - j) / 2 of the 3D slab."""
+    n, s = 16, 5
+    m, h = n - s, 1.0 / n
+    H = I.slab((1, n, n), s, normal_axis=1)
+    R = O.stokes(H, [0.0, 0.0, 1.0], O.StokesParams(eps=1e-12, alpha0=300, beta0=300, b0=300, adaptive=False,
+                                                    max_iter=60000, deriv=O.CENTRAL))
+    assert R.converged
+    assert R.K_col[2] == pytest.approx(h * h * m * (m + 1) * (m + 2) / (12.0 * n), rel=1e-8)
+
+
+# --------------------------------------------------------------------------
 # invariants
 # --------------------------------------------------------------------------
 def test_admm_invariants():
@@ -447,7 +485,7 @@ def test_one_ls_iteration_satisfies_eq17_with_stencils():
     np.testing.assert_allclose(R.grad_chi, DO.grad_fd(chi1), atol=1e-10 * np.abs(R.grad_chi).max())
 
 
-@pytest.mark.parametrize("shape,seed", [((4, 4, 4), 61), ((6, 4, 6), 62)])
+@pytest.mark.parametrize("shape,seed", [((4, 4, 4), 61), ((6, 4, 6), 62), ((1, 8, 6), 63)])
 def test_converged_ls_matches_dense_fixed_point(shape, seed):
     H = I.random_indicator(shape, 0.4, seed)
     u = 0.2 * I.random_field((3,) + shape, seed + 1)
