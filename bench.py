@@ -345,9 +345,18 @@ def run_gpu(args, rank, world, dist):
 
     # time to permeability on one GPU only (several ranks would each hold a GPU for it)
     ttk = time_to_permeability(acm, ctx, Hd, stream, args.ttk_long) if (args.ttk and world == 1) else None
-    ttk_c = (time_to_permeability(acm, ctx, Hd, stream, args.ttk_long_central, deriv=acm.DERIV_CENTRAL,
-                                  fixed_penalty=4.0)
-             if (args.ttk and world == 1 and args.ttk_long_central > 0) else None)
+    ttk_c = None
+    if args.ttk and world == 1 and args.ttk_iters > 0:
+        from paper_2312_15554_gb300 import ttk as TTK
+        t_ref = time.perf_counter()
+        K_ref, ref = TTK.reference_single(acm, Hd, eps=1e-10)
+        ref_s = time.perf_counter() - t_ref
+        ttk_c = TTK.plain(acm, ctx, Hd, stream, args.ttk_iters, K_ref)
+        ttk_c.update({"K_ref": K_ref.tolist(), "reference": {"kind": "FP64 tensor solve at eps 1e-10, voxel units "
+                                                                     "(nu = h^2), scaled to the cell's units",
+                                                             "seconds": ref_s, **ref},
+                      "form": "plain (FP32, unit cell, nu = 1), approximate derivative symbols (Eq. 21), fixed "
+                              f"penalties {TTK.PORE_SCALE:g} / l^2 x the default (pore length l)"})
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -385,7 +394,7 @@ def run_gpu(args, rank, world, dist):
     if ttk is not None:
         line["time_to_permeability"] = ttk
     if ttk_c is not None:
-        line["time_to_permeability_central"] = ttk_c
+        line["time_to_permeability_fp64_reference"] = ttk_c
     print(json.dumps(line), flush=True)
 
 
@@ -442,45 +451,15 @@ def run_batched(args, rank, world, dist):
     ms = e0.elapsed_time(e1)
     ttk = None
     if args.ttk_batched > 0 and world == 1:
-        # time to permeability of the batched form: every problem's K after every
-        # iteration (batch history), crossing iterations per cell against the
-        # cell's own last tensor, times the batch's time per iteration
-        n_it = args.ttk_batched
-        acm.acm_batch_history_enable(batch, n_it)
-        pl = acm.stokes_params(eps=0.0, max_iter=n_it, precision=acm.FP32)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        acm.acm_batch_stokes(batch, Hd, pl)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        per_iter = f0.elapsed_time(f1) / 1e3 / n_it
-        crossing = {r: [] for r in (1e-1, 3e-2, 1e-2)}
-        tails = []
-        for cell in range(len(shapes)):
-            hs = [acm.acm_batch_history(batch, cell, j) for j in range(3)]
-            m = min(len(h) for h in hs)
-            Kn = np.stack([hs[j][:m, 15:18] for j in range(3)], axis=-1)
-            Kr = Kn[-1]
-            err = np.linalg.norm(Kn - Kr, axis=(1, 2)) / np.linalg.norm(Kr)
-            tail = float(np.linalg.norm(Kn[-1] - Kn[max(0, m - 1 - m // 10)]) / np.linalg.norm(Kr))
-            tails.append(tail)
-            for rel in crossing:
-                bad = np.nonzero(err > rel)[0]
-                ok = rel > tail and (len(bad) == 0 or bad[-1] + 1 < m)
-                crossing[rel].append((int(bad[-1]) + 2 if len(bad) else 1) if ok else None)
-        acm.acm_batch_history_enable(batch, 0)
-        ttk = {"iterations": n_it, "seconds_per_batch_iteration": per_iter,
-               "reference": "each cell's tensor after the last iteration",
-               "reference_last10pct_change_median": float(np.median(tails)), "thresholds": {}}
-        for rel, xs in crossing.items():
-            got = [x for x in xs if x is not None]
-            ttk["thresholds"][f"{rel:g}"] = {
-                "cells_resolved": len(got), "cells": len(xs),
-                "iterations_median": float(np.median(got)) if got else None,
-                "iterations_max": int(max(got)) if got else None,
-                "seconds_all_resolved_cells": (max(got) * per_iter) if got else None}
+        # time to permeability of the batched form (Eq. 21 symbols, pore-scale
+        # fixed penalties): every problem's K after every iteration of one
+        # batched FP32 run, each cell against its FP64 limit at eps 1e-10
+        from paper_2312_15554_gb300 import ttk as TTK
+        r = TTK.batched(acm, Hd, args.ttk_batched, stream)
+        r.pop("n_star")
+        r.pop("K_ref")
+        ttk = {"form": "batched (FP32, nu = 1), approximate derivative symbols (Eq. 21), fixed penalties "
+                       f"{TTK.PORE_SCALE:g} / l^2 x the default per cell", **r}
     # per-kernel shares of one more step, host-launched with CUDA events
     acm.acm_batch_profile_read(batch)
     acm.acm_batch_profile_enable(batch, True)
@@ -635,9 +614,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ttk", action=argparse.BooleanOptionalAction, default=True,
                     help="also measure time-to-permeability (K within 1e-4 of a long-run reference)")
-    ap.add_argument("--ttk-long", type=int, default=20000, help="iterations of the reference run")
-    ap.add_argument("--ttk-long-central", type=int, default=8000,
-                    help="iterations of the reference run with the Eq. 21 symbols (0: skip that form)")
+    ap.add_argument("--ttk-long", type=int, default=8000,
+                    help="iterations of the library-default form's self-referenced run")
+    ap.add_argument("--ttk-iters", type=int, default=1000,
+                    help="iterations of the FP32 run timed against the FP64 reference (0: skip that form)")
     ap.add_argument("--config", default="cell256", choices=["cell256", "batched", "grf512"],
                     help="cell256: the 256^3 cell (default); batched: 384 cells (192 at 64^3, 192 at 128^3); "
                          "grf512: the 512^3 Gaussian random field with the FP32/FP64 comparison")

@@ -103,6 +103,13 @@ typedef struct acm_stokes_params {
   int check_every;     /* iterations between host checks of the stop flag (default 16) */
   int device_loop;     /* 1: the whole iteration loop is one device-resident CUDA graph
                           launch (default); 0: host-launched chunks of check_every */
+  double pore_scale;   /* > 0: every penalty not given explicitly starts at
+                          pore_scale / l^2 times its default, l = (pore voxels) /
+                          (solid-pore voxel faces) of the cell, in voxels (per cell in
+                          a batch). Not part of the paper: Eq. 22 compares a velocity
+                          with a penalty times a velocity, so the best fixed penalty
+                          follows the pore scale; 9 with adaptive = 0 is the measured
+                          choice for time to permeability. 0 (default): off */
 } acm_stokes_params;
 
 /* Solute (Lippmann-Schwinger) parameters, Section 3.2. */

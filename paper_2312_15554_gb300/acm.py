@@ -40,7 +40,7 @@ class acm_stokes_params(C.Structure):
                 ("b0", C.c_double), ("phi", C.c_double * 3), ("tau", C.c_double * 3),
                 ("psi_min_frac", C.c_double), ("eps32", C.c_double), ("max_iter", C.c_int),
                 ("adaptive", C.c_int), ("deriv", C.c_int), ("precision", C.c_int), ("check_every", C.c_int),
-                ("device_loop", C.c_int)]
+                ("device_loop", C.c_int), ("pore_scale", C.c_double)]
 
 
 class acm_advdiff_params(C.Structure):

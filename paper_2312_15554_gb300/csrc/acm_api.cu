@@ -370,7 +370,8 @@ double default_penalty(const Geo& g, double nu) {
 template <typename T>
 acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs, int lph, const double (*gs)[3],
                         const acm_stokes_params& P, double eps, const void* const* init_u,
-                        const void* const* init_lam, const int* preset_status = nullptr, int stall_win = 0) {
+                        const void* const* init_lam, const int* preset_status = nullptr, int stall_win = 0,
+                        const double* pore_l = nullptr) {
   CKS(ensure_prec<T>(c));
   Prec& w = prec<T>(c);
   Geo g = c->g;
@@ -418,9 +419,11 @@ acm_status stokes_setup(acm_ctx* c, int nprob, const uint8_t* Hdev, long long hs
       d.phi[k] = P.phi[k];
       d.tau[k] = P.tau[k];
     }
-    d.psi[0] = P.alpha0 > 0 ? P.alpha0 : p0;
-    d.psi[1] = P.beta0 > 0 ? P.beta0 : p0;
-    d.psi[2] = P.b0 > 0 ? P.b0 : p0;
+    // pore-scale rule: penalties not given start at pore_scale / l^2 times the default
+    const double pd = (P.pore_scale > 0 && pore_l && pore_l[p] > 0) ? p0 * P.pore_scale / (pore_l[p] * pore_l[p]) : p0;
+    d.psi[0] = P.alpha0 > 0 ? P.alpha0 : pd;
+    d.psi[1] = P.beta0 > 0 ? P.beta0 : pd;
+    d.psi[2] = P.b0 > 0 ? P.b0 : pd;
     for (int k = 0; k < 3; ++k) d.psi_min[k] = P.psi_min_frac * d.psi[k];
     // u~^0 = u^0 on the solid: s_prev = b_prev / (b_prev + alpha_prev) = 1
     d.psi_prev[0] = 0.0;
@@ -736,7 +739,8 @@ acm_status stokes_reports(acm_ctx* c, int nprob, acm_report* rep, int fp64_from,
 
 acm_status check_stokes_args(const acm_stokes_params& P) {
   if (!(P.nu > 0) || !(P.eps >= 0) || P.max_iter < 1 || (P.device_loop != 0 && P.device_loop != 1) || (P.deriv != 0 && P.deriv != 1) || P.precision < 0 ||
-      P.precision > 2 || !(P.psi_min_frac > 0) || !(P.eps32 > 0))
+      P.precision > 2 || !(P.psi_min_frac > 0) || !(P.eps32 > 0) || !(P.pore_scale >= 0) ||
+      !std::isfinite(P.pore_scale))
     return ACM_ERR_ARG;
   for (int k = 0; k < 3; ++k)
     if (!(P.phi[k] >= 1.0) || !(P.tau[k] >= 1.0)) return ACM_ERR_ARG;
@@ -759,16 +763,25 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
   if (Hdev != c->Hd) CK(cudaMemcpyAsync(c->Hd, Hdev, (size_t)c->g.V, cudaMemcpyDeviceToDevice, c->st));
   Hdev = c->Hd;  // one stable buffer, so a cached device loop stays valid
   LK(ACM_K_OTHER, pack_hbits(c->Hd, c->Hb, c->g.V, c->st));
+  std::vector<double> pore_l(nprob, 0.0);
+  if (P.pore_scale > 0) {
+    CK(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long), c->st));
+    LK(ACM_K_OTHER, count_faces_add(c->Hd, c->n0, c->n1, c->n2, c->cnt, c->st));
+    CK(cudaMemcpyAsync(c->pin, c->cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    const double faces = (double)*(unsigned long long*)c->pin;
+    for (auto& x : pore_l) x = (double)(c->g.V - nsolid) / faces;
+  }
   const bool dl = P.device_loop != 0;
   acm_status st = ACM_OK;
   const std::vector<const void*> iu(nprob, init_u), il(nprob, init_lam);
   if (P.precision == ACM_FP32) {
-    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, P.eps, iu.data(), il.data()));
+    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, P.eps, iu.data(), il.data(), nullptr, 0, pore_l.data()));
     CKS(stokes_iterate<float>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     CKS(stokes_outputs<float>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
     st = stokes_reports(c, nprob, rep, -1, t0);
   } else if (P.precision == ACM_FP64) {
-    CKS(stokes_setup<double>(c, nprob, Hdev, 0, 1, gs, P, P.eps, iu.data(), il.data()));
+    CKS(stokes_setup<double>(c, nprob, Hdev, 0, 1, gs, P, P.eps, iu.data(), il.data(), nullptr, 0, pore_l.data()));
     CKS(stokes_iterate<double>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     CKS(stokes_outputs<double>(c, nprob, u_out, u_stride, p_out, lam_out, Kcol));
     st = stokes_reports(c, nprob, rep, -2, t0);
@@ -776,7 +789,8 @@ acm_status stokes_solve(acm_ctx* c, int nprob, const uint8_t* H, const double (*
     // FP32 iterations to eps32 (warm start given in double is cast on the host side by the caller)
     const double e32 = P.eps < P.eps32 ? P.eps32 : P.eps;
     if (init_u || init_lam) return ACM_ERR_ARG;  // warm starts are taken in the FP32 or FP64 modes
-    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, e32, nullptr, nullptr, nullptr, STALL_WINDOW));
+    CKS(stokes_setup<float>(c, nprob, Hdev, 0, 1, gs, P, e32, nullptr, nullptr, nullptr, STALL_WINDOW,
+                            pore_l.data()));
     CKS(stokes_iterate<float>(c, nprob, Hdev, 0, 1, P.deriv, P.check_every, P.max_iter, dl));
     std::vector<StokesDev> hp(nprob);
     CK(cudaMemcpy(hp.data(), c->sprm, nprob * sizeof(StokesDev), cudaMemcpyDeviceToHost));
@@ -1144,7 +1158,7 @@ struct acm_batch {
   int ncells = 0;
   std::vector<BatchGroup> groups;
   GraphCache graph;
-  unsigned long long* counts = nullptr;  // device [ncells] solid voxels
+  unsigned long long* counts = nullptr;  // device [2][ncells]: solid voxels, solid-pore faces
 };
 
 namespace {
@@ -1155,7 +1169,8 @@ acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_sto
                             void* const* lam_out, double* K, acm_report* rep) {
   const double t0 = now_ms();
   // indicators into each group's cell slots, solid counts per cell
-  CK(cudaMemsetAsync(b->counts, 0, (size_t)b->ncells * sizeof(unsigned long long), b->st));
+  // counts[cell] = solid voxels, counts[ncells + cell] = solid-pore faces
+  CK(cudaMemsetAsync(b->counts, 0, (size_t)2 * b->ncells * sizeof(unsigned long long), b->st));
   for (auto& gr : b->groups) {
     const long long V = gr.c->g.V;
     for (size_t i = 0; i < gr.cells.size(); ++i) {
@@ -1163,10 +1178,12 @@ acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_sto
       if (!H[cell]) return ACM_ERR_ARG;
       CK(cudaMemcpyAsync(gr.c->Hd + i * V, H[cell], (size_t)V, cudaMemcpyDefault, b->st));
       CK(count_solid_add(gr.c->Hd + i * V, V, b->counts + cell, b->st));
+      if (P.pore_scale > 0)
+        CK(count_faces_add(gr.c->Hd + i * V, gr.n[0], gr.n[1], gr.n[2], b->counts + b->ncells + cell, b->st));
     }
     CK(pack_hbits(gr.c->Hd, gr.c->Hb, (long long)gr.cells.size() * V, b->st));
   }
-  std::vector<unsigned long long> cnt(b->ncells);
+  std::vector<unsigned long long> cnt(2 * (size_t)b->ncells);
   CK(cudaMemcpyAsync(cnt.data(), b->counts, cnt.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->st));
   CK(cudaStreamSynchronize(b->st));
   // per-problem set-up (degenerate cells are reported, not iterated)
@@ -1189,8 +1206,14 @@ acm_status batch_stokes_run(acm_batch* b, const uint8_t* const* H, const acm_sto
       if (init_u && init_u[cell]) iu[p] = (const char*)init_u[cell] + off;
       if (init_lam && init_lam[cell]) il[p] = (const char*)init_lam[cell] + off;
     }
+    std::vector<double> pore_l(np, 0.0);
+    for (int p = 0; p < np; ++p) {
+      const int cell = gr.cells[p / 3];
+      const unsigned long long faces = cnt[(size_t)b->ncells + cell];
+      if (faces > 0) pore_l[p] = (double)(V - (long long)cnt[cell]) / (double)faces;
+    }
     CKS(stokes_setup<T>(gr.c, np, gr.c->Hd, V, 3, reinterpret_cast<const double(*)[3]>(gs.data()), P, P.eps,
-                        iu.data(), il.data(), preset.data()));
+                        iu.data(), il.data(), preset.data(), 0, pore_l.data()));
     grp.push_back({gr.c, np, gr.c->Hd, V, 3});
   }
   bool prof = false;
@@ -1672,7 +1695,7 @@ acm_status acm_batch_create(acm_batch** out, int ncells, const int* dims, void* 
     if (s != ACM_OK) break;
     gr.c->spec_comps = 3;  // Stokes only
   }
-  if (s == ACM_OK && (cudaMalloc(&b->counts, (size_t)ncells * sizeof(unsigned long long)) != cudaSuccess ||
+  if (s == ACM_OK && (cudaMalloc(&b->counts, (size_t)2 * ncells * sizeof(unsigned long long)) != cudaSuccess ||
                       cudaMalloc(&b->graph.counter, sizeof(unsigned int)) != cudaSuccess)) {
     cudaGetLastError();
     s = ACM_ERR_NOMEM;

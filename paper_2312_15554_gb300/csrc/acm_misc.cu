@@ -161,6 +161,27 @@ __global__ void __launch_bounds__(256) k_solute_finalize(SoluteDev* __restrict__
   }
 }
 
+// solid-pore faces of the periodic voxel grid: each voxel counts the faces it
+// shares with its +1 neighbours along the three axes where H changes (a grid of
+// one plane has no face along axis 0)
+__global__ void k_count_faces(const uint8_t* __restrict__ H, int n0, int n1, int n2, unsigned long long* out) {
+  const long long V = (long long)n0 * n1 * n2;
+  unsigned long long c = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+    const int i2 = (int)(i % n2);
+    const long long r = i / n2;
+    const int i1 = (int)(r % n1), i0 = (int)(r / n1);
+    const uint8_t h = H[i] != 0;
+    const long long a0 = ((long long)((i0 + 1) % n0) * n1 + i1) * n2 + i2;
+    const long long a1 = ((long long)i0 * n1 + (i1 + 1) % n1) * n2 + i2;
+    const long long a2 = ((long long)i0 * n1 + i1) * n2 + (i2 + 1) % n2;
+    c += (unsigned long long)(h != (H[a0] != 0)) + (h != (H[a1] != 0)) + (h != (H[a2] != 0));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 __global__ void k_count_solid(const uint8_t* __restrict__ H, long long V, unsigned long long* out) {
   unsigned long long c = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
@@ -223,6 +244,11 @@ cudaError_t count_solid(const uint8_t* H, long long V, unsigned long long* out, 
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   k_count_solid<<<304, 256, 0, s>>>(H, V, out);
+  return cudaGetLastError();
+}
+
+cudaError_t count_faces_add(const uint8_t* H, int n0, int n1, int n2, unsigned long long* out, cudaStream_t s) {
+  k_count_faces<<<304, 256, 0, s>>>(H, n0, n1, n2, out);
   return cudaGetLastError();
 }
 

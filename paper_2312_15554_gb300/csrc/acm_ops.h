@@ -67,6 +67,8 @@ cudaError_t count_solid(const uint8_t* H, long long V, unsigned long long* out, 
 // Hb[w] = bits of H[32 w .. 32 w + 31] (n a multiple of 32)
 cudaError_t pack_hbits(const uint8_t* H, uint32_t* Hb, long long n, cudaStream_t s);
 cudaError_t count_solid_add(const uint8_t* H, long long V, unsigned long long* out, cudaStream_t s);
+// adds the number of solid-pore faces of H (periodic) to *out
+cudaError_t count_faces_add(const uint8_t* H, int n0, int n1, int n2, unsigned long long* out, cudaStream_t s);
 
 // Condition of the device-resident loop (a CUDA graph while node): continue
 // while any problem of any group has not set its stop flag, and at most `cap`

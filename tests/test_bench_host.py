@@ -1,5 +1,6 @@
 """Host-side arithmetic of the bench line (no GPU): the step-level roofline and
 the algorithmic byte counts it is built from."""
+import numpy as np
 import pytest
 
 import bench
@@ -27,3 +28,17 @@ def test_algorithmic_bytes_count_half_spectrum_components_and_the_solid_share():
     hi = bench.algorithmic_bytes_per_voxel("x_stokes_local", n2, 0.3)
     assert hi - lo == pytest.approx(24.0 * 0.3, rel=1e-12)
     assert bench.algorithmic_bytes_per_voxel("finalize", n2, 0.35) == 0.0
+
+
+def test_time_to_permeability_crossing_is_the_first_iteration_that_stays_within():
+    from paper_2312_15554_gb300 import ttk
+    K_ref = np.eye(3)
+    errs = [0.5, 0.05, 0.2, 0.02, 0.008, 0.009, 0.001]   # Frobenius errors e / sqrt(3) of K_ref = I
+    hist = np.stack([K_ref * (1 + e / np.sqrt(3)) for e in errs])   # Frobenius error e
+    assert ttk.crossing(hist, K_ref, 0.1) == 4          # 0.2 at iteration 3 breaks the earlier entry
+    assert ttk.crossing(hist, K_ref, 0.01) == 5
+    assert ttk.crossing(hist, K_ref, 1e-4) is None      # never reached within the run
+    assert ttk.crossing(hist, K_ref, 1.0) == 1
+    # voxel units of a cube and of a plane cell
+    assert ttk.grid_nu((64, 64, 64)) == pytest.approx(1 / 64**2, rel=1e-12)
+    assert ttk.grid_nu((1, 128, 128)) == pytest.approx(1 / 128**2, rel=1e-12)

@@ -121,3 +121,36 @@ def test_solute_device_loop_equals_host_loop(lib, precision):
     assert out[0][0] == out[1][0]
     np.testing.assert_array_equal(out[0][1], out[1][1])
     np.testing.assert_array_equal(out[0][2], out[1][2])
+
+
+def test_pore_scale_penalties_follow_each_cells_pore_length(lib):
+    """pore_scale = f starts every penalty at f / l^2 times the default, l = pore
+    voxels / solid-pore faces (counted here with numpy), per cell in a batch;
+    the fields then equal the oracle's with those fixed penalties."""
+    from oracle import acm_oracle as Ora
+
+    def expected(H, f=9.0):
+        faces = sum(int(np.count_nonzero(H != np.roll(H, -1, axis=a))) for a in range(3) if H.shape[a] > 1)
+        l = np.count_nonzero(H == 0) / faces
+        return f / l**2 * Ora.default_penalty(H.shape, 1.0)
+
+    H = I.sphere_pack((32, 32, 32), 0.45, 4.0, 12)[0]
+    ctx = lib.acm_ctx(H.shape)
+    u = torch.zeros((3,) + H.shape, dtype=torch.float64, device=DEV)
+    s, K, rep = lib.acm_stokes(ctx, torch.as_tensor(H, device=DEV), [1.0, 0.0, 0.0], lib.stokes_params(
+        precision=lib.FP64, eps=0.0, max_iter=5, adaptive=0, pore_scale=9.0), None, None, u, None, None)
+    ctx.close()
+    psi = expected(H)
+    np.testing.assert_allclose(rep.psi[:3], [psi] * 3, rtol=1e-12)
+    R = Ora.stokes(H, [1.0, 0.0, 0.0], Ora.StokesParams(eps=0.0, max_iter=5, adaptive=False, alpha0=psi, beta0=psi,
+                                                        b0=psi))
+    np.testing.assert_allclose(u.cpu().numpy(), R.state.u, rtol=0, atol=1e-10 * np.abs(R.state.u).max())
+    shapes = [(32, 32, 32), (1, 64, 64), (32, 32, 32)]
+    Hs = [H, I.disk_pack(64, 64, 0.5, (3.0, 6.0), 5), I.sphere_pack((32, 32, 32), 0.3, 3.0, 13)[0]]
+    batch = lib.acm_batch(shapes)
+    s, Kb, reps = lib.acm_batch_stokes(batch, [torch.as_tensor(h, device=DEV) for h in Hs], lib.stokes_params(
+        precision=lib.FP32, eps=0.0, max_iter=3, adaptive=0, pore_scale=9.0))
+    batch.close()
+    for i, h in enumerate(Hs):
+        for r in reps[i]:
+            np.testing.assert_allclose(r.psi[:3], [expected(h)] * 3, rtol=1e-12)
