@@ -344,19 +344,23 @@ def run_gpu(args, rank, world, dist):
             for k, v in prof.items() if v[1]}
 
     # time to permeability on one GPU only (several ranks would each hold a GPU for it)
-    ttk = time_to_permeability(acm, ctx, Hd, stream, args.ttk_long) if (args.ttk and world == 1) else None
-    ttk_c = None
+    ttk = (time_to_permeability(acm, ctx, Hd, stream, args.ttk_long)
+           if (args.ttk and args.ttk_default_form and world == 1) else None)
+    ttk_c = ttk_b = None
     if args.ttk and world == 1 and args.ttk_iters > 0:
         from paper_2312_15554_gb300 import ttk as TTK
-        t_ref = time.perf_counter()
-        K_ref, ref = TTK.reference_single(acm, Hd, eps=1e-10)
-        ref_s = time.perf_counter() - t_ref
-        ttk_c = TTK.plain(acm, ctx, Hd, stream, args.ttk_iters, K_ref)
-        ttk_c.update({"K_ref": K_ref.tolist(), "reference": {"kind": "FP64 tensor solve at eps 1e-10, voxel units "
-                                                                     "(nu = h^2), scaled to the cell's units",
-                                                             "seconds": ref_s, **ref},
-                      "form": "plain (FP32, unit cell, nu = 1), approximate derivative symbols (Eq. 21), fixed "
-                              f"penalties {TTK.PORE_SCALE:g} / l^2 x the default (pore length l)"})
+        ttk_c = TTK.plain(acm, ctx, Hd, stream, args.ttk_iters)
+        ttk_c["form"] = ("plain (FP32, unit cell, nu = 1), approximate derivative symbols (Eq. 21), fixed "
+                         f"penalties {TTK.PORE_SCALE:g} / l^2 x the default (pore length l)")
+        if args.ttk_cells > 0:
+            # a reduced batched figure: cells of the batched workload's recipe
+            Hb = [torch.as_tensor(_batched_cell(i), device=dev) for i in range(args.ttk_cells)]
+            r = TTK.batched(acm, Hb, args.ttk_iters, stream)
+            r.pop("n_star")
+            r.pop("K_ref")
+            ttk_b = {"form": f"batched, {args.ttk_cells} cells of the batched recipe (half 64^3, half 128^3), "
+                             "FP32, Eq. 21 symbols, pore-scale fixed penalties per cell", **r}
+            del Hb
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -395,6 +399,8 @@ def run_gpu(args, rank, world, dist):
         line["time_to_permeability"] = ttk
     if ttk_c is not None:
         line["time_to_permeability_fp64_reference"] = ttk_c
+    if ttk_b is not None:
+        line["time_to_permeability_batched_fp64_reference"] = ttk_b
     print(json.dumps(line), flush=True)
 
 
@@ -618,6 +624,10 @@ def main():
                     help="iterations of the library-default form's self-referenced run")
     ap.add_argument("--ttk-iters", type=int, default=1000,
                     help="iterations of the FP32 run timed against the FP64 reference (0: skip that form)")
+    ap.add_argument("--ttk-cells", type=int, default=8,
+                    help="cells of the reduced batched time-to-permeability figure (0: skip)")
+    ap.add_argument("--ttk-default-form", action="store_true",
+                    help="also time the library defaults (Eq. 13 symbols, Eq. 22) against their own long run")
     ap.add_argument("--config", default="cell256", choices=["cell256", "batched", "grf512"],
                     help="cell256: the 256^3 cell (default); batched: 384 cells (192 at 64^3, 192 at 128^3); "
                          "grf512: the 512^3 Gaussian random field with the FP32/FP64 comparison")
