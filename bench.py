@@ -349,13 +349,13 @@ def run_gpu(args, rank, world, dist):
     ttk_c = ttk_b = None
     if args.ttk and world == 1 and args.ttk_iters > 0:
         from paper_2312_15554_gb300 import ttk as TTK
-        ttk_c = TTK.plain(acm, ctx, Hd, stream, args.ttk_iters)
+        ttk_c = TTK.plain(acm, ctx, Hd, stream, args.ttk_iters, ref_max_iter=args.ttk_ref_iters)
         ttk_c["form"] = ("plain (FP32, unit cell, nu = 1), approximate derivative symbols (Eq. 21), fixed "
                          f"penalties {TTK.PORE_SCALE:g} / l^2 x the default (pore length l)")
         if args.ttk_cells > 0:
             # a reduced batched figure: cells of the batched workload's recipe
             Hb = [torch.as_tensor(_batched_cell(i), device=dev) for i in range(args.ttk_cells)]
-            r = TTK.batched(acm, Hb, args.ttk_iters, stream)
+            r = TTK.batched(acm, Hb, args.ttk_iters, stream, ref_max_iter=args.ttk_ref_iters)
             r.pop("n_star")
             r.pop("K_ref")
             ttk_b = {"form": f"batched, {args.ttk_cells} cells of the batched recipe (half 64^3, half 128^3), "
@@ -461,7 +461,7 @@ def run_batched(args, rank, world, dist):
         # fixed penalties): every problem's K after every iteration of one
         # batched FP32 run, each cell against its FP64 limit at eps 1e-10
         from paper_2312_15554_gb300 import ttk as TTK
-        r = TTK.batched(acm, Hd, args.ttk_batched, stream)
+        r = TTK.batched(acm, Hd, args.ttk_batched, stream, ref_max_iter=args.ttk_ref_iters)
         r.pop("n_star")
         r.pop("K_ref")
         ttk = {"form": "batched (FP32, nu = 1), approximate derivative symbols (Eq. 21), fixed penalties "
@@ -624,6 +624,8 @@ def main():
                     help="iterations of the library-default form's self-referenced run")
     ap.add_argument("--ttk-iters", type=int, default=1000,
                     help="iterations of the FP32 run timed against the FP64 reference (0: skip that form)")
+    ap.add_argument("--ttk-ref-iters", type=int, default=2000,
+                    help="iteration cap of the FP64 references (started from the FP32 end state)")
     ap.add_argument("--ttk-cells", type=int, default=8,
                     help="cells of the reduced batched time-to-permeability figure (0: skip)")
     ap.add_argument("--ttk-default-form", action="store_true",
