@@ -1,0 +1,53 @@
+"""The parameter sweeps (paper_2312_15554_gb300.sweeps) on a reduced workload:
+the paper's two findings about iteration counts, and the invariance of the
+converged answer.
+
+* Section 4.1: the ADMM's rate depends strongly on fixed penalties, and the
+  adaptive rule of Eq. 22 removes most of that dependence; whatever the
+  penalties, the converged permeability is the same.
+* Section 4.2: the Lippmann-Schwinger iteration converges only for a large
+  enough comparison medium A0, and the smallest A0 that converges is the
+  fastest.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2312_15554_gb300 import inputs as I
+from paper_2312_15554_gb300 import sweeps as SW
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def test_penalty_sweep_rates_differ_and_the_answer_does_not(lib):
+    n = 32
+    Hs = []
+    for s in range(4):
+        por, radii = I.cell_recipe(700_000 + s)
+        Hs.append(torch.as_tensor(I.sphere_pack((n, n, n), por, (radii[0] / 2, radii[1] / 2), 700_000 + s)[0],
+                                  device=DEV))
+    stream = torch.cuda.current_stream()
+    r = SW.stokes_penalties(lib, Hs, 1.0 / n**2, 1e-5, 40000, stream, factors=(0.25, 4.0))
+    st = r["settings"]
+    assert all(v["converged_frac"] == 1.0 for v in st.values())
+    lo, hi = st["fixed 0.25 x default"]["iters_mean"], st["fixed 4 x default"]["iters_mean"]
+    assert max(lo, hi) > 2 * min(lo, hi)                      # fixed penalties: rate depends on them
+    ad = st["adaptive, tau (5, 10, 5)"]["iters_mean"]
+    assert ad < max(lo, hi)                                   # the adaptive rule avoids the slow end
+    Ks = [v["K_mean_diag"] for v in st.values()]
+    assert (max(Ks) - min(Ks)) / np.mean(Ks) < 2e-3           # the same answer to the tolerance
+
+
+def test_comparison_medium_sweep_smallest_converging_a0_is_fastest(lib):
+    n = 32
+    por, radii = I.cell_recipe(700_000)
+    H = I.sphere_pack((n, n, n), por, (radii[0] / 2, radii[1] / 2), 700_000)[0]
+    u = 0.5 * torch.as_tensor(I.random_field((3, n, n, n), 5) * (1 - H)[None], dtype=torch.float32, device=DEV)
+    stream = torch.cuda.current_stream()
+    out = SW.solute_a0(lib, H, u, 1.0, 1e-6, 5000, stream, a0s=(0.3, 0.55, 1.0, 2.0))
+    assert out["0.3"]["status"] == -5                         # too small a comparison medium diverges
+    its = [max(out[k]["iters"]) for k in ("0.55", "1", "2")]
+    assert all(all(out[k]["converged"]) for k in ("0.55", "1", "2"))
+    assert its[0] < its[1] < its[2]
