@@ -349,16 +349,20 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Block sum of NS values per thread, written by thread 0 to out[0..NS).
-// scratch: NS * 32 doubles of shared memory. Deterministic for a fixed block size.
-template <int NS>
-__device__ __forceinline__ void block_sum_store(double (&v)[NS], double* scratch, double* out) {
+// Block sum of NS values per thread, written by thread 0 to out[0..NS) as
+// doubles. The warp and block stages run in T: FP32 kernels sum their block's
+// few hundred partials in FP32 (FP64 arithmetic is scarce on this GPU) and
+// hand FP64 on to the grid stage. scratch: NS * 32 values of T in shared
+// memory. Deterministic for a fixed block size.
+template <int NS, typename T>
+__device__ __forceinline__ void block_sum_store(T (&v)[NS], T* scratch, double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < NS; ++k) v[k] = warp_sum(v[k]);
@@ -371,9 +375,9 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NS], double* scratch
   if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      double a = lane < nw ? scratch[k * 32 + lane] : 0.0;
+      T a = lane < nw ? scratch[k * 32 + lane] : (T)0;
       a = warp_sum(a);
-      if (lane == 0) out[k] = a;
+      if (lane == 0) out[k] = (double)a;
     }
   }
 }

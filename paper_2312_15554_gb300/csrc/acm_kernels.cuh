@@ -136,6 +136,7 @@ __device__ __forceinline__ void x_fft(cx<T>* sm, const cx<T>* tw) {
 // ---------------------------------------------------------------------------
 constexpr int XS_WARPS = 8;   // warps per block of the line-resident x passes
 constexpr int XS_GPW = 4;     // line groups per warp
+constexpr int XS_PCACHE = 4;  // solute x pass: problems whose parameters a block converts once
 
 template <typename T, int N2>
 __host__ __device__ constexpr int xs_tw_slots() { return (tw_total(N2 / 2) + N2 / 2 + 1 + 1) / 2 * 2; }
@@ -173,15 +174,22 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* lines = tw + xs_tw_slots<T, N2>();
-  __shared__ double red[5 * 32];
+  __shared__ T red[5 * 32];
+  __shared__ T kpar[3];
   const int p = blockIdx.y;
   StokesDev* P = prm + p;
   if (P->done) return;
   load_tw_x<T, N2>(tw, twg);
+  if (threadIdx.x == 0) {
+    // penalties in the kernel's precision, converted once per block;
+    // u~^n on solid voxels = s_prev u^n (s_prev = 1 before the first iteration)
+    kpar[0] = (T)P->psi[0];
+    kpar[1] = (T)P->psi[2];
+    kpar[2] = (T)(P->psi_prev[2] / (P->psi_prev[2] + P->psi_prev[0]));
+  }
   __syncthreads();
-  const T alpha = (T)P->psi[0], b = (T)P->psi[2];
-  // u~^n on solid voxels = s_prev u^n (s_prev = 1 before the first iteration)
-  const T s_prev = (T)(P->psi_prev[2] / (P->psi_prev[2] + P->psi_prev[0]));
+  const T alpha = kpar[0], b = kpar[1];
+  const T s_prev = kpar[2];
   const T s_now = b / (b + alpha);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ll = lane / TL, t = lane % TL;
@@ -194,7 +202,8 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
   const long long hcell = (long long)(p / g.lph) * g.hs;
   const uint8_t* Hp = H + hcell;
   const uint32_t* Hbp = Hb + hcell / 32;
-  double d5[5] = {0, 0, 0, 0, 0};
+  // residual partials of the lane over all its lines, in T (a few hundred terms)
+  T d5[5] = {0, 0, 0, 0, 0};
   const int ngroups = g.n0 * g.n1 / LPW;
   const int gbase = (blockIdx.x * XS_WARPS + warp) * XS_GPW;
 #pragma unroll 1
@@ -303,11 +312,11 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
         __syncwarp(mask);
       }
     }
-    d5[0] += (double)a0;
-    d5[1] += (double)a1;
-    d5[2] += (double)a2;
-    d5[3] += (double)a3;
-    d5[4] += (double)a4;
+    d5[0] += a0;
+    d5[1] += a1;
+    d5[2] += a2;
+    d5[3] += a3;
+    d5[4] += a4;
   }
   block_sum_store<5>(d5, red, part + ((long long)p * gridDim.x + blockIdx.x) * 8);
 }
@@ -328,14 +337,20 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* lines = tw + xs_tw_slots<T, N2>();
+  __shared__ T kpar[2];
   const int p = blockIdx.y;
   const StokesDev* P = prm + p;
   if (P->done) return;
   load_tw_x<T, N2>(tw, twg);
+  if (threadIdx.x == 0) {
+    // converted once per block; u~^n on solid voxels = s_prev u^n with the
+    // penalties of the iteration just taken
+    kpar[0] = (T)P->psi[2];
+    kpar[1] = (T)(P->psi_prev[2] / (P->psi_prev[2] + P->psi_prev[0]));
+  }
   __syncthreads();
-  const T b = (T)P->psi[2];
-  // u~^n on solid voxels = s_prev u^n with the penalties of the iteration just taken
-  const T s_prev = (T)(P->psi_prev[2] / (P->psi_prev[2] + P->psi_prev[0]));
+  const T b = kpar[0];
+  const T s_prev = kpar[1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ll = lane / TL, t = lane % TL;
   const unsigned mask = xl_mask();
@@ -418,13 +433,29 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
   T* acc = reinterpret_cast<T*>(lines + XS_WARPS * LPW * LB) + (threadIdx.x >> 5) * 32 * 2 * E;
   // Problems that share one velocity and indicator (us = hs = 0, e.g. the three
   // composition loads of a tensor solve) run back to back on the same warp, so
-  // each velocity row crosses DRAM once; otherwise blockIdx.y is the problem.
+  // each velocity row crosses DRAM once (up to XS_PCACHE problems per block,
+  // blockIdx.y numbering the groups); otherwise blockIdx.y is the problem.
   const bool shared = g.us == 0 && g.hs == 0;
-  const int pbeg = shared ? 0 : blockIdx.y, pend = shared ? nprob : blockIdx.y + 1;
+  const int pbeg = shared ? blockIdx.y * XS_PCACHE : blockIdx.y;
+  const int pend = shared ? min(nprob, pbeg + XS_PCACHE) : blockIdx.y + 1;
   bool any = false;
   for (int p = pbeg; p < pend; ++p) any = any || !prm[p].done;
   if (!any) return;
   load_tw_x<T, N2>(tw, twg);
+  // parameters of the block's problems in T, converted once per block:
+  // (g_c, B0_c) for c = 0..2, then A0, eta, Pe, Fc
+  __shared__ T spar[XS_PCACHE][10];
+  for (int i = threadIdx.x; pbeg + i < pend; i += blockDim.x) {
+    const SoluteDev& Q = prm[pbeg + i];
+    for (int c = 0; c < 3; ++c) {
+      spar[i][2 * c] = (T)Q.g[c];
+      spar[i][2 * c + 1] = (T)Q.B0[c];
+    }
+    spar[i][6] = (T)Q.A0;
+    spar[i][7] = (T)Q.eta;
+    spar[i][8] = (T)Q.Pe;
+    spar[i][9] = (T)Q.Fc;
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ll = lane / TL, t = lane % TL;
@@ -467,9 +498,8 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
         cx<T>* bc = c == 1 ? b1 : b0;
         if (c < 3) {
           xl_inverse<T, N2>(bc, tw, t, mask, v);
-          const T gc = (T)(c == 0 ? P->g[0] : c == 1 ? P->g[1] : P->g[2]);
-          const T Bc = (T)(c == 0 ? P->B0[0] : c == 1 ? P->B0[1] : P->B0[2]);
-          const T A0 = (T)P->A0, eta = (T)P->eta, Pe = (T)P->Pe;
+          const T* q = spar[p - pbeg];
+          const T gc = q[2 * c], Bc = q[2 * c + 1], A0 = q[6], eta = q[7], Pe = q[8];
           const T* uc = up + c * g.V + v0;
 #pragma unroll
           for (int m = 0; m < E; ++m) {
@@ -490,7 +520,7 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
           }
         } else {
           // s = F - (B - B0).(grad chi + g): the accumulated terms plus Pe ubar.g on pore voxels
-          const T Fc = (T)P->Fc;
+          const T Fc = spar[p - pbeg][9];
 #pragma unroll
           for (int m = 0; m < E; ++m) {
             const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
@@ -644,10 +674,27 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = sm + NC * TX * C::LS;
-  __shared__ double red[4 * 32];
+  __shared__ T red[4 * 32];
+  // the operator's parameters, converted once per block: (nu, beta, b) or
+  // (A0, B0), and 1/V
+  __shared__ T opar[5];
   const int p = blockIdx.z, outer = blockIdx.y, kx0 = blockIdx.x * TX;
   if (a.sprm && a.sprm[p].done) return;
   if (a.cprm && a.cprm[p].done) return;
+  if constexpr (OP == OP_STOKES) {
+    if (threadIdx.x == 0) {
+      opar[0] = (T)a.sprm[p].nu;
+      opar[1] = (T)a.sprm[p].psi[1];
+      opar[2] = (T)a.sprm[p].psi[2];
+      opar[4] = (T)a.invV;
+    }
+  } else if constexpr (OP == OP_SOLUTE) {
+    if (threadIdx.x == 0) {
+      opar[0] = (T)a.cprm[p].A0;
+      for (int k = 0; k < 3; ++k) opar[1 + k] = (T)a.cprm[p].B0[k];
+      opar[4] = (T)a.invV;
+    }
+  }
   cx<T>* base = a.spec + p * a.probStride + outer * a.outerStride + kx0;
   const int w = min(TX, a.Pu - kx0);
   for (int idx = threadIdx.x; idx < NIN * N * TX; idx += blockDim.x) {
@@ -709,21 +756,21 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
   }
   if constexpr (OP == OP_STOKES || OP == OP_SOLUTE) {
     __syncthreads();
-    const T invV = (T)a.invV;
+    const T invV = opar[4];
     const int ky = outer;
     const T d1 = a.sym.d1[ky], l1 = a.sym.l1[ky];
     T acc0 = 0, acc1 = 0, acc2 = 0;
     // hoisted parameters of the operator
     T nu = 0, beta = 0, b = 0, A0 = 0, B00 = 0, B01 = 0, B02 = 0;
     if constexpr (OP == OP_STOKES) {
-      nu = (T)a.sprm[p].nu;
-      beta = (T)a.sprm[p].psi[1];
-      b = (T)a.sprm[p].psi[2];
+      nu = opar[0];
+      beta = opar[1];
+      b = opar[2];
     } else {
-      A0 = (T)a.cprm[p].A0;
-      B00 = (T)a.cprm[p].B0[0];
-      B01 = (T)a.cprm[p].B0[1];
-      B02 = (T)a.cprm[p].B0[2];
+      A0 = opar[0];
+      B00 = opar[1];
+      B01 = opar[2];
+      B02 = opar[3];
     }
     // The operator state (q^ and div^, or chi^) is read and rewritten in place:
     // each chunk loads its state before any store (see k_x_stokes_local).
@@ -827,7 +874,7 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
         }
       }
     }
-    double v3[3] = {(double)acc0, (double)acc1, (double)acc2};
+    T v3[3] = {acc0, acc1, acc2};
     const int nb = gridDim.x * gridDim.y;
     block_sum_store<3>(v3, red, a.part + ((long long)p * nb + blockIdx.y * gridDim.x + blockIdx.x) * 4);
     __syncthreads();

@@ -81,12 +81,14 @@ static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u
   constexpr int smem = xs_smem_bytes<T, N2, 2, 2 * XL<T, N2>::E>();
   static const cudaError_t attr = set_smem(k_x_solute<T, N2>, smem);
   if (attr != cudaSuccess) return attr;
-  // problems sharing the velocity and the indicator loop inside the kernel, with
-  // fewer line groups per warp so that the grid keeps its size
+  // problems sharing the velocity and the indicator loop inside the kernel (up
+  // to XS_PCACHE per block), with fewer line groups per warp so that the grid
+  // keeps its size
   const bool shared = g.us == 0 && g.hs == 0;
-  const int gpw = shared ? (XS_GPW / nprob > 1 ? XS_GPW / nprob : 1) : XS_GPW;
+  const int np_blk = nprob < XS_PCACHE ? nprob : XS_PCACHE;
+  const int gpw = shared ? (XS_GPW / np_blk > 1 ? XS_GPW / np_blk : 1) : XS_GPW;
   const int ngroups = g.n0 * g.n1 / XL<T, N2>::LPW;
-  dim3 grid((ngroups + XS_WARPS * gpw - 1) / (XS_WARPS * gpw), shared ? 1 : nprob);
+  dim3 grid((ngroups + XS_WARPS * gpw - 1) / (XS_WARPS * gpw), shared ? (nprob + XS_PCACHE - 1) / XS_PCACHE : nprob);
   k_x_solute<T, N2><<<grid, XS_WARPS * 32, smem, s>>>((cx<T>*)spec, (const T*)u, H, Hb, prm, g, (const cx<T>*)tw,
                                                         d2, nprob, gpw);
   return cudaGetLastError();

@@ -332,7 +332,7 @@ __device__ __forceinline__ void rr_prefetch_state(const PassArgs<T>& a, cx<T>* s
 template <typename T, int N, int OP, int NC, int W>
 __device__ __forceinline__ void rr_apply(const PassArgs<T>& a, cx<T> (&u)[rr_nin<OP, NC>()][16], int p, int outer,
                                          int kx, bool ok, cx<T>* base, int col, int t, cx<T>* buf0, cx<T>* buf1,
-                                         const cx<T>* tw, const cx<T>* sq, const cx<T>* sd, int ss, double* red,
+                                         const cx<T>* tw, const cx<T>* sq, const cx<T>* sd, int ss, T* red,
                                          double* part) {
   constexpr int TL = N / 16;
   if constexpr (OP == OP_FWD) {
@@ -376,8 +376,7 @@ __device__ __forceinline__ void rr_apply(const PassArgs<T>& a, cx<T> (&u)[rr_nin
     T acc[3] = {(T)0, (T)0, (T)0};
     if constexpr (OP == OP_STOKES) rr_stokes_op<T, N>(a, u, p, outer, kx, ok, t, sq, sd, ss, acc);
     else rr_solute_op<T, N>(a, u, p, outer, kx, ok, t, sq, ss, acc);
-    double v3[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-    block_sum_store<3>(v3, red, part);
+    block_sum_store<3>(acc, red, part);
     // the sums' barriers separate the last forward transform's buffer reads from
     // the inverse transforms' writes
 #pragma unroll
@@ -400,7 +399,7 @@ __global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
   cx<T>* buf1 = buf0 + W * C::BS;
   cx<T>* tw = buf1 + W * C::BS;
   cx<T>* stp = tw + N;  // state slots [value][element][thread]
-  __shared__ double red[4 * 32];
+  __shared__ T red[4 * 32];
   const RTiles tl = rr_tiles(a.Pu, a.nouter, W);
   const int p = blockIdx.x / tl.nlive, r = blockIdx.x % tl.nlive;
   if ((a.sprm && a.sprm[p].done) || (a.cprm && a.cprm[p].done)) return;
