@@ -148,11 +148,10 @@ constexpr bool tx_ok() {
 }
 
 // The register-resident variant (acm_rpass.cuh) of a tunable pass: lines of
-// 64, 128 or 256 points; not the FP64 z Stokes pass (its three components of
-// 16 FP64 complex values per thread exceed the register file).
+// 64, 128 or 256 points.
 template <typename T, int N, int OP, int NC>
 constexpr bool rr_ok() {
-  return (N == 64 || N == 128 || N == 256) && tunable<N, OP, NC>() && !(sizeof(T) == 8 && OP == OP_STOKES);
+  return (N == 64 || N == 128 || N == 256) && tunable<N, OP, NC>();
 }
 
 // tile width of (T, N, OP, NC) under the choice `shift`; the register-resident
@@ -222,12 +221,13 @@ template <typename T, int N, int OP, int NC, int W>
 static cudaError_t l_pass_rr(const Geo& g, int axis, int nprob, void* spec, long long probStride, const Sym<T>& sym,
                              const void* tw, void* st0, void* st1, StokesDev* sprm, SoluteDev* cprm, double* part,
                              cudaStream_t s) {
-  using C = RCfg<T, N, W, rr_nst<OP>()>;
-  static const cudaError_t attr = set_smem(k_rstrided<T, N, OP, NC, W>, C::SMEM);
+  using C = RCfg<T, N, W>;
+  constexpr int smem = rr_smem<T, N, OP, NC, W>();
+  static const cudaError_t attr = set_smem(k_rstrided<T, N, OP, NC, W>, smem);
   if (attr != cudaSuccess) return attr;
   const PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
   const RTiles tl = rr_tiles(g.Pu, a.nouter, W);
-  k_rstrided<T, N, OP, NC, W><<<nprob * tl.nlive, C::NT, C::SMEM, s>>>(a);
+  k_rstrided<T, N, OP, NC, W><<<nprob * tl.nlive, C::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -10,10 +10,9 @@
 // 16-point DFT over m in registers, applies W_N^{t k1}, and hands the values to
 // the thread that owns k1 through ONE shared-memory transpose; that thread
 // takes the TL-point DFTs over t and holds X[k] for k = s + TL i + 16 k2. The
-// inverse runs the same steps backwards from those registers, so a pass with an
-// operator between the two transforms (the z passes: Eq. 13, Eq. 20) touches
-// shared memory only for two transposes per component, against twelve
-// round trips of a block-wide Stockham tile.
+// inverse runs the same steps backwards from those registers: a transform
+// crosses shared memory once (one transpose), against two round trips of a
+// block-wide Stockham line plus the staging of its loads and stores.
 //
 // A tile is W consecutive kx columns of one pencil (W x 8 bytes of a row per
 // access: W = 16, 8 or 4 in FP32), held by W x TL threads; thread (col, t) =
@@ -26,9 +25,11 @@
 // transform suffices.
 //
 // k_rstrided runs one tile per block; its global loads go straight to
-// registers (in the y passes the next component's loads are issued before the
-// current component's transform; a z pass requests all its components and the
-// operator state, which cp.async brings into slots private to each thread).
+// registers, the next component's loads issued before the current component's
+// transform. A z pass (an operator between the two transforms: Eq. 13, Eq. 20)
+// needs every component of a wavevector at once: it parks each forward-
+// transformed component in slots of that component's transpose buffer private
+// to the thread, so registers never hold more than two components.
 #pragma once
 #include "acm_fft.cuh"
 #include "acm_types.h"
@@ -41,10 +42,7 @@ namespace acm {
 template <typename T>
 __host__ __device__ constexpr int rr_wdef() { return 128 / (int)sizeof(cx<T>); }
 
-// NST: operator-state values per element a z pass prefetches (2 Stokes: q^ and
-// div^; 1 solute: chi^; 0 for the y passes); NIN: input components of a tile
-template <int OP>
-__host__ __device__ constexpr int rr_nst() { return OP == OP_STOKES ? 2 : (OP == OP_SOLUTE ? 1 : 0); }
+// NIN: input components of a tile
 template <int OP, int NC>
 __host__ __device__ constexpr int rr_nin() {
   return OP == OP_FWD_SOL ? 3 : (OP == OP_INV_SOL ? 2 : (OP == OP_STOKES ? 3 : (OP == OP_SOLUTE ? 2 : NC)));
@@ -52,13 +50,20 @@ __host__ __device__ constexpr int rr_nin() {
 
 // shared memory of a block (complex elements): two transpose buffers, the
 // twiddles and the per-thread state slots
-template <typename T, int N, int W, int NST = 0>
+template <typename T, int N, int W>
 struct RCfg {
-  static constexpr int TL = N / 16;                        // threads per line
-  static constexpr int NT = W * TL;                        // threads per block
-  static constexpr int BS = N + 1;                         // column stride of a transpose buffer (odd)
-  static constexpr int SMEM = (2 * W * BS + N + NST * 16 * NT) * (int)sizeof(cx<T>);
+  static constexpr int TL = N / 16;  // threads per line
+  static constexpr int NT = W * TL;  // threads per block
+  static constexpr int BS = N + 1;   // column stride of a transpose buffer (odd)
 };
+
+// shared memory of a block of pass OP (bytes): transpose buffers of W columns
+// (two, or in a z pass one per input component, which then holds that
+// component's slots) and the twiddles
+template <typename T, int N, int OP, int NC, int W>
+__host__ __device__ constexpr int rr_smem() {
+  return (((OP == OP_STOKES || OP == OP_SOLUTE) ? rr_nin<OP, NC>() : 2) * W * (N + 1) + N) * (int)sizeof(cx<T>);
+}
 
 // The live tiles of one problem: nreg = gxr pencils x column blocks, then (when
 // the Nyquist column is packed) nouter / W Nyquist tiles.
@@ -179,34 +184,35 @@ __device__ __forceinline__ void rr_store_k(const cx<T> (&v)[16], cx<T>* __restri
   for (int e = 0; e < 16; ++e) dst[(long long)rr_krow<TL>(s, e) * rowStride] = v[e];
 }
 
-// ---------------------------------------------------------------------------
-// The z-pass operators on a thread's 16 wavevectors (kz = rr_krow(t, e)), with
-// the operator state read from per-thread slots sq[e * ss] (q^ or chi^) and
-// sd[e * ss] (div^), and rewritten in place in global memory.
-// ---------------------------------------------------------------------------
-// Eq. 13 per wavevector, the q^ update of Eq. 9, the Parseval partials of the
-// divergence residuals (acc) and the k = 0 tap; u[c] leaves as u^_c / V.
-template <typename T, int N>
-__device__ __forceinline__ void rr_stokes_op(const PassArgs<T>& a, cx<T> (&u)[3][16], int p, int ky, int kx, bool ok,
-                                             int t, const cx<T>* sq, const cx<T>* sd, int ss, T (&acc)[3]) {
-  constexpr int TL = N / 16, CH = 4;
-  const T invV = (T)a.invV;
+// The z-pass operators on slots: component c of the thread's element e sits
+// at sl[c][e * NT] (k-ordered, kz = rr_krow(t, e)) and is replaced there by
+// the operator's output; the operator state is read from global memory in
+// chunks of SCH elements, all loads of a chunk in flight together. par: the
+// operator's parameters in T ((nu, beta, b) or (A0, B0)) and 1/V.
+template <typename T>
+__host__ __device__ constexpr int rz_chunk() { return sizeof(T) == 4 ? 8 : 4; }
+
+template <typename T, int N, int NT>
+__device__ __forceinline__ void rz_stokes_op(const PassArgs<T>& a, cx<T>* const (&sl)[3], const T* par, int p, int ky,
+                                             int kx, bool ok, int t, T (&acc)[3]) {
+  constexpr int TL = N / 16, SCH = rz_chunk<T>();
+  const T nu = par[0], beta = par[1], b = par[2], invV = par[4];
   const T d1 = a.sym.d1[ky], l1 = a.sym.l1[ky];
   const T d2 = ok ? a.sym.d2[kx] : (T)0, l2 = ok ? a.sym.l2[kx] : (T)0;
   const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
   const T l12 = l1 + l2, d12 = d1 * d1 + d2 * d2;
   const long long gst = (long long)p * a.compStride + (long long)ky * a.outerStride + kx;
-  const T nu = (T)a.sprm[p].nu, beta = (T)a.sprm[p].psi[1], b = (T)a.sprm[p].psi[2];
 #pragma unroll
-  for (int e0 = 0; e0 < 16; e0 += CH) {
-    cx<T> qs[CH], ds[CH];
+  for (int e0 = 0; e0 < 16; e0 += SCH) {
+    cx<T> qs[SCH], ds[SCH];
 #pragma unroll
-    for (int j = 0; j < CH; ++j) {
-      qs[j] = sq[(e0 + j) * ss];
-      ds[j] = sd[(e0 + j) * ss];
+    for (int j = 0; j < SCH; ++j) {
+      const long long gi = gst + (long long)rr_krow<TL>(t, e0 + j) * a.rowStride;
+      qs[j] = ok ? a.st0[gi] : mk<T>(0, 0);
+      ds[j] = ok ? a.st1[gi] : mk<T>(0, 0);
     }
 #pragma unroll
-    for (int j = 0; j < CH; ++j) {
+    for (int j = 0; j < SCH; ++j) {
       const int e = e0 + j, kz = rr_krow<TL>(t, e);
       const long long gi = gst + (long long)kz * a.rowStride;
       const T d0 = a.sym.d0[kz], l0 = a.sym.l0[kz];
@@ -214,7 +220,8 @@ __device__ __forceinline__ void rr_stokes_op(const PassArgs<T>& a, cx<T> (&u)[3]
       const bool k0 = (kz == 0 && ky == 0 && kx == 0);
       // r = w^ - i d q^ (+ g V at k = 0)
       const cx<T> iq = mul_i(qs[j]);
-      cx<T> r0 = u[0][e] - cscale(iq, d0), r1 = u[1][e] - cscale(iq, d1), r2 = u[2][e] - cscale(iq, d2);
+      cx<T> r0 = sl[0][e * NT] - cscale(iq, d0), r1 = sl[1][e * NT] - cscale(iq, d1),
+            r2 = sl[2][e * NT] - cscale(iq, d2);
       if (k0) {
         const StokesDev& P = a.sprm[p];
         const T Vt = (T)(1.0 / a.invV);
@@ -248,40 +255,39 @@ __device__ __forceinline__ void rr_stokes_op(const PassArgs<T>& a, cx<T> (&u)[3]
         a.sprm[p].mean_u[1] = (double)v1.x * a.invV;
         a.sprm[p].mean_u[2] = (double)v2.x * a.invV;
       }
-      u[0][e] = cscale(v0, invV);
-      u[1][e] = cscale(v1, invV);
-      u[2][e] = cscale(v2, invV);
+      sl[0][e * NT] = cscale(v0, invV);
+      sl[1][e * NT] = cscale(v1, invV);
+      sl[2][e * NT] = cscale(v2, invV);
     }
   }
 }
 
-// F^ = s'' + i d0 tau_0 (Eq. 18; the axis-2 and axis-1 terms were added in the
-// x and y passes), Eq. 20 with chi^(0) = 0, the Parseval partials of Eq. 19;
-// u leaves as (i d0 chi^, chi^) / V.
-template <typename T, int N>
-__device__ __forceinline__ void rr_solute_op(const PassArgs<T>& a, cx<T> (&u)[2][16], int p, int ky, int kx, bool ok,
-                                             int t, const cx<T>* sq, int ss, T (&acc)[3]) {
-  constexpr int TL = N / 16, CH = 4;
-  const T invV = (T)a.invV;
+// F^ = s'' + i d0 tau_0, Eq. 20 with chi^(0) = 0, the Parseval partials of
+// Eq. 19; the slots leave as (i d0 chi^, chi^) / V.
+template <typename T, int N, int NT>
+__device__ __forceinline__ void rz_solute_op(const PassArgs<T>& a, cx<T>* const (&sl)[2], const T* par, int p, int ky,
+                                             int kx, bool ok, int t, T (&acc)[3]) {
+  constexpr int TL = N / 16, SCH = rz_chunk<T>();
+  const T A0 = par[0], B00 = par[1], B01 = par[2], B02 = par[3], invV = par[4];
   const T d1 = a.sym.d1[ky], l1 = a.sym.l1[ky];
   const T d2 = ok ? a.sym.d2[kx] : (T)0, l2 = ok ? a.sym.l2[kx] : (T)0;
   const T wgt = (kx == 0 || kx == a.nkx) ? (T)1 : (T)2;
   const T l12 = l1 + l2, d12 = d1 * d1 + d2 * d2;
   const long long gst = (long long)p * a.compStride + (long long)ky * a.outerStride + kx;
-  const T A0 = (T)a.cprm[p].A0, B00 = (T)a.cprm[p].B0[0], B01 = (T)a.cprm[p].B0[1], B02 = (T)a.cprm[p].B0[2];
 #pragma unroll
-  for (int e0 = 0; e0 < 16; e0 += CH) {
-    cx<T> cs[CH];
+  for (int e0 = 0; e0 < 16; e0 += SCH) {
+    cx<T> cs[SCH];
 #pragma unroll
-    for (int j = 0; j < CH; ++j) cs[j] = sq[(e0 + j) * ss];
+    for (int j = 0; j < SCH; ++j)
+      cs[j] = ok ? a.st0[gst + (long long)rr_krow<TL>(t, e0 + j) * a.rowStride] : mk<T>(0, 0);
 #pragma unroll
-    for (int j = 0; j < CH; ++j) {
+    for (int j = 0; j < SCH; ++j) {
       const int e = e0 + j, kz = rr_krow<TL>(t, e);
       const long long gi = gst + (long long)kz * a.rowStride;
       const T d0 = a.sym.d0[kz], l0 = a.sym.l0[kz];
       const T L = l0 + l12, dd = d0 * d0 + d12;
       const bool k0 = (kz == 0 && ky == 0 && kx == 0);
-      const cx<T> F = u[1][e] + mul_i(cscale(u[0][e], d0));
+      const cx<T> F = sl[1][e * NT] + mul_i(cscale(sl[0][e * NT], d0));
       const T dre = A0 * L, dim = B00 * d0 + B01 * d1 + B02 * d2;
       cx<T> chi = mk<T>(0, 0);
       if (!k0 && ok) {
@@ -295,24 +301,9 @@ __device__ __forceinline__ void rr_solute_op(const PassArgs<T>& a, cx<T> (&u)[2]
         acc[1] += wgt * dd * cabs2(dch);
       }
       const cx<T> c1 = cscale(chi, invV);
-      u[0][e] = cscale(mul_i(c1), d0);
-      u[1][e] = c1;
+      sl[0][e * NT] = cscale(mul_i(c1), d0);
+      sl[1][e * NT] = c1;
     }
-  }
-}
-
-// issue the cp.async copies of the operator state of a thread's 16 wavevectors
-// into its private slots slot[e * ss] (and slot[(16 + e) * ss] for div^)
-template <typename T, int N, int NST>
-__device__ __forceinline__ void rr_prefetch_state(const PassArgs<T>& a, cx<T>* slot, int ss, int p, int ky, int kx,
-                                                  bool ok, int t) {
-  constexpr int TL = N / 16;
-  const long long gst = (long long)p * a.compStride + (long long)ky * a.outerStride + kx;
-#pragma unroll
-  for (int e = 0; e < 16; ++e) {
-    const long long gi = gst + (long long)rr_krow<TL>(t, e) * a.rowStride;
-    cp_async_pred<(int)sizeof(cx<T>)>(&slot[e * ss], ok ? &a.st0[gi] : a.st0, ok);
-    if constexpr (NST == 2) cp_async_pred<(int)sizeof(cx<T>)>(&slot[(16 + e) * ss], ok ? &a.st1[gi] : a.st1, ok);
   }
 }
 
@@ -324,82 +315,21 @@ __device__ __forceinline__ void rr_prefetch_state(const PassArgs<T>& a, cx<T>* s
 //                    and the Parseval partials of the divergence residuals, inverse.
 //   OP_SOLUTE (z)    forward of (tau_0, s''), F^ = s'' + i d0 tau_0, Eq. 20 with
 //                    the Parseval partials of Eq. 19, inverse of (i d0 chi^, chi^).
-//
-// The work on one tile whose inputs are already in registers (x-ordered,
-// v[m] = x[t + TL m], for the forward operators; k-ordered, v[e] = X[krow(t, e)],
-// for the inverse ones), ending with the stores to global memory. sq / sd:
-// the thread's state slots (z passes). part: the tile's partial-sum record.
-template <typename T, int N, int OP, int NC, int W>
-__device__ __forceinline__ void rr_apply(const PassArgs<T>& a, cx<T> (&u)[rr_nin<OP, NC>()][16], int p, int outer,
-                                         int kx, bool ok, cx<T>* base, int col, int t, cx<T>* buf0, cx<T>* buf1,
-                                         const cx<T>* tw, const cx<T>* sq, const cx<T>* sd, int ss, T* red,
-                                         double* part) {
-  constexpr int TL = N / 16;
-  if constexpr (OP == OP_FWD) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      rr_fft<T, N, -1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
-      rr_store_k<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
-    }
-  } else if constexpr (OP == OP_INV) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      rr_ifft<T, N, +1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
-      rr_store_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
-    }
-  } else if constexpr (OP == OP_FWD_SOL) {
-    rr_fft<T, N, -1>(u[0], buf0, tw, col, t);
-    rr_store_k<T, N>(u[0], base, a.rowStride, t, ok);
-    rr_fft<T, N, -1>(u[1], buf1, tw, col, t);
-    rr_fft<T, N, -1>(u[2], buf0, tw, col, t);
-#pragma unroll
-    for (int e = 0; e < 16; ++e) u[2][e] = u[2][e] + cscale(mul_i(u[1][e]), a.sym.d1[rr_krow<TL>(t, e)]);
-    rr_store_k<T, N>(u[2], base + a.compStride, a.rowStride, t, ok);
-  } else if constexpr (OP == OP_INV_SOL) {
-    rr_ifft<T, N, +1>(u[0], buf0, tw, col, t);
-    rr_store_x<T, N>(u[0], base, a.rowStride, t, ok);
-    cx<T> v[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = cscale(mul_i(u[1][e]), a.sym.d1[rr_krow<TL>(t, e)]);
-    rr_ifft<T, N, +1>(v, buf1, tw, col, t);
-    rr_store_x<T, N>(v, base + a.compStride, a.rowStride, t, ok);
-    rr_ifft<T, N, +1>(u[1], buf0, tw, col, t);
-    // i d2(kx) applied after the (linear) transform: a factor per column
-    const T d2 = ok ? a.sym.d2[kx] : (T)0;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) u[1][m] = cscale(mul_i(u[1][m]), d2);
-    rr_store_x<T, N>(u[1], base + 2 * a.compStride, a.rowStride, t, ok);
-  } else {
-    constexpr int NIN = rr_nin<OP, NC>();
-#pragma unroll
-    for (int c = 0; c < NIN; ++c) rr_fft<T, N, -1>(u[c], (c & 1) ? buf1 : buf0, tw, col, t);
-    T acc[3] = {(T)0, (T)0, (T)0};
-    if constexpr (OP == OP_STOKES) rr_stokes_op<T, N>(a, u, p, outer, kx, ok, t, sq, sd, ss, acc);
-    else rr_solute_op<T, N>(a, u, p, outer, kx, ok, t, sq, ss, acc);
-    block_sum_store<3>(acc, red, part);
-    // the sums' barriers separate the last forward transform's buffer reads from
-    // the inverse transforms' writes
-#pragma unroll
-    for (int c = 0; c < NIN; ++c) {
-      rr_ifft<T, N, +1>(u[c], ((c + NIN) & 1) ? buf1 : buf0, tw, col, t);
-      rr_store_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
-    }
-  }
-}
-
 // One tile per block (blockIdx.x = problem x live tiles + tile); inputs loaded
-// from global memory straight into registers.
+// from global memory straight into registers; a z pass writes one partial-sum
+// record per tile.
 template <typename T, int N, int OP, int NC, int W>
 __global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
-  using C = RCfg<T, N, W, rr_nst<OP>()>;
-  constexpr int NIN = rr_nin<OP, NC>(), NST = rr_nst<OP>();
-  constexpr bool FWDIN = OP == OP_FWD || OP == OP_FWD_SOL || OP == OP_STOKES || OP == OP_SOLUTE;
+  using C = RCfg<T, N, W>;
+  constexpr int NIN = rr_nin<OP, NC>();
+  constexpr bool ZOP = OP == OP_STOKES || OP == OP_SOLUTE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* buf1 = buf0 + W * C::BS;
-  cx<T>* tw = buf1 + W * C::BS;
-  cx<T>* stp = tw + N;  // state slots [value][element][thread]
+  // twiddles after the buffers: NIN of them in a z pass, two otherwise
+  cx<T>* tw = buf0 + (ZOP ? NIN : 2) * W * C::BS;
   __shared__ T red[4 * 32];
+  __shared__ T opar[5];
   const RTiles tl = rr_tiles(a.Pu, a.nouter, W);
   const int p = blockIdx.x / tl.nlive, r = blockIdx.x % tl.nlive;
   if ((a.sprm && a.sprm[p].done) || (a.cprm && a.cprm[p].done)) return;
@@ -408,8 +338,59 @@ __global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
   rr_tile_lane(tl, r, W, col, a.Pu, &outer, &kx);
   const bool ok = kx < a.Pu;
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = a.twg[k * (TW_MAX / N)];
+  if constexpr (ZOP) {
+    // the operator's parameters, converted once per block
+    if (threadIdx.x == 0) {
+      if constexpr (OP == OP_STOKES) {
+        opar[0] = (T)a.sprm[p].nu;
+        opar[1] = (T)a.sprm[p].psi[1];
+        opar[2] = (T)a.sprm[p].psi[2];
+      } else {
+        opar[0] = (T)a.cprm[p].A0;
+        for (int k = 0; k < 3; ++k) opar[1 + k] = (T)a.cprm[p].B0[k];
+      }
+      opar[4] = (T)a.invV;
+    }
+  }
   cx<T>* base = a.spec + p * a.probStride + (long long)outer * a.outerStride + kx;
-  if constexpr (OP == OP_FWD || OP == OP_INV) {
+  if constexpr (ZOP) {
+    // One component at a time: forward transform in registers (the next
+    // component's loads in flight), its k-ordered values parked in slots of its
+    // own buffer private to the thread (sl[c][e * NT]); the operator reads and
+    // rewrites the slots element by element; then one inverse transform at a
+    // time through the same buffers. Registers hold two components at most.
+    constexpr int NT = C::NT;
+    cx<T>* sl[NIN];
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) sl[c] = buf0 + c * W * C::BS + threadIdx.x;
+    cx<T> v[16], w[16];
+    rr_load_x<T, N>(v, base, a.rowStride, t, ok);
+    __syncthreads();  // twiddles and parameters
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) {
+      cx<T>(&cur)[16] = (c & 1) ? w : v;
+      cx<T>(&nxt)[16] = (c & 1) ? v : w;
+      if (c + 1 < NIN) rr_load_x<T, N>(nxt, base + (c + 1) * a.compStride, a.rowStride, t, ok);
+      cx<T>* bc = buf0 + c * W * C::BS;
+      rr_fft<T, N, -1>(cur, bc, tw, col, t);
+      __syncthreads();  // every thread has read its transposed values from bc
+#pragma unroll
+      for (int e = 0; e < 16; ++e) sl[c][e * NT] = cur[e];
+    }
+    T acc[3] = {(T)0, (T)0, (T)0};
+    if constexpr (OP == OP_STOKES) rz_stokes_op<T, N, NT>(a, sl, opar, p, outer, kx, ok, t, acc);
+    else rz_solute_op<T, N, NT>(a, sl, opar, p, outer, kx, ok, t, acc);
+    block_sum_store<3>(acc, red, a.part + ((long long)p * tl.nlive + r) * 4);
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) {
+      cx<T>* bc = buf0 + c * W * C::BS;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[e] = sl[c][e * NT];
+      __syncthreads();  // every thread holds its slots of c before bc is a transpose buffer again
+      rr_ifft<T, N, +1>(v, bc, tw, col, t);
+      rr_store_x<T, N>(v, base + c * a.compStride, a.rowStride, t, ok);
+    }
+  } else if constexpr (OP == OP_FWD || OP == OP_INV) {
     // component c + 1 travels while component c is transformed
     cx<T> v[16], w[16];
     if constexpr (OP == OP_FWD) rr_load_x<T, N>(v, base, a.rowStride, t, ok);
@@ -448,22 +429,25 @@ __global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
     for (int e = 0; e < 16; ++e) v[e] = v[e] + w[e];
     rr_store_k<T, N>(v, base + a.compStride, a.rowStride, t, ok);
   } else {
-    // OP_INV_SOL and the z passes: every input component in registers first
-    cx<T> u[NIN][16];
-#pragma unroll
-    for (int c = 0; c < NIN; ++c) {
-      if constexpr (FWDIN) rr_load_x<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
-      else rr_load_k<T, N>(u[c], base + c * a.compStride, a.rowStride, t, ok);
-    }
-    if constexpr (NST > 0) {
-      rr_prefetch_state<T, N, NST>(a, stp + threadIdx.x, C::NT, p, outer, kx, ok, t);
-      cp_async_commit();
-    }
+    // OP_INV_SOL: both inputs in registers first
+    constexpr int TL = N / 16;
+    static_assert(OP == OP_INV_SOL, "inverse solute pass");
+    cx<T> v[16], w[16];
+    rr_load_k<T, N>(v, base, a.rowStride, t, ok);
+    rr_load_k<T, N>(w, base + a.compStride, a.rowStride, t, ok);
     __syncthreads();
-    if constexpr (NST > 0) cp_async_wait<0>();
-    rr_apply<T, N, OP, NC, W>(a, u, p, outer, kx, ok, base, col, t, buf0, buf1, tw, stp + threadIdx.x,
-                              stp + 16 * C::NT + threadIdx.x, C::NT, red,
-                              a.part + ((long long)p * tl.nlive + r) * 4);
+    rr_ifft<T, N, +1>(v, buf0, tw, col, t);
+    rr_store_x<T, N>(v, base, a.rowStride, t, ok);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = cscale(mul_i(w[e]), a.sym.d1[rr_krow<TL>(t, e)]);
+    rr_ifft<T, N, +1>(v, buf1, tw, col, t);
+    rr_store_x<T, N>(v, base + a.compStride, a.rowStride, t, ok);
+    rr_ifft<T, N, +1>(w, buf0, tw, col, t);
+    // i d2(kx) applied after the (linear) transform: a factor per column
+    const T d2 = ok ? a.sym.d2[kx] : (T)0;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) w[m] = cscale(mul_i(w[m]), d2);
+    rr_store_x<T, N>(w, base + 2 * a.compStride, a.rowStride, t, ok);
   }
 }
 

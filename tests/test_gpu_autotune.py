@@ -67,10 +67,10 @@ def test_every_tile_width_gives_identical_fields(lib, shape, fp64):
     base, opts = _widths(lib, ctx, fp64)
     assert any(len(v) > 1 for v in opts.values())
     # the register-resident variant exists for every tuned pass at 64, 128 and
-    # 256 points, except the FP64 z Stokes pass
+    # 256 points
     for k, ws in opts.items():
         n = shape[1] if k.startswith("y") else shape[0]
-        want = n in (64, 128, 256) and not (fp64 and k == "z_stokes")
+        want = n in (64, 128, 256)
         assert any(w < 0 for w in ws) == want, (k, ws)
     u0, r0 = _stokes(lib, ctx, H, fp64)
     uin = 1e3 * u0
