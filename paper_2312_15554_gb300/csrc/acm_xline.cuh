@@ -149,13 +149,22 @@ __device__ __forceinline__ void xl_inverse(cx<T>* sl, const cx<T>* tw, int t, un
 }
 
 // Forward real transform of one line: v[m] = z[t + TL m] in; on return
-// X[m] = X_{t + TL m} (m = 0..E-1) and, on lane t = 0, xn = X_M. sl is used
-// as exchange buffer (its previous contents are dropped).
+// X[m] = X_{t + TL m} (m = 0..E-1) and, on lane t = 0, xn = X_M (X may be v).
+// sl is used as exchange buffer (its previous contents are dropped) and is
+// free for the line's lanes on return.
+//
+// The post-processing pairs Z_k with Z_{M-k}. With k = t + TL m, M - k is
+// position E-1-m of lane TL - t when t > 0, and position E - m of lane 0 itself
+// when t = 0, so the partners travel by warp shuffles (lane t exchanges with
+// lane (TL - t) mod TL of its line) instead of a second pass through sl.
+// Positions m and E-1-m are finished together; lane 0's partner E - m of
+// position m was overwritten one step earlier and is carried in a register.
 template <typename T, int N2>
 __device__ __forceinline__ void xl_forward(cx<T>* sl, const cx<T>* tw, int t, unsigned mask,
                                            cx<T> (&v)[XL<T, N2>::E], cx<T> (&X)[XL<T, N2>::E], cx<T>& xn) {
   using L = XL<T, N2>;
   constexpr int M = L::M, E = L::E, TL = L::TL;
+  static_assert(E % 2 == 0, "positions finish in pairs");
   const cx<T> wt = tw[tw_total(M) + t];
   dft<E, -1>(v);
   __syncwarp(mask);  // earlier readers of sl are done
@@ -164,23 +173,32 @@ __device__ __forceinline__ void xl_forward(cx<T>* sl, const cx<T>* tw, int t, un
   if constexpr (TL > 1) {
     __syncwarp(mask);
     xl_stage2<T, N2, -1>(sl, tw, t, v);
-    __syncwarp(mask);
-    // stage-2 outputs back to their positions t + TL m for the pairing
-#pragma unroll
-    for (int m = 0; m < E; ++m) sl[pad(t + TL * m)] = v[m];
+    __syncwarp(mask);  // the stage-2 reads are done before sl is reused
   }
-  __syncwarp(mask);
-  // Z_k is the lane's own value (still in v); only Z_{M-k} comes from another lane
-  static_for<E>([&](auto I) {
-    constexpr int m = decltype(I)::value;
-    const int k = t + TL * m;
-    const cx<T> Zk = v[m];
-    if (k == 0) {
-      X[m] = mk<T>(Zk.x + Zk.y, (T)0);
-      xn = mk<T>(Zk.x - Zk.y, (T)0);
+  // Z_k sits in v[m] of its own lane
+  const int lane = threadIdx.x & 31;
+  const int src = (lane - t) + (TL - t) % TL;
+  cx<T> carry = mk<T>((T)0, (T)0);
+  static_for<E / 2>([&](auto I) {
+    constexpr int m = decltype(I)::value, mb = E - 1 - m;
+    const cx<T> a = v[m], b = v[mb];
+    cx<T> pa, pb;  // the partner lane's v[E-1-m] and v[m]
+    pa.x = __shfl_sync(mask, b.x, src);
+    pa.y = __shfl_sync(mask, b.y, src);
+    pb.x = __shfl_sync(mask, a.x, src);
+    pb.y = __shfl_sync(mask, a.y, src);
+    // lane 0: Z_{M-k} of position m is its own old v[E-m] (carried; position 0
+    // is k = 0), that of position E-1-m its own v[m+1] (b itself when m+1 = E-1-m)
+    const cx<T> zm = t == 0 ? carry : pa;
+    const cx<T> zb = t == 0 ? (m + 1 == mb ? b : v[m + 1 < E ? m + 1 : 0]) : pb;
+    carry = b;
+    if (m == 0 && t == 0) {
+      X[m] = mk<T>(a.x + a.y, (T)0);
+      xn = mk<T>(a.x - a.y, (T)0);
     } else {
-      X[m] = xl_post<m, E>(Zk, sl[pad(M - k)], wt);
+      X[m] = xl_post<m, E>(a, zm, wt);
     }
+    X[mb] = xl_post<mb, E>(b, zb, wt);
   });
 }
 
