@@ -869,7 +869,8 @@ acm_status solute_body(acm_ctx* c, int nprob, const uint8_t* Hdev, const void* u
   const long long ps = 4 * g.S;
   // spectral components per problem: x -> (tau_0, tau_1, s + d2 tau_2), y forward -> (tau_0, s''),
   // z -> (d0 chi, chi), y inverse -> (d0 chi, d1 chi, d2 chi)
-  LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym, c->st));
+  LK(ACM_K_X_SOLUTE, Ops<T>::x_solute(g, nprob, w.spec, udev, Hdev, c->Hb, c->cprm, w.tw, sym,
+                                     c->solute_deriv == ACM_DERIV_CENTRAL, c->st));
   LK(ACM_K_Y_FWD_SOLUTE, Ops<T>::pass(g, 1, P_FWD_SOL, 3, nprob, w.spec, ps, sym, w.tw, nullptr, nullptr, nullptr, c->cprm,
                                      nullptr, c->st));
   LK(ACM_K_Z_SOLUTE, Ops<T>::pass(g, 0, P_SOLUTE, 2, nprob, w.spec, ps, sym, w.tw, w.st0, nullptr, nullptr, c->cprm,

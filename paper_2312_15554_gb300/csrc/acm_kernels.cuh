@@ -411,13 +411,17 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
 //   tau = (A - A0)(grad chi + g),  s = F - (B - B0).(grad chi + g),
 //   A = (1 - H) + eta H,  B = Pe (1 - H) u,  F = Pe (1 - H) ubar.g,
 // then R2C of (tau_0, tau_1, tau_2, s), stored as (tau_0, tau_1, s + i d2 tau_2).
+// With the central symbols of Eq. 21 (CEN), i d2(kx) is the transform of the
+// periodic central difference (f[j+1] - f[j-1]) N2 / 2 along the line, so
+// s + D2 tau_2 is formed on the voxels and one R2C replaces two; the
+// neighbouring values of tau_2 come from the adjacent lanes by warp shuffles.
 //
 // Line-resident (acm_xline.cuh): every warp owns LPW lines; their three
 // spectrum rows arrive by cp.async, then each component is inverse-transformed
 // into registers, turned into tau_c (and its share of s accumulated) on the
 // same registers and forward-transformed, without a block-wide barrier.
 // ---------------------------------------------------------------------------
-template <typename T, int N2>
+template <typename T, int N2, bool CEN>
 __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
     k_x_solute(cx<T>* __restrict__ spec, const T* __restrict__ u, const uint8_t* __restrict__ H,
                const uint32_t* __restrict__ Hb, const SoluteDev* __restrict__ prm, Geo g,
@@ -429,8 +433,8 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* lines = tw + xs_tw_slots<T, N2>();
-  // s accumulated per lane: [m][lane] for conflict-free access
-  T* acc = reinterpret_cast<T*>(lines + XS_WARPS * LPW * LB) + (threadIdx.x >> 5) * 32 * 2 * E;
+  // s accumulated per lane as voxel pairs: [m][lane] for conflict-free access
+  T2* acc = reinterpret_cast<T2*>(lines + XS_WARPS * LPW * LB) + (threadIdx.x >> 5) * 32 * E;
   // Problems that share one velocity and indicator (us = hs = 0, e.g. the three
   // composition loads of a tensor solve) run back to back on the same warp, so
   // each velocity row crosses DRAM once (up to XS_PCACHE problems per block,
@@ -488,7 +492,12 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
       }
       cp_async_commit();
 #pragma unroll
-      for (int m = 0; m < 2 * E; ++m) acc[m * 32 + lane] = (T)0;
+      for (int m = 0; m < E; ++m) {
+        T2 z;
+        z.x = (T)0;
+        z.y = (T)0;
+        acc[m * 32 + lane] = z;
+      }
       cp_async_wait<0>();
       __syncwarp(mask);
       cx<T> v[E];
@@ -513,18 +522,42 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
               uu = *reinterpret_cast<const T2*>(uc + 2 * k);
             }
             const T ea = v[m].x + gc, eb = v[m].y + gc;
-            acc[(2 * m) * 32 + lane] += (Bc - (sa ? (T)0 : Pe * uu.x)) * ea;
-            acc[(2 * m + 1) * 32 + lane] += (Bc - (sb ? (T)0 : Pe * uu.y)) * eb;
+            T2 a2 = acc[m * 32 + lane];
+            a2.x += (Bc - (sa ? (T)0 : Pe * uu.x)) * ea;
+            a2.y += (Bc - (sb ? (T)0 : Pe * uu.y)) * eb;
+            acc[m * 32 + lane] = a2;
             v[m].x = ((sa ? eta : (T)1) - A0) * ea;
             v[m].y = ((sb ? eta : (T)1) - A0) * eb;
           }
+          if (CEN && c == 2) {
+            // s += D2 tau_2: the neighbours of the lane's pair 2k, 2k+1 are
+            // voxel 2k - 1 (lane t - 1, or lane TL - 1 at position m - 1) and
+            // 2k + 2 (lane t + 1, or lane 0 at position m + 1); each lane hands
+            // on the value its neighbour needs
+            const T hc = (T)(N2 / 2);
+            const int lb = lane - t;
+            const int src_r = lb + (t + 1) % TL, src_l = lb + (t + TL - 1) % TL;
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+              const T pr = t == 0 ? v[(m + 1) % E].x : v[m].x;
+              const T pl = t == TL - 1 ? v[(m + E - 1) % E].y : v[m].y;
+              const T right = __shfl_sync(mask, pr, src_r), left = __shfl_sync(mask, pl, src_l);
+              T2 a2 = acc[m * 32 + lane];
+              a2.x += (v[m].y - left) * hc;
+              a2.y += (right - v[m].x) * hc;
+              acc[m * 32 + lane] = a2;
+            }
+            continue;  // tau_2 itself is not transformed
+          }
         } else {
           // s = F - (B - B0).(grad chi + g): the accumulated terms plus Pe ubar.g on pore voxels
+          // (with CEN also + D2 tau_2)
           const T Fc = spar[p - pbeg][9];
 #pragma unroll
           for (int m = 0; m < E; ++m) {
             const bool sa = (hm >> (2 * m)) & 1u, sb = (hm >> (2 * m + 1)) & 1u;
-            v[m] = mk<T>(acc[(2 * m) * 32 + lane] + (sa ? (T)0 : Fc), acc[(2 * m + 1) * 32 + lane] + (sb ? (T)0 : Fc));
+            const T2 a2 = acc[m * 32 + lane];
+            v[m] = mk<T>(a2.x + (sa ? (T)0 : Fc), a2.y + (sb ? (T)0 : Fc));
           }
         }
         cx<T> xn;
@@ -548,6 +581,11 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
           for (int m = 0; m < E; ++m) b1[pad(t + TL * m)] = cscale(mul_i(v[m]), d2[t + TL * m]);
           if (t == 0) b1[pad(M)] = cscale(mul_i(xn), d2[M]);
+        } else if (CEN) {
+          cx<T>* dst = sp + 2 * g.S + line * g.P;
+#pragma unroll
+          for (int m = 0; m < E; ++m) dst[t + TL * m] = v[m];
+          if (t == 0) dst[M] = xn;
         } else {
           cx<T>* dst = sp + 2 * g.S + line * g.P;
 #pragma unroll

@@ -31,7 +31,7 @@ struct Ops {
                                   cudaStream_t s);
   static cudaError_t x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
                               const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym,
-                              cudaStream_t s);
+                              bool central, cudaStream_t s);
   // nc in {1, 3}
   static cudaError_t x_r2c(const Geo& g, int nprob, int nc, void* spec, long long specProbStride,
                            const void* in, long long inProbStride, const void* tw, cudaStream_t s);

@@ -77,10 +77,13 @@ static cudaError_t l_x_rhs(const Geo& g, int nprob, void* spec, const void* u, c
 
 template <typename T, int N2>
 static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
-                              const uint32_t* Hb, const SoluteDev* prm, const void* tw, const T* d2, cudaStream_t s) {
+                              const uint32_t* Hb, const SoluteDev* prm, const void* tw, const T* d2, bool central,
+                              cudaStream_t s) {
   constexpr int smem = xs_smem_bytes<T, N2, 2, 2 * XL<T, N2>::E>();
-  static const cudaError_t attr = set_smem(k_x_solute<T, N2>, smem);
-  if (attr != cudaSuccess) return attr;
+  static const cudaError_t attr0 = set_smem(k_x_solute<T, N2, false>, smem);
+  static const cudaError_t attr1 = set_smem(k_x_solute<T, N2, true>, smem);
+  if (attr0 != cudaSuccess) return attr0;
+  if (attr1 != cudaSuccess) return attr1;
   // problems sharing the velocity and the indicator loop inside the kernel (up
   // to XS_PCACHE per block), with fewer line groups per warp so that the grid
   // keeps its size
@@ -89,8 +92,12 @@ static cudaError_t l_x_solute(const Geo& g, int nprob, void* spec, const void* u
   const int gpw = shared ? (XS_GPW / np_blk > 1 ? XS_GPW / np_blk : 1) : XS_GPW;
   const int ngroups = g.n0 * g.n1 / XL<T, N2>::LPW;
   dim3 grid((ngroups + XS_WARPS * gpw - 1) / (XS_WARPS * gpw), shared ? (nprob + XS_PCACHE - 1) / XS_PCACHE : nprob);
-  k_x_solute<T, N2><<<grid, XS_WARPS * 32, smem, s>>>((cx<T>*)spec, (const T*)u, H, Hb, prm, g, (const cx<T>*)tw,
-                                                        d2, nprob, gpw);
+  if (central)
+    k_x_solute<T, N2, true><<<grid, XS_WARPS * 32, smem, s>>>((cx<T>*)spec, (const T*)u, H, Hb, prm, g,
+                                                               (const cx<T>*)tw, d2, nprob, gpw);
+  else
+    k_x_solute<T, N2, false><<<grid, XS_WARPS * 32, smem, s>>>((cx<T>*)spec, (const T*)u, H, Hb, prm, g,
+                                                                (const cx<T>*)tw, d2, nprob, gpw);
   return cudaGetLastError();
 }
 
@@ -363,8 +370,8 @@ cudaError_t Ops<T>::x_stokes_rhs(const Geo& g, int nprob, void* spec, const void
 template <typename T>
 cudaError_t Ops<T>::x_solute(const Geo& g, int nprob, void* spec, const void* u, const uint8_t* H,
                              const uint32_t* Hb, const SoluteDev* prm, const void* tw, const Sym<T>& sym,
-                             cudaStream_t s) {
-  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, Hb, prm, tw, sym.d2, s)
+                             bool central, cudaStream_t s) {
+  ACM_DISPATCH_N(g.n2, l_x_solute, g, nprob, spec, u, H, Hb, prm, tw, sym.d2, central, s)
 }
 
 template <typename T>
