@@ -692,15 +692,18 @@ struct SCfg {
   static constexpr int SMEM = (NC * TX * LS + tw_total(N)) * (int)sizeof(cx<T>);
 };
 
+// Transforms the tile's lines (line = component * TX + column); lines of the
+// columns w..TX-1 that a tile at the end of a pencil leaves empty are skipped.
 template <typename T, int N, int OP, int NC, int TX, int SIGN, int NLINES>
-__device__ __forceinline__ void s_fft(cx<T>* sm, const cx<T>* tw) {
+__device__ __forceinline__ void s_fft(cx<T>* sm, const cx<T>* tw, int w) {
   using C = SCfg<T, N, OP, NC, TX>;
   constexpr int per_round = C::NT / C::TL;
 #pragma unroll 1
   for (int r = 0; r < C::ROUNDS; ++r) {
     const int job = r * per_round + threadIdx.x / C::TL;
-    const unsigned mask = __ballot_sync(0xffffffffu, job < NLINES);
-    if (job < NLINES) fft_line<T, N, SIGN>(sm + job * C::LS, threadIdx.x % C::TL, tw, mask);
+    const bool live = job < NLINES && job % TX < w;
+    const unsigned mask = __ballot_sync(0xffffffffu, live);
+    if (live) fft_line<T, N, SIGN>(sm + job * C::LS, threadIdx.x % C::TL, tw, mask);
   }
 }
 
@@ -766,9 +769,9 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
       }
       __syncthreads();
     }
-    s_fft<T, N, OP, NC, TX, +1, NC * TX>(sm, tw);
+    s_fft<T, N, OP, NC, TX, +1, NC * TX>(sm, tw, w);
   } else {
-    s_fft<T, N, OP, NC, TX, -1, NIN * TX>(sm, tw);
+    s_fft<T, N, OP, NC, TX, -1, NIN * TX>(sm, tw, w);
   }
   if constexpr (OP == OP_FWD_SOL) {
     // s'' = s' + i d1(ky) tau_1 into line 1
@@ -790,7 +793,7 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
       x = cscale(mul_i(x), d * invV);
     }
     __syncthreads();
-    s_fft<T, N, OP, NC, TX, +1, NC * TX>(sm, tw);
+    s_fft<T, N, OP, NC, TX, +1, NC * TX>(sm, tw, w);
   }
   if constexpr (OP == OP_STOKES || OP == OP_SOLUTE) {
     __syncthreads();
@@ -916,7 +919,7 @@ __global__ void __launch_bounds__(SCfg<T, N, OP, NC, TX>::NT) k_strided(PassArgs
     const int nb = gridDim.x * gridDim.y;
     block_sum_store<3>(v3, red, a.part + ((long long)p * nb + blockIdx.y * gridDim.x + blockIdx.x) * 4);
     __syncthreads();
-    s_fft<T, N, OP, NC, TX, +1, NOUT * TX>(sm, tw);
+    s_fft<T, N, OP, NC, TX, +1, NOUT * TX>(sm, tw, w);
   }
   __syncthreads();
   // OP_INV_SOL: line 2 leaves as i d2(kx) b; with NT a multiple of TX every
@@ -954,20 +957,21 @@ __global__ void __launch_bounds__(256) k_field_sums(const T* __restrict__ u, con
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; v0 < V; v0 += stride * CHK) {
     T c[7] = {0, 0, 0, 0, 0, 0, 0};
+    // predicated (not early-exit) iterations, so the loads of an unrolled
+    // group are all in flight together
 #pragma unroll 4
     for (int k = 0; k < CHK; ++k) {
       const long long v = v0 + k * stride;
-      if (v >= V) break;
-      const T a = up[v], b = up[V + v], cc = up[2 * V + v];
+      const bool in = v < V;
+      const T a = in ? up[v] : (T)0, b = in ? up[V + v] : (T)0, cc = in ? up[2 * V + v] : (T)0;
+      const bool pore = in && Hp[in ? v : 0] == 0;
       c[0] += a;
       c[1] += b;
       c[2] += cc;
-      if (Hp[v] == 0) {
-        c[3] += a;
-        c[4] += b;
-        c[5] += cc;
-        c[6] += (T)1;
-      }
+      c[3] += pore ? a : (T)0;
+      c[4] += pore ? b : (T)0;
+      c[5] += pore ? cc : (T)0;
+      c[6] += pore ? (T)1 : (T)0;
     }
 #pragma unroll
     for (int k = 0; k < 7; ++k) acc[k] += (double)c[k];
@@ -998,19 +1002,22 @@ __global__ void __launch_bounds__(256) k_diffusivity(const T* __restrict__ chi, 
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; v0 < V; v0 += stride * CHK) {
     T c[6] = {0, 0, 0, 0, 0, 0};
+    // predicated (not early-exit) iterations, so the loads of an unrolled
+    // group are all in flight together
 #pragma unroll 4
     for (int k = 0; k < CHK; ++k) {
       const long long v = v0 + k * stride;
-      if (v >= V) break;
-      const T ch = cp[v];
-      const bool pore = Hp[v] == 0;
+      const bool in = v < V;
+      const long long vi = in ? v : 0;
+      const T ch = cp[vi];
+      const bool pore = Hp[vi] == 0;
       const T A = pore ? (T)1 : eta;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const T gi = gg[i] + gp[i * V + v];
-        const T pe = pore ? Pe * (ub[i] - up[i * V + v]) * ch : (T)0;
-        if (pore) c[i] += gi + pe;
-        c[3 + i] += A * gi + pe;
+        const T gi = gg[i] + gp[i * V + vi];
+        const T pe = pore ? Pe * (ub[i] - up[i * V + vi]) * ch : (T)0;
+        c[i] += (in && pore) ? gi + pe : (T)0;
+        c[3 + i] += in ? A * gi + pe : (T)0;
       }
     }
 #pragma unroll
@@ -1030,12 +1037,14 @@ __global__ void __launch_bounds__(256) k_pore_products(const T* __restrict__ f, 
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; v0 < V; v0 += stride * CHK) {
     T c[6] = {0, 0, 0, 0, 0, 0};
+    // predicated (not early-exit) iterations, so the loads of an unrolled
+    // group are all in flight together
 #pragma unroll 4
     for (int k = 0; k < CHK; ++k) {
       const long long v = v0 + k * stride;
-      if (v >= V) break;
-      if (H[v]) continue;
-      const T a = f[v], b = f[V + v], d = f[2 * V + v];
+      const long long vi = v < V ? v : 0;
+      const bool use = v < V && H[vi] == 0;
+      const T a = use ? f[vi] : (T)0, b = use ? f[V + vi] : (T)0, d = use ? f[2 * V + vi] : (T)0;
       c[0] += a * a;
       c[1] += a * b;
       c[2] += a * d;
