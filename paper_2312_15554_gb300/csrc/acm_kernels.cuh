@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
   using L = XL<T, N2>;
   constexpr int M = L::M, E = L::E, TL = L::TL, LPW = L::LPW, LS = L::LS;
   constexpr int LB = L::template lb<2>();
-  constexpr int CH = E < 8 ? E : 8;  // voxel pairs per load-then-store chunk
+  constexpr int CH = E < 4 ? E : 4;  // voxel pairs per load-then-store chunk
   using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
     __syncwarp(mask);
     T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
     cx<T> v[E];
-    static_assert(E % CH == 0 && E / CH <= 2, "two chunks per component");
+    static_assert(E % CH == 0, "whole chunks per component");
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
       cx<T>* bc = c == 1 ? b1 : b0;
@@ -304,9 +304,16 @@ __global__ void __launch_bounds__(XS_WARPS * 32, sizeof(T) == 4 ? 2 : 1)
         for (int e = t; e <= M; e += TL) cp_async<(int)sizeof(cx<T>)>(&b0[pad(e)], &srow[2 * g.S + e]);
         cp_async_commit();
       }
-      if constexpr (E / CH == 2) load_chunk(CH, ub, lb);
-      step_chunk(0, ua, la);
-      if constexpr (E / CH == 2) step_chunk(CH, ub, lb);
+      // rolling: chunk j + 1 travels while chunk j is stepped
+#pragma unroll
+      for (int j = 0; j < E / CH; ++j) {
+        if (j + 1 < E / CH) {
+          if (j & 1) load_chunk((j + 1) * CH, ua, la);
+          else load_chunk((j + 1) * CH, ub, lb);
+        }
+        if (j & 1) step_chunk(j * CH, ub, lb);
+        else step_chunk(j * CH, ua, la);
+      }
       if (c == 1) {
         cp_async_wait<0>();
         __syncwarp(mask);
