@@ -230,11 +230,16 @@ static cudaError_t l_pass_rr(const Geo& g, int axis, int nprob, void* spec, long
                              cudaStream_t s) {
   using C = RCfg<T, N, W>;
   constexpr int smem = rr_smem<T, N, OP, NC, W>();
-  static const cudaError_t attr = set_smem(k_rstrided<T, N, OP, NC, W>, smem);
+  constexpr bool wide = rr_y_wide<T, OP, W>() && N == 256;
+  static const cudaError_t attr = [] {
+    if constexpr (wide) return set_smem(k_rstrided_w<T, N, OP, NC, W>, smem);
+    else return set_smem(k_rstrided<T, N, OP, NC, W>, smem);
+  }();
   if (attr != cudaSuccess) return attr;
   const PassArgs<T> a = pass_args<T>(g, axis, spec, probStride, sym, tw, st0, st1, sprm, cprm, part, 0);
   const RTiles tl = rr_tiles(g.Pu, a.nouter, W);
-  k_rstrided<T, N, OP, NC, W><<<nprob * tl.nlive, C::NT, smem, s>>>(a);
+  if constexpr (wide) k_rstrided_w<T, N, OP, NC, W><<<nprob * tl.nlive, C::NT, smem, s>>>(a);
+  else k_rstrided<T, N, OP, NC, W><<<nprob * tl.nlive, C::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

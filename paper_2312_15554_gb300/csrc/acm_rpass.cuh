@@ -319,7 +319,7 @@ __device__ __forceinline__ void rz_solute_op(const PassArgs<T>& a, cx<T>* const 
 // from global memory straight into registers; a z pass writes one partial-sum
 // record per tile.
 template <typename T, int N, int OP, int NC, int W>
-__global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
+__device__ __forceinline__ void rr_pass_body(const PassArgs<T>& a) {
   using C = RCfg<T, N, W>;
   constexpr int NIN = rr_nin<OP, NC>();
   constexpr bool ZOP = OP == OP_STOKES || OP == OP_SOLUTE;
@@ -449,6 +449,23 @@ __global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
     for (int m = 0; m < 16; ++m) w[m] = cscale(mul_i(w[m]), d2);
     rr_store_x<T, N>(w, base + 2 * a.compStride, a.rowStride, t, ok);
   }
+}
+
+// the y passes at W = rr_wdef run two blocks per SM whatever their registers
+// (shared memory and the register file), so they are given 128 a thread
+template <typename T, int OP, int W>
+__host__ __device__ constexpr bool rr_y_wide() {
+  return OP != OP_STOKES && OP != OP_SOLUTE && sizeof(T) == 4 && W == rr_wdef<T>();
+}
+
+template <typename T, int N, int OP, int NC, int W>
+__global__ void __launch_bounds__(RCfg<T, N, W>::NT) k_rstrided(PassArgs<T> a) {
+  rr_pass_body<T, N, OP, NC, W>(a);
+}
+
+template <typename T, int N, int OP, int NC, int W>
+__global__ void __launch_bounds__(RCfg<T, N, W>::NT, 2) k_rstrided_w(PassArgs<T> a) {
+  rr_pass_body<T, N, OP, NC, W>(a);
 }
 
 }  // namespace acm
