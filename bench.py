@@ -72,7 +72,7 @@ def algorithmic_bytes_per_voxel(kind: str, n2: int, porosity: float, share: int 
 # kernel at the default workload (256^3, porosity 0.35, 3 problems per launch),
 # from one ncu capture of that kernel (mean over its captured launches). An
 # entry holds only while the kernel is unchanged since that capture.
-MEASURED_TRAFFIC = {"x_solute": 836.852e6 + 569.529e6}
+MEASURED_TRAFFIC = {"x_solute": 836.852e6 + 569.529e6, "x_stokes_local": 2403.660e6 + 1052.283e6}
 
 
 def step_roofline(kern: dict, peak: float) -> dict:
