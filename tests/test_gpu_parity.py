@@ -223,7 +223,7 @@ def test_stokes_tensor_and_gradient_form_match_oracle(lib):
 @pytest.mark.parametrize("deriv", [O.CENTRAL, O.EXACT])
 @pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("explicit_B0", [False, True])
-@pytest.mark.parametrize("shape", [(16, 8, 32), (8, 8, 8), (8, 8, 64), (8, 8, 512)])
+@pytest.mark.parametrize("shape", [(16, 8, 32), (8, 8, 8), (8, 16, 16), (8, 8, 64), (8, 8, 512)])
 def test_solute_fixed_iterations_match_oracle(lib, deriv, fp64, explicit_B0, shape):
     H = I.random_indicator(shape, 0.4, 8)
     u = 0.3 * I.random_field((3,) + shape, 9) * (1 - H)[None]
