@@ -50,11 +50,20 @@ __host__ __device__ constexpr int rr_nin() {
 
 // shared memory of a block (complex elements): two transpose buffers, the
 // twiddles and the per-thread state slots
+// Transpose buffers hold element (k1, t) of a column at k1 TL + t, the columns
+// N + 1 apart, in the wide tiles (a half-warp spans 16 columns, one thread
+// each: conflict-free). In the narrow tiles a half-warp holds two threads of
+// each of 8 columns, so there the element sits at k1 TL + ((t + k1) mod TL) (a
+// skew by k1) and the columns N + 2 apart: the writes by (column, t) and the
+// reads by (column, s) of one access then fall on distinct banks.
 template <typename T, int N, int W>
 struct RCfg {
-  static constexpr int TL = N / 16;  // threads per line
-  static constexpr int NT = W * TL;  // threads per block
-  static constexpr int BS = N + 1;   // column stride of a transpose buffer (odd)
+  static constexpr int TL = N / 16;                          // threads per line
+  static constexpr int NT = W * TL;                          // threads per block
+  static constexpr bool SKEW = W != rr_wdef<T>();            // narrow tile
+  static constexpr int BS = N + (SKEW ? 2 : 1);              // column stride of a transpose buffer
+  // position of element (k1, t) within its column
+  __device__ static __forceinline__ int at(int k1, int t) { return k1 * TL + (SKEW ? ((t + k1) & (TL - 1)) : t); }
 };
 
 // shared memory of a block of pass OP (bytes): transpose buffers of W columns
@@ -62,7 +71,8 @@ struct RCfg {
 // component's slots) and the twiddles
 template <typename T, int N, int OP, int NC, int W>
 __host__ __device__ constexpr int rr_smem() {
-  return (((OP == OP_STOKES || OP == OP_SOLUTE) ? rr_nin<OP, NC>() : 2) * W * (N + 1) + N) * (int)sizeof(cx<T>);
+  return (((OP == OP_STOKES || OP == OP_SOLUTE) ? rr_nin<OP, NC>() : 2) * W * RCfg<T, N, W>::BS + N) *
+         (int)sizeof(cx<T>);
 }
 
 // The live tiles of one problem: nreg = gxr pencils x column blocks, then (when
@@ -105,29 +115,30 @@ __device__ __forceinline__ cx<T> rtw(const cx<T>* tw, int e) {
 
 // Forward-ordered half: on entry v[m] = x[t + TL m]; on exit v[i TL + k2] =
 // X[k1 + 16 k2] with k1 = t + TL i (the thread now owns k1 = t, t + TL, ...).
-template <typename T, int N, int SIGN>
+template <typename T, int N, int W, int SIGN>
 __device__ __forceinline__ void rr_fft(cx<T> (&v)[16], cx<T>* buf, const cx<T>* tw, int col, int t) {
-  constexpr int TL = N / 16, BS = N + 1;
+  constexpr int TL = N / 16, BS = RCfg<T, N, W>::BS;
   dft<16, SIGN>(v);
 #pragma unroll
   for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], rtw<T, N, SIGN>(tw, t * k1));
   cx<T>* b = buf + col * BS;
 #pragma unroll
-  for (int k1 = 0; k1 < 16; ++k1) b[k1 * TL + t] = v[k1];
+  for (int k1 = 0; k1 < 16; ++k1) b[RCfg<T, N, W>::at(k1, t)] = v[k1];
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 16 / TL; ++i) {
+    const int k1 = t + TL * i;
 #pragma unroll
-    for (int tt = 0; tt < TL; ++tt) v[i * TL + tt] = b[(t + TL * i) * TL + tt];
+    for (int tt = 0; tt < TL; ++tt) v[i * TL + tt] = b[RCfg<T, N, W>::at(k1, tt)];
     dft<TL, SIGN>(&v[i * TL]);
   }
 }
 
 // Inverse-ordered half: on entry v[i TL + k2] = X[k1 + 16 k2], k1 = s + TL i;
 // on exit v[m] = x[s + TL m].
-template <typename T, int N, int SIGN>
+template <typename T, int N, int W, int SIGN>
 __device__ __forceinline__ void rr_ifft(cx<T> (&v)[16], cx<T>* buf, const cx<T>* tw, int col, int s) {
-  constexpr int TL = N / 16, BS = N + 1;
+  constexpr int TL = N / 16, BS = RCfg<T, N, W>::BS;
   cx<T>* b = buf + col * BS;
 #pragma unroll
   for (int i = 0; i < 16 / TL; ++i) {
@@ -136,11 +147,11 @@ __device__ __forceinline__ void rr_ifft(cx<T> (&v)[16], cx<T>* buf, const cx<T>*
 #pragma unroll
     for (int tt = 1; tt < TL; ++tt) v[i * TL + tt] = cmul(v[i * TL + tt], rtw<T, N, SIGN>(tw, tt * k1));
 #pragma unroll
-    for (int tt = 0; tt < TL; ++tt) b[k1 * TL + tt] = v[i * TL + tt];
+    for (int tt = 0; tt < TL; ++tt) b[RCfg<T, N, W>::at(k1, tt)] = v[i * TL + tt];
   }
   __syncthreads();
 #pragma unroll
-  for (int k1 = 0; k1 < 16; ++k1) v[k1] = b[k1 * TL + s];
+  for (int k1 = 0; k1 < 16; ++k1) v[k1] = b[RCfg<T, N, W>::at(k1, s)];
   dft<16, SIGN>(v);
 }
 
@@ -372,7 +383,7 @@ __device__ __forceinline__ void rr_pass_body(const PassArgs<T>& a) {
       cx<T>(&nxt)[16] = (c & 1) ? v : w;
       if (c + 1 < NIN) rr_load_x<T, N>(nxt, base + (c + 1) * a.compStride, a.rowStride, t, ok);
       cx<T>* bc = buf0 + c * W * C::BS;
-      rr_fft<T, N, -1>(cur, bc, tw, col, t);
+      rr_fft<T, N, W, -1>(cur, bc, tw, col, t);
       __syncthreads();  // every thread has read its transposed values from bc
 #pragma unroll
       for (int e = 0; e < 16; ++e) sl[c][e * NT] = cur[e];
@@ -387,7 +398,7 @@ __device__ __forceinline__ void rr_pass_body(const PassArgs<T>& a) {
 #pragma unroll
       for (int e = 0; e < 16; ++e) v[e] = sl[c][e * NT];
       __syncthreads();  // every thread holds its slots of c before bc is a transpose buffer again
-      rr_ifft<T, N, +1>(v, bc, tw, col, t);
+      rr_ifft<T, N, W, +1>(v, bc, tw, col, t);
       rr_store_x<T, N>(v, base + c * a.compStride, a.rowStride, t, ok);
     }
   } else if constexpr (OP == OP_FWD || OP == OP_INV) {
@@ -405,10 +416,10 @@ __device__ __forceinline__ void rr_pass_body(const PassArgs<T>& a) {
         else rr_load_k<T, N>(nxt, base + (c + 1) * a.compStride, a.rowStride, t, ok);
       }
       if constexpr (OP == OP_FWD) {
-        rr_fft<T, N, -1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
+        rr_fft<T, N, W, -1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
         rr_store_k<T, N>(cur, base + c * a.compStride, a.rowStride, t, ok);
       } else {
-        rr_ifft<T, N, +1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
+        rr_ifft<T, N, W, +1>(cur, (c & 1) ? buf1 : buf0, tw, col, t);
         rr_store_x<T, N>(cur, base + c * a.compStride, a.rowStride, t, ok);
       }
     }
@@ -418,13 +429,13 @@ __device__ __forceinline__ void rr_pass_body(const PassArgs<T>& a) {
     rr_load_x<T, N>(v, base, a.rowStride, t, ok);
     rr_load_x<T, N>(w, base + a.compStride, a.rowStride, t, ok);
     __syncthreads();
-    rr_fft<T, N, -1>(v, buf0, tw, col, t);
+    rr_fft<T, N, W, -1>(v, buf0, tw, col, t);
     rr_store_k<T, N>(v, base, a.rowStride, t, ok);
     rr_load_x<T, N>(v, base + 2 * a.compStride, a.rowStride, t, ok);
-    rr_fft<T, N, -1>(w, buf1, tw, col, t);
+    rr_fft<T, N, W, -1>(w, buf1, tw, col, t);
 #pragma unroll
     for (int e = 0; e < 16; ++e) w[e] = cscale(mul_i(w[e]), a.sym.d1[rr_krow<TL>(t, e)]);
-    rr_fft<T, N, -1>(v, buf0, tw, col, t);
+    rr_fft<T, N, W, -1>(v, buf0, tw, col, t);
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = v[e] + w[e];
     rr_store_k<T, N>(v, base + a.compStride, a.rowStride, t, ok);
@@ -436,13 +447,13 @@ __device__ __forceinline__ void rr_pass_body(const PassArgs<T>& a) {
     rr_load_k<T, N>(v, base, a.rowStride, t, ok);
     rr_load_k<T, N>(w, base + a.compStride, a.rowStride, t, ok);
     __syncthreads();
-    rr_ifft<T, N, +1>(v, buf0, tw, col, t);
+    rr_ifft<T, N, W, +1>(v, buf0, tw, col, t);
     rr_store_x<T, N>(v, base, a.rowStride, t, ok);
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = cscale(mul_i(w[e]), a.sym.d1[rr_krow<TL>(t, e)]);
-    rr_ifft<T, N, +1>(v, buf1, tw, col, t);
+    rr_ifft<T, N, W, +1>(v, buf1, tw, col, t);
     rr_store_x<T, N>(v, base + a.compStride, a.rowStride, t, ok);
-    rr_ifft<T, N, +1>(w, buf0, tw, col, t);
+    rr_ifft<T, N, W, +1>(w, buf0, tw, col, t);
     // i d2(kx) applied after the (linear) transform: a factor per column
     const T d2 = ok ? a.sym.d2[kx] : (T)0;
 #pragma unroll
@@ -451,11 +462,11 @@ __device__ __forceinline__ void rr_pass_body(const PassArgs<T>& a) {
   }
 }
 
-// the y passes at W = rr_wdef run two blocks per SM whatever their registers
-// (shared memory and the register file), so they are given 128 a thread
+// the FP32 passes at W = rr_wdef run two blocks per SM at most (shared memory
+// and the register file), so they are given 128 registers a thread
 template <typename T, int OP, int W>
 __host__ __device__ constexpr bool rr_y_wide() {
-  return OP != OP_STOKES && OP != OP_SOLUTE && sizeof(T) == 4 && W == rr_wdef<T>();
+  return sizeof(T) == 4 && W == rr_wdef<T>();
 }
 
 template <typename T, int N, int OP, int NC, int W>
