@@ -16,8 +16,8 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- * Grid      (n0, n1, n2): n1 and n2 powers of two in [8, 512], n0 the same or 1;
- *           axis 2 is contiguous. The cell is the unit cube; h_c = 1/n_c;
+ * Grid      (n0, n1, n2): n1 and n2 powers of two in [8, 512], n0 the same or 1
+ *           (then n1 >= 32); axis 2 is contiguous. The cell is the unit cube; h_c = 1/n_c;
  *           V = n0*n1*n2 voxels. n0 = 1 is a single plane: the two-dimensional
  *           cell of the paper's experiments (Section 4), with the symbols of
  *           axis 0 equal to zero (no variation along it); vector fields keep
@@ -152,7 +152,7 @@ acm_status acm_advdiff_default_params(acm_advdiff_params* p);
 /* Create a context for grids of shape (n0, n1, n2) whose device work runs on
  * `cuda_stream` (a cudaStream_t, NULL for the default stream) of the current
  * device. Returns ACM_ERR_UNSUPPORTED_SIZE unless n1 and n2 are powers of two
- * in [8, 512] and n0 is one too or 1. */
+ * in [8, 512] and n0 is one too, or 1 with n1 >= 32. */
 acm_status acm_create(acm_ctx** ctx, int n0, int n1, int n2, void* cuda_stream);
 acm_status acm_destroy(acm_ctx* ctx);
 

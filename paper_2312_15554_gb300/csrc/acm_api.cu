@@ -167,7 +167,11 @@ bool pow2_in_range(int n) { return n >= 8 && n <= 512 && (n & (n - 1)) == 0; }
 
 // Supported grids: n1, n2 powers of two in [8, 512]; n0 the same or 1 (a
 // single plane: the two-dimensional problem of the paper's experiments).
-bool shape_ok(int n0, int n1, int n2) { return (n0 == 1 || pow2_in_range(n0)) && pow2_in_range(n1) && pow2_in_range(n2); }
+// A plane cell needs n1 >= 32: the line-resident x passes hand lines out in
+// groups of up to 32 (one warp), and a plane of fewer lines forms none.
+bool shape_ok(int n0, int n1, int n2) {
+  return (pow2_in_range(n0) || (n0 == 1 && n1 >= 32)) && pow2_in_range(n1) && pow2_in_range(n2);
+}
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;

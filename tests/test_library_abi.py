@@ -57,6 +57,9 @@ def test_host_only_calls(libpath):
     h = ctypes.c_void_p()
     assert lib.acm_create(ctypes.byref(h), 12, 16, 16, None) == -10
     assert lib.acm_create(ctypes.byref(h), 16, 16, 1024, None) == -10
+    # a plane cell needs at least 32 lines (one warp's group of x lines)
+    assert lib.acm_create(ctypes.byref(h), 1, 16, 64, None) == -10
+    assert lib.acm_create(ctypes.byref(h), 1, 8, 8, None) == -10
     assert lib.acm_create(None, 16, 16, 16, None) == -1
     assert lib.acm_stokes_default_params(None) == -1
 
