@@ -630,6 +630,56 @@ __global__ void __launch_bounds__(NC * 64) k_x_r2c(cx<T>* __restrict__ spec, con
   x_post_store_spec<T, N2, NC>(sm, spec + p * specProbStride, g.S, g.P, line0, tw);
 }
 
+// Line-resident C2R along the contiguous axis (acm_xline.cuh): a warp owns
+// LPW lines of one component at a time; the row arrives by cp.async, the
+// inverse transform leaves the voxel pairs 2k, 2k+1 (k = t + TL m) of the lane
+// in registers, and they are stored as vectors. blockIdx.y = problem * nc +
+// component.
+template <typename T, int N2>
+__global__ void __launch_bounds__(XS_WARPS * 32) k_x_c2r_lr(const cx<T>* __restrict__ spec, T* __restrict__ out,
+                                                           Geo g, int nc, long long outProbStride,
+                                                           long long specProbStride, const cx<T>* __restrict__ twg) {
+  using L = XL<T, N2>;
+  constexpr int M = L::M, E = L::E, TL = L::TL, LPW = L::LPW;
+  constexpr int LB = L::template lb<1>();
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* tw = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* lines = tw + xs_tw_slots<T, N2>();
+  const int p = blockIdx.y / nc, c = blockIdx.y % nc;
+  load_tw_x<T, N2>(tw, twg);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ll = lane / TL, t = lane % TL;
+  const unsigned mask = xl_mask();
+  cx<T>* bl = lines + (warp * LPW + ll) * LB;
+  const cx<T>* sp = spec + p * specProbStride + c * g.S;
+  T* op = out + p * outProbStride + c * g.V;
+  const int ngroups = g.n0 * g.n1 / LPW;
+  const int gbase = (blockIdx.x * XS_WARPS + warp) * XS_GPW;
+#pragma unroll 1
+  for (int gi = 0; gi < XS_GPW; ++gi) {
+    const int grp = gbase + gi;
+    if (grp >= ngroups) break;
+    const long long line = (long long)grp * LPW + ll;
+    __syncwarp(mask);  // the previous line's readers of bl are done
+    for (int e = t; e <= M; e += TL) cp_async<(int)sizeof(cx<T>)>(&bl[pad(e)], &sp[line * g.P + e]);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp(mask);
+    cx<T> v[E];
+    xl_inverse<T, N2>(bl, tw, t, mask, v);
+    T* orow = op + line * N2;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      T2 w;
+      w.x = v[m].x;
+      w.y = v[m].y;
+      *reinterpret_cast<T2*>(orow + 2 * (t + TL * m)) = w;
+    }
+  }
+}
+
 template <typename T, int N2, int NC>
 __global__ void __launch_bounds__(NC * 64) k_x_c2r(const cx<T>* __restrict__ spec, T* __restrict__ out, Geo g,
                                                   long long outProbStride, long long specProbStride,

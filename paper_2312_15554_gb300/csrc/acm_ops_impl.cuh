@@ -129,9 +129,21 @@ static cudaError_t l_x_c2r_nc(const Geo& g, int nprob, const void* spec, long lo
   k_x_c2r<T, N2, NC><<<grid, NC * 64, smem, s>>>((const cx<T>*)spec, (T*)out, g, ops, sps, (const cx<T>*)tw);
   return cudaGetLastError();
 }
+// The line-resident kernel stores voxel pairs as vectors: it runs when `out`
+// is aligned to a pair (the strides are even); otherwise the block-phase
+// kernel with element stores does.
 template <typename T, int N2>
 static cudaError_t l_x_c2r(const Geo& g, int nprob, int nc, const void* spec, long long sps, void* out,
                            long long ops, const void* tw, cudaStream_t s) {
+  if ((uintptr_t)out % (2 * sizeof(T)) == 0 && ops % 2 == 0 && g.V % 2 == 0) {
+    constexpr int smem = xs_smem_bytes<T, N2, 1, 0>();
+    static const cudaError_t attr = set_smem(k_x_c2r_lr<T, N2>, smem);
+    if (attr != cudaSuccess) return attr;
+    dim3 grid(xs_blocks(g.n0 * g.n1, XL<T, N2>::LPW), nprob * nc);
+    k_x_c2r_lr<T, N2><<<grid, XS_WARPS * 32, smem, s>>>((const cx<T>*)spec, (T*)out, g, nc, ops, sps,
+                                                        (const cx<T>*)tw);
+    return cudaGetLastError();
+  }
   if (nc == 1) return l_x_c2r_nc<T, N2, 1>(g, nprob, spec, sps, out, ops, tw, s);
   if (nc == 3) return l_x_c2r_nc<T, N2, 3>(g, nprob, spec, sps, out, ops, tw, s);
   return cudaErrorInvalidValue;
